@@ -1,0 +1,293 @@
+/*
+ * epbr.h — C ABI of libepbr, a GB300 (sm_103a) implementation of the per-pixel deferred
+ * physically-based shading pass of EasyPBR (Rosu & Behnke, "EasyPBR: A Lightweight
+ * Physically-Based Renderer", arXiv 2012.03325).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Every function returns an epbr_status.  On failure a thread-local message is available
+ *    from epbr_last_error().  No C++ exception crosses this boundary.
+ *  - The caller owns every buffer.  Buffers named "device" are CUDA device pointers on the
+ *    current device; "host" structs are read during the call only and may be freed after it
+ *    returns.  The library never frees caller memory and keeps no pointer after a call returns
+ *    (except the objects with an explicit create/destroy pair).
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).  All device
+ *    work is enqueued asynchronously on it.  Argument validation is synchronous and happens
+ *    before anything is enqueued; on a validation error nothing is enqueued.
+ *  - Images are row-major; `pitch` arguments are bytes between consecutive rows and must be a
+ *    multiple of 16 bytes for 16-byte texel formats (float4) and of the texel size otherwise.
+ *  - Pixel (x, y) has its centre at (x + 0.5, y + 0.5); y grows downwards; the camera looks
+ *    along its local -z axis.
+ *  - Environment maps are equirectangular.  Direction d maps to
+ *        u = 0.5 + atan2(d.x, -d.z) / (2 pi),   v = atan2(sqrt(d.x^2 + d.z^2), d.y) / pi,
+ *    texel (i, j) has its centre at ((i + 0.5)/W, (j + 0.5)/H); bilinear filtering wraps in u
+ *    and clamps in v.  (The paper stores the environment as a cubemap, Sec. 3.1; equirect is
+ *    the representation used here.)
+ */
+#ifndef EPBR_H
+#define EPBR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---------------------------------------------------------------------------------------- */
+/* Status                                                                                   */
+/* ---------------------------------------------------------------------------------------- */
+typedef int32_t epbr_status;
+enum {
+  EPBR_OK = 0,
+  EPBR_ERR_INVALID_ARG = 1,   /* a pointer, size, pitch, format or flag is invalid */
+  EPBR_ERR_UNSUPPORTED = 2,   /* valid request this build does not implement */
+  EPBR_ERR_CUDA = 3,          /* a CUDA runtime call failed; message has cudaGetErrorString */
+  EPBR_ERR_NO_MEMORY = 4,     /* workspace too small or a library-owned allocation failed */
+  EPBR_ERR_ADMISSION = 5,     /* serving: request can never fit the memory budget */
+  EPBR_ERR_TIMEOUT = 6,       /* a bounded wait ran out */
+  EPBR_ERR_DEVICE_STATUS = 7  /* a kernel reported an error through its device status word */
+};
+
+/* Thread-local message describing the last failure of a call made by this thread. */
+const char* epbr_last_error(void);
+/* Library version string. */
+const char* epbr_version(void);
+
+/* ---------------------------------------------------------------------------------------- */
+/* Scene description                                                                        */
+/* ---------------------------------------------------------------------------------------- */
+
+/* Pinhole camera.  view_to_world is a column-major 4x4 rigid transform: columns 0..2 are the
+ * camera's x (right), y (up) and z (backwards) axes in world space, column 3 is the eye.
+ * A pixel's view-space ray is r = (px, py, -1) with
+ *   px = (2 (x + 0.5) / width - 1) * tan(fov_y / 2) * width / height,
+ *   py = (1 - 2 (y + 0.5) / height) * tan(fov_y / 2),
+ * and the surface point at eye depth e is e * r (view space).  Host struct. */
+typedef struct epbr_camera {
+  float view_to_world[16];
+  float fov_y;       /* radians, in (0, pi) */
+  int32_t width;     /* full-resolution pixels, >= 1 */
+  int32_t height;    /* >= 1 */
+} epbr_camera;
+
+/* Point light: position, intensity and colour (Sec. 6 names exactly these three).
+ * Radiance arriving at P is intensity * color / |pos - P|^2; no range cutoff, no shadow.
+ * Arrays of lights live in DEVICE memory, 32 bytes each. */
+typedef struct epbr_light {
+  float pos[3];
+  float intensity;
+  float color[3];
+  float pad;
+} epbr_light;
+
+/* G-buffer (Table 1 of the paper gives four render targets; Sec. 4 stores depth instead of
+ * position).  Two storage formats:
+ *   EPBR_GBUFFER_FP32     rt[0] float4 (albedo.r, albedo.g, albedo.b, metalness)  16 B/px
+ *                         rt[1] float4 (normal.x, normal.y, normal.z, roughness)  16 B/px
+ *                         rt[2] unused (may be NULL)
+ *                         rt[3] float  eye depth e > 0, +inf where no surface      4 B/px
+ *   EPBR_GBUFFER_COMPACT  rt[0] uchar4 (sRGB8 albedo r, g, b, weight)              4 B/px
+ *                         rt[1] half2  octahedral unit normal (Cigolle et al. 2014) 4 B/px
+ *                         rt[2] uchar2 (UNORM8 metalness, UNORM8 roughness)         2 B/px
+ *                         rt[3] float  eye depth e, as above                        4 B/px
+ * Normals are in world space.  Albedo is linear in FP32 form and sRGB-encoded in COMPACT form.
+ * Roughness is clamped to [0.045, 1] and metalness to [0, 1] when decoded.  All rt pointers
+ * are DEVICE pointers; pitch[i] is bytes per row of rt[i].  The weight channel (used by the
+ * paper for surfel accumulation) is carried but not read.  Host struct. */
+enum { EPBR_GBUFFER_FP32 = 0, EPBR_GBUFFER_COMPACT = 1 };
+typedef struct epbr_gbuffer {
+  int32_t format;
+  int32_t width;
+  int32_t height;
+  int32_t reserved;
+  const void* rt[4];
+  int64_t pitch[4];
+} epbr_gbuffer;
+
+/* HDR environment map (Sec. 3.1: every texel acts as a light source).  DEVICE float4 texels
+ * (r, g, b, ignored), dense rows of `width` texels.  Host struct. */
+typedef struct epbr_env {
+  const float* texels;
+  int32_t width;
+  int32_t height;
+} epbr_env;
+
+/* ---------------------------------------------------------------------------------------- */
+/* Image-based lighting precompute (Sec. 3.1; split sum of Karis 2013)                     */
+/* ---------------------------------------------------------------------------------------- */
+#define EPBR_MAX_LEVELS 16
+
+typedef struct epbr_ibl_params {
+  int32_t num_levels;         /* M in [1, EPBR_MAX_LEVELS]: specular mips, level m has
+                                 roughness m / (M - 1) (level 0 = copy of the source) */
+  int32_t prefilter_samples;  /* GGX importance samples per prefiltered texel, >= 1 */
+  int32_t lut_size;           /* S: the BRDF LUT is S x S float2, >= 1 */
+  int32_t lut_samples;        /* GGX samples per LUT texel, >= 1 */
+  int32_t irr_width;          /* diffuse irradiance map size (equirect), >= 1 */
+  int32_t irr_height;
+} epbr_ibl_params;
+
+/* Precomputed lighting set, all DEVICE pointers into one caller-owned buffer:
+ *   irradiance  float4[irr_height][irr_width]  cosine-weighted mean radiance E(n)/pi
+ *   lut         float2[S][S]   row j = roughness (j + 0.5)/S, column i = n.v = (i + 0.5)/S,
+ *                              value (A, B) with F_ss E_ss = F0 A + B
+ *   level[m]    float4[level_height[m]][level_width[m]], sizes max(1, W_e >> m) x
+ *               max(1, H_e >> m)
+ * Filled by epbr_ibl_layout; read by epbr_shade.  Host struct. */
+typedef struct epbr_ibl {
+  float* irradiance;
+  int32_t irr_width;
+  int32_t irr_height;
+  float* lut;
+  int32_t lut_size;
+  int32_t num_levels;
+  float* level[EPBR_MAX_LEVELS];
+  int32_t level_width[EPBR_MAX_LEVELS];
+  int32_t level_height[EPBR_MAX_LEVELS];
+} epbr_ibl;
+
+/* Computes the size of one lighting set for an env of env_width x env_height texels.  If
+ * `buffer` is NULL only *bytes is written.  Otherwise `buffer` must be a DEVICE allocation of
+ * at least *bytes bytes aligned to 256 B, and *out receives pointers into it (each sub-array
+ * 256-B aligned).  Host-only: enqueues nothing. */
+epbr_status epbr_ibl_layout(const epbr_ibl_params* params, int32_t env_width,
+                            int32_t env_height, void* buffer, size_t* bytes, epbr_ibl* out);
+
+/* Workspace bytes that epbr_precompute_ibl / epbr_irradiance need (the irradiance reduction
+ * keeps per-block partial sums there). */
+epbr_status epbr_precompute_ibl_workspace_size(const epbr_ibl_params* params,
+                                               int32_t env_width, int32_t env_height,
+                                               size_t* bytes);
+
+/* Full lighting-set precompute for one environment (Sec. 3.1: "increasingly blurrier
+ * versions" for the diffuse term, split-sum prefiltered mips plus a BRDF integration table for
+ * the specular term).  Runs epbr_brdf_lut, epbr_irradiance and epbr_prefilter on `stream`.
+ * `ibl` must come from epbr_ibl_layout with the same params and env size.  `workspace` is a
+ * DEVICE buffer of at least epbr_precompute_ibl_workspace_size bytes, 256-B aligned. */
+epbr_status epbr_precompute_ibl(const epbr_env* env, const epbr_ibl_params* params,
+                                const epbr_ibl* ibl, void* workspace, size_t workspace_bytes,
+                                void* stream);
+
+/* BRDF integration table (split sum, second factor; Sec. 3.1 citing Karis 2013).  For texel
+ * (i, j): mu = (i + 0.5)/S, r = (j + 0.5)/S, alpha = r^2, v = (sqrt(1 - mu^2), 0, mu),
+ * n = (0, 0, 1), Hammersley points (k/N, radical_inverse_2(k)), GGX half vectors, l = reflect.
+ * A = (1/N) sum_{n.l>0} (1 - Fc) Gvis,  B = (1/N) sum_{n.l>0} Fc Gvis,  Fc = (1 - v.h)^5,
+ * Gvis = G(n.l, n.v) (v.h) / ((n.h)(n.v)),  G Smith-Schlick with k = alpha / 2.
+ * `lut` is DEVICE float2[S][S]. */
+epbr_status epbr_brdf_lut(int32_t lut_size, int32_t num_samples, float* lut, void* stream);
+
+/* Diffuse irradiance map: for output texel direction n,
+ *   out(n) = sum_t L_t max(n.d_t, 0) Omega_t / sum_t max(n.d_t, 0) Omega_t
+ * over every source texel t (exact row solid angle Omega_t), i.e. E(n)/pi as a ratio
+ * estimator, exact for a uniform environment.  `out` is DEVICE float4[irr_h][irr_w].
+ * `workspace` as for epbr_precompute_ibl. */
+epbr_status epbr_irradiance(const epbr_env* env, int32_t irr_width, int32_t irr_height,
+                            float* out, void* workspace, size_t workspace_bytes, void* stream);
+
+/* Specular prefilter chain (split sum, first factor): level 0 is a copy of the source; level
+ * m >= 1 with roughness r = m/(M-1), alpha = r^2 and n = v = texel direction is
+ *   sum_k L(l_k) (n.l_k) / sum_k (n.l_k)  over the GGX half vectors of N Hammersley points,
+ * keeping n.l_k > 0, with L read bilinearly from the source.  `ibl` levels are written. */
+epbr_status epbr_prefilter(const epbr_env* env, int32_t num_samples, const epbr_ibl* ibl,
+                           void* stream);
+
+/* ---------------------------------------------------------------------------------------- */
+/* Screen-space ambient occlusion (Sec. 5.2: normal-oriented hemisphere of Bavoil & Sainz     */
+/* 2008, computed at half resolution and bilaterally blurred)                               */
+/* ---------------------------------------------------------------------------------------- */
+typedef struct epbr_ssao_params {
+  int32_t num_samples;   /* K >= 1 */
+  int32_t scale;         /* 1: AO at full resolution, 2: half resolution (the paper's) */
+  float radius;          /* hemisphere radius, world/view units, > 0 */
+  float bias;            /* depth bias, >= 0 */
+  int32_t blur_radius;   /* bilateral blur half-width in AO texels (3 = 7x7), 0..8 */
+  float sigma_s;         /* blur spatial sigma, AO texels, > 0 */
+  float sigma_z;         /* blur relative depth sigma, > 0 */
+  int32_t reserved;
+  const float* kernel;   /* DEVICE float4[K]: tangent-space sample offsets (x, y, z > 0, -) */
+  const float* noise;    /* DEVICE float2[16]: 4x4 tiled rotation vectors (view-space x, y) */
+} epbr_ssao_params;
+
+/* AO image size for a view: ceil(width/scale) x ceil(height/scale) floats. */
+epbr_status epbr_ssao_size(const epbr_gbuffer* gbuffer, const epbr_ssao_params* params,
+                           int32_t* ao_width, int32_t* ao_height);
+/* Workspace bytes for epbr_ssao (the unblurred AO image). */
+epbr_status epbr_ssao_workspace_size(const epbr_gbuffer* gbuffer,
+                                     const epbr_ssao_params* params, size_t* bytes);
+
+/* Unblurred AO.  AO texel (i, j) uses full-resolution pixel (scale*i, scale*j): view-space
+ * point P and normal n; noise vector (noise[(j%4)*4 + i%4], 0) made orthogonal to n gives the
+ * tangent frame (fallback to a branchless orthonormal basis when it is parallel to n).  Sample
+ * S_k = P + radius * TBN * kernel[k] is projected to pixel (floor X, floor Y); its depth e_b is
+ * fetched; the sample occludes by [e_b <= e_S - bias] * smoothstep(0, 1, radius / |e_P - e_b|).
+ * Off-screen, behind-camera and background samples do not occlude.  AO = 1 - sum / K.  AO of a
+ * background pixel is 1.  `ao` is DEVICE float, rows of `ao_pitch` bytes. */
+epbr_status epbr_ssao_raw(const epbr_gbuffer* gbuffer, const epbr_camera* camera,
+                          const epbr_ssao_params* params, float* ao, int64_t ao_pitch,
+                          void* stream);
+
+/* Depth-aware blur of an AO image: out_p = sum_q w_q ao_q / sum_q w_q over the
+ * (2R+1)^2 window (clipped to the image) with w_q = exp(-(dx^2+dy^2)/(2 sigma_s^2)) *
+ * exp(-|e_q - e_p| / (sigma_z e_p)), background taps weighted 0; background pixels get 1. */
+epbr_status epbr_ssao_blur(const epbr_gbuffer* gbuffer, const epbr_ssao_params* params,
+                           const float* ao_in, int64_t in_pitch, float* ao_out,
+                           int64_t out_pitch, void* stream);
+
+/* epbr_ssao_raw into `workspace`, then epbr_ssao_blur into `ao` (blur_radius 0: copy). */
+epbr_status epbr_ssao(const epbr_gbuffer* gbuffer, const epbr_camera* camera,
+                      const epbr_ssao_params* params, float* ao, int64_t ao_pitch,
+                      void* workspace, size_t workspace_bytes, void* stream);
+
+/* ---------------------------------------------------------------------------------------- */
+/* Deferred compose (Sec. 3 Eq. 1 with the UE4 Cook-Torrance model; Sec. 3.1 IBL with the     */
+/* multiple-scattering extension of Fdez-Aguera 2019; Sec. 5.4 compositing)                 */
+/* ---------------------------------------------------------------------------------------- */
+enum {
+  EPBR_SHADE_DIRECT = 1,        /* sum over point lights */
+  EPBR_SHADE_IBL = 2,           /* split-sum ambient term (needs ibl) */
+  EPBR_SHADE_MULTISCATTER = 4,  /* Fdez-Aguera energy compensation of the IBL term */
+  EPBR_SHADE_DIFFUSE_ONLY = 8,  /* Lambert only: albedo/pi direct, albedo*irradiance ambient */
+  EPBR_SHADE_ALL = 7
+};
+enum { EPBR_HDR_RGBA32F = 0, EPBR_HDR_RGBA16F = 1 };
+
+typedef struct epbr_shade_params {
+  uint32_t flags;        /* EPBR_SHADE_* */
+  int32_t ao_scale;      /* pixel (x, y) reads ao[(y/ao_scale) * pitch + x/ao_scale] */
+  const float* ao;       /* DEVICE AO image or NULL (AO = 1); multiplies the ambient term */
+  int64_t ao_pitch;      /* bytes */
+} epbr_shade_params;
+
+/* Per pixel: decode the G-buffer, reconstruct P from depth, v = normalize(eye - P),
+ *   L_direct = sum_i [ (1 - F) c_diff / pi + D G F / (4 (n.l)(n.v)) ] I_i c_i / d_i^2 (n.l)
+ * for n.l > 0 (GGX D with alpha = r^2, Smith-Schlick G with k = (r + 1)^2 / 8, Schlick F from
+ * F0 = mix(0.04, albedo, metal), c_diff = albedo (1 - metal), n.v clamped to >= 1e-4), plus the
+ * split-sum ambient term times AO.  Background pixels (e = +inf) get the environment's level 0
+ * along the view ray (0 without IBL).  Output: DEVICE RGBA32F or RGBA16F (round to nearest,
+ * saturated to +-65504), alpha = 1.  `lights` is DEVICE epbr_light[num_lights], num_lights in
+ * [0, 65536].  `ibl` may be NULL when flags has no EPBR_SHADE_IBL. */
+epbr_status epbr_shade(const epbr_gbuffer* gbuffer, const epbr_camera* camera,
+                       const epbr_light* lights, int32_t num_lights, const epbr_ibl* ibl,
+                       const epbr_shade_params* params, void* hdr, int32_t hdr_format,
+                       int64_t hdr_pitch, void* stream);
+
+/* ---------------------------------------------------------------------------------------- */
+/* Tone mapping (Sec. 5.4: ACES, optional Reinhard, then gamma correction)                  */
+/* ---------------------------------------------------------------------------------------- */
+enum { EPBR_TONEMAP_ACES = 0, EPBR_TONEMAP_REINHARD = 1 };
+typedef struct epbr_tonemap_params {
+  float exposure;  /* x = exposure * hdr */
+  int32_t op;      /* EPBR_TONEMAP_ACES (Narkowicz 2015 fit) or EPBR_TONEMAP_REINHARD x/(1+x) */
+} epbr_tonemap_params;
+
+/* out = round_half_up(255 * sRGB_OETF(clamp(op(exposure * hdr.rgb), 0, 1))), alpha 255.
+ * `hdr` DEVICE RGBA32F/RGBA16F, `out` DEVICE uchar4. */
+epbr_status epbr_tonemap(const void* hdr, int32_t hdr_format, int32_t width, int32_t height,
+                         int64_t hdr_pitch, const epbr_tonemap_params* params, uint8_t* out,
+                         int64_t out_pitch, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* EPBR_H */

@@ -1,0 +1,798 @@
+/*
+ * epbr_oracle.c — plain, slow, double-precision CPU restatement of the deferred PBR shading
+ * pass of EasyPBR (arXiv 2012.03325).  TEST INFRASTRUCTURE ONLY: it exists to check the CUDA
+ * library and is called only by the test suite, the package's smoke check and the benchmark's
+ * CPU-baseline leg.  It shares no code, header, table or constant generator with the CUDA
+ * path and includes nothing from it.
+ *
+ * Each function follows the definition it cites, in the order the source states it, with no
+ * blocking, fusion or reordering:
+ *   - reflectance equation (paper Sec. 3, Eq. 1) with the Cook-Torrance model of UE4 (Sec. 3;
+ *     Karis 2013: GGX distribution, Smith-Schlick geometry with k = (r+1)^2/8, Schlick Fresnel);
+ *   - image-based lighting (Sec. 3.1): diffuse irradiance by exact quadrature, split-sum
+ *     prefiltered environment and BRDF table (Karis 2013, Hammersley + GGX importance
+ *     sampling, k = alpha/2), multiple-scattering compensation (Fdez-Aguera 2019);
+ *   - G-buffer of Table 1 with position reconstructed from depth (Sec. 4);
+ *   - normal-oriented hemisphere SSAO at half resolution with a bilateral blur (Sec. 5.2;
+ *     Bavoil & Sainz 2008);
+ *   - ACES filmic tone mapping (Narkowicz 2015 fit) or Reinhard, then the sRGB transfer
+ *     function of IEC 61966-2-1 (Sec. 5.4).
+ * Conventions the paper leaves open (equirect mapping, sample sets, SSAO constants, rounding)
+ * are stated beside the code that uses them.
+ *
+ * Parity status: every function here is pinned by the CPU test suite (closed forms, invariants,
+ * brute-force quadrature, special cases); see tests/test_oracle_pins.py.
+ */
+#include <math.h>
+#include <pthread.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#include <unistd.h>
+
+#define OR_PI 3.14159265358979323846
+
+/* ------------------------------------------------------------------------------------------ */
+/* threads: split an index range into contiguous chunks                                       */
+/* ------------------------------------------------------------------------------------------ */
+typedef void (*or_body_fn)(void* ctx, long i0, long i1);
+typedef struct {
+  or_body_fn fn;
+  void* ctx;
+  long i0, i1;
+} or_job;
+
+static void* or_job_run(void* p) {
+  or_job* j = (or_job*)p;
+  j->fn(j->ctx, j->i0, j->i1);
+  return NULL;
+}
+
+static int or_threads(int requested) {
+  if (requested > 0) return requested;
+  long n = sysconf(_SC_NPROCESSORS_ONLN);
+  return n > 0 ? (int)n : 1;
+}
+
+static void or_parallel_for(long n, int threads, or_body_fn fn, void* ctx) {
+  int t = or_threads(threads);
+  if (t > n) t = (int)(n > 0 ? n : 1);
+  if (t <= 1) {
+    fn(ctx, 0, n);
+    return;
+  }
+  pthread_t* th = (pthread_t*)malloc(sizeof(pthread_t) * t);
+  or_job* jobs = (or_job*)malloc(sizeof(or_job) * t);
+  for (int k = 0; k < t; ++k) {
+    jobs[k].fn = fn;
+    jobs[k].ctx = ctx;
+    jobs[k].i0 = n * k / t;
+    jobs[k].i1 = n * (k + 1) / t;
+    pthread_create(&th[k], NULL, or_job_run, &jobs[k]);
+  }
+  for (int k = 0; k < t; ++k) pthread_join(th[k], NULL);
+  free(th);
+  free(jobs);
+}
+
+int or_num_threads(int requested) { return or_threads(requested); }
+
+/* ------------------------------------------------------------------------------------------ */
+/* small vector helpers                                                                        */
+/* ------------------------------------------------------------------------------------------ */
+static double dot3(const double* a, const double* b) { return a[0] * b[0] + a[1] * b[1] + a[2] * b[2]; }
+static void normalize3(double* a) {
+  double s = sqrt(dot3(a, a));
+  a[0] /= s;
+  a[1] /= s;
+  a[2] /= s;
+}
+static void cross3(const double* a, const double* b, double* c) {
+  c[0] = a[1] * b[2] - a[2] * b[1];
+  c[1] = a[2] * b[0] - a[0] * b[2];
+  c[2] = a[0] * b[1] - a[1] * b[0];
+}
+static double clampd(double x, double lo, double hi) { return x < lo ? lo : (x > hi ? hi : x); }
+
+/* Branchless orthonormal basis around a unit vector n (Duff et al., JCGT 6(1), 2017). */
+static void onb_duff(const double* n, double* t, double* b) {
+  double s = copysign(1.0, n[2]);
+  double a = -1.0 / (s + n[2]);
+  double c = n[0] * n[1] * a;
+  t[0] = 1.0 + s * n[0] * n[0] * a;
+  t[1] = s * c;
+  t[2] = -s * n[0];
+  b[0] = c;
+  b[1] = s + n[1] * n[1] * a;
+  b[2] = -n[1];
+}
+
+/* ------------------------------------------------------------------------------------------ */
+/* equirectangular environment maps (the paper uses a cubemap, Sec. 3.1)                      */
+/*   u = 0.5 + atan2(d.x, -d.z) / (2 pi),  v = atan2(sqrt(d.x^2 + d.z^2), d.y) / pi           */
+/* ------------------------------------------------------------------------------------------ */
+static void dir_to_uv(const double* d, double* u, double* v) {
+  *u = 0.5 + atan2(d[0], -d[2]) / (2.0 * OR_PI);
+  *v = atan2(sqrt(d[0] * d[0] + d[2] * d[2]), d[1]) / OR_PI;
+}
+static void uv_to_dir(double u, double v, double* d) {
+  double phi = 2.0 * OR_PI * (u - 0.5), th = OR_PI * v;
+  d[0] = sin(th) * sin(phi);
+  d[1] = cos(th);
+  d[2] = -sin(th) * cos(phi);
+}
+/* Bilinear read of an RGBA (4 doubles per texel) equirect map: wrap in u, clamp in v. */
+static void equirect_bilinear(const double* map, int W, int H, double u, double v, double* out) {
+  double x = u * W - 0.5, y = v * H - 0.5;
+  double x0 = floor(x), y0 = floor(y);
+  double fx = x - x0, fy = y - y0;
+  long ix0 = (long)x0, iy0 = (long)y0;
+  long i0 = ((ix0 % W) + W) % W, i1 = (((ix0 + 1) % W) + W) % W;
+  long j0 = iy0 < 0 ? 0 : (iy0 > H - 1 ? H - 1 : iy0);
+  long j1 = iy0 + 1 < 0 ? 0 : (iy0 + 1 > H - 1 ? H - 1 : iy0 + 1);
+  for (int c = 0; c < 3; ++c) {
+    double a = map[(j0 * W + i0) * 4 + c], b = map[(j0 * W + i1) * 4 + c];
+    double p = map[(j1 * W + i0) * 4 + c], q = map[(j1 * W + i1) * 4 + c];
+    out[c] = (1.0 - fy) * ((1.0 - fx) * a + fx * b) + fy * ((1.0 - fx) * p + fx * q);
+  }
+}
+static void equirect_lookup(const double* map, int W, int H, const double* d, double* out) {
+  double u, v;
+  dir_to_uv(d, &u, &v);
+  equirect_bilinear(map, W, H, u, v, out);
+}
+
+/* ------------------------------------------------------------------------------------------ */
+/* Hammersley set and GGX importance sampling (Karis 2013)                                     */
+/* ------------------------------------------------------------------------------------------ */
+/* Van der Corput radical inverse in base 2: the bits of i mirrored about the binary point. */
+static double radical_inverse2(uint32_t i) {
+  double r = 0.0, f = 0.5;
+  while (i) {
+    if (i & 1u) r += f;
+    f *= 0.5;
+    i >>= 1;
+  }
+  return r;
+}
+/* Half vector for Hammersley point (xi1, xi2) = (k/N, radical_inverse(k)) around n:
+ * phi = 2 pi xi1, cos(theta) = sqrt((1 - xi2) / (1 + (alpha^2 - 1) xi2)), i.e. the inverse CDF
+ * of the GGX distribution of normals D(h)(n.h). */
+static void ggx_half_vector(double xi1, double xi2, double alpha, const double* n, double* h) {
+  double a2 = alpha * alpha;
+  double phi = 2.0 * OR_PI * xi1;
+  double ct = sqrt((1.0 - xi2) / (1.0 + (a2 - 1.0) * xi2));
+  double st = sqrt(1.0 - ct * ct);
+  double hx = st * cos(phi), hy = st * sin(phi), hz = ct;
+  double t[3], b[3];
+  onb_duff(n, t, b);
+  for (int c = 0; c < 3; ++c) h[c] = t[c] * hx + b[c] * hy + n[c] * hz;
+}
+
+/* ------------------------------------------------------------------------------------------ */
+/* Cook-Torrance BRDF of UE4 (paper Sec. 3; Karis 2013)                                        */
+/* ------------------------------------------------------------------------------------------ */
+static double ggx_D(double nh, double alpha) {
+  double a2 = alpha * alpha;
+  double den = nh * nh * (a2 - 1.0) + 1.0;
+  return a2 / (OR_PI * den * den);
+}
+static double smith_schlick_G1(double x, double k) { return x / (x * (1.0 - k) + k); }
+
+#define OR_ROUGH_MIN 0.045
+#define OR_NV_MIN 1e-4
+
+/* f_r(l, v) in RGB for unit n, l, v and a metalness/roughness material:
+ *   f = (1 - F) c_diff / pi + D G F / (4 (n.l)(n.v)),
+ * D = GGX with alpha = r^2, G = G1(n.l) G1(n.v) with k = (r + 1)^2 / 8,
+ * F = F0 + (1 - F0)(1 - v.h)^5, F0 = mix(0.04, albedo, metal), c_diff = albedo (1 - metal).
+ * n.l and n.v must be positive. */
+void or_brdf(const double* n, const double* l, const double* v, const double* albedo,
+             double metal, double rough, double* out) {
+  double h[3] = {l[0] + v[0], l[1] + v[1], l[2] + v[2]};
+  normalize3(h);
+  double nl = dot3(n, l), nv = dot3(n, v), nh = dot3(n, h), vh = dot3(v, h);
+  double alpha = rough * rough;
+  double k = (rough + 1.0) * (rough + 1.0) / 8.0;
+  double D = ggx_D(nh, alpha);
+  double G = smith_schlick_G1(nl, k) * smith_schlick_G1(nv, k);
+  double fc = pow(1.0 - vh, 5.0);
+  for (int c = 0; c < 3; ++c) {
+    double F0 = 0.04 * (1.0 - metal) + albedo[c] * metal;
+    double F = F0 + (1.0 - F0) * fc;
+    double cdiff = albedo[c] * (1.0 - metal);
+    out[c] = (1.0 - F) * cdiff / OR_PI + D * G * F / (4.0 * nl * nv);
+  }
+}
+
+/* ------------------------------------------------------------------------------------------ */
+/* A1: BRDF integration table (split sum, second factor)                                       */
+/* ------------------------------------------------------------------------------------------ */
+typedef struct {
+  int S, N;
+  double* out;
+} lut_ctx;
+
+static void lut_body(void* p, long i0, long i1) {
+  lut_ctx* c = (lut_ctx*)p;
+  const double n[3] = {0.0, 0.0, 1.0};
+  for (long t = i0; t < i1; ++t) {
+    int i = (int)(t % c->S), j = (int)(t / c->S);
+    double mu = (i + 0.5) / c->S, r = (j + 0.5) / c->S;
+    double alpha = r * r, k = alpha / 2.0;
+    double v[3] = {sqrt(1.0 - mu * mu), 0.0, mu};
+    double A = 0.0, B = 0.0;
+    for (int s = 0; s < c->N; ++s) {
+      double h[3], l[3];
+      ggx_half_vector((double)s / c->N, radical_inverse2((uint32_t)s), alpha, n, h);
+      double vh = dot3(v, h);
+      for (int q = 0; q < 3; ++q) l[q] = 2.0 * vh * h[q] - v[q];
+      double nl = l[2], nh = h[2], nv = mu;
+      if (nl > 0.0) {
+        double G = smith_schlick_G1(nl, k) * smith_schlick_G1(nv, k);
+        double Gvis = G * vh / (nh * nv);
+        double Fc = pow(1.0 - vh, 5.0);
+        A += (1.0 - Fc) * Gvis;
+        B += Fc * Gvis;
+      }
+    }
+    c->out[t * 2 + 0] = A / c->N;
+    c->out[t * 2 + 1] = B / c->N;
+  }
+}
+
+/* out: S*S*2 doubles, row j = roughness, column i = n.v. */
+int or_brdf_lut(int S, int N, double* out, int threads) {
+  if (S < 1 || N < 1 || !out) return 1;
+  lut_ctx c = {S, N, out};
+  or_parallel_for((long)S * S, threads, lut_body, &c);
+  return 0;
+}
+
+/* ------------------------------------------------------------------------------------------ */
+/* A2: diffuse irradiance by exact quadrature over every source texel                          */
+/*   out(n) = sum_t L_t max(n.d_t, 0) Omega_t / sum_t max(n.d_t, 0) Omega_t                   */
+/*   Omega of row y = (2 pi / W)(cos(pi y / H) - cos(pi (y + 1) / H))                          */
+/* ------------------------------------------------------------------------------------------ */
+typedef struct {
+  const double* env;
+  int We, He, Wi, Hi;
+  const int* texels;
+  double* out;
+} irr_ctx;
+
+static void irr_body(void* p, long i0, long i1) {
+  irr_ctx* c = (irr_ctx*)p;
+  for (long t = i0; t < i1; ++t) {
+    long idx = c->texels ? c->texels[t] : t;
+    int i = (int)(idx % c->Wi), j = (int)(idx / c->Wi);
+    double n[3];
+    uv_to_dir((i + 0.5) / c->Wi, (j + 0.5) / c->Hi, n);
+    double num[3] = {0, 0, 0}, den = 0.0;
+    for (int y = 0; y < c->He; ++y) {
+      double omega = (2.0 * OR_PI / c->We) * (cos(OR_PI * y / c->He) - cos(OR_PI * (y + 1) / c->He));
+      for (int x = 0; x < c->We; ++x) {
+        double d[3];
+        uv_to_dir((x + 0.5) / c->We, (y + 0.5) / c->He, d);
+        double w = dot3(n, d);
+        if (w <= 0.0) continue;
+        w *= omega;
+        const double* L = c->env + ((long)y * c->We + x) * 4;
+        num[0] += L[0] * w;
+        num[1] += L[1] * w;
+        num[2] += L[2] * w;
+        den += w;
+      }
+    }
+    for (int q = 0; q < 3; ++q) c->out[t * 3 + q] = num[q] / den;
+  }
+}
+
+/* env: He*We*4 doubles.  texels: indices j*Wi+i to evaluate (NULL = all, in order).
+ * out: n*3 doubles. */
+int or_irradiance(const double* env, int We, int He, int Wi, int Hi, const int* texels,
+                  long n, double* out, int threads) {
+  if (!env || !out || We < 1 || He < 1 || Wi < 1 || Hi < 1) return 1;
+  irr_ctx c = {env, We, He, Wi, Hi, texels, out};
+  long cnt = texels ? n : (long)Wi * Hi;
+  or_parallel_for(cnt, threads, irr_body, &c);
+  return 0;
+}
+
+/* ------------------------------------------------------------------------------------------ */
+/* A3: GGX-prefiltered environment level m >= 1 (split sum, first factor), n = v = R           */
+/* ------------------------------------------------------------------------------------------ */
+typedef struct {
+  const double* env;
+  int We, He, M, N, level, Wl, Hl;
+  const int* texels;
+  double* out;
+} pre_ctx;
+
+static void pre_body(void* p, long i0, long i1) {
+  pre_ctx* c = (pre_ctx*)p;
+  double r = (c->M > 1) ? (double)c->level / (c->M - 1) : 0.0;
+  double alpha = r * r;
+  for (long t = i0; t < i1; ++t) {
+    long idx = c->texels ? c->texels[t] : t;
+    int i = (int)(idx % c->Wl), j = (int)(idx / c->Wl);
+    double n[3];
+    uv_to_dir((i + 0.5) / c->Wl, (j + 0.5) / c->Hl, n);
+    const double* v = n;
+    double sum[3] = {0, 0, 0}, wsum = 0.0;
+    for (int s = 0; s < c->N; ++s) {
+      double h[3], l[3], L[3];
+      ggx_half_vector((double)s / c->N, radical_inverse2((uint32_t)s), alpha, n, h);
+      double vh = dot3(v, h);
+      for (int q = 0; q < 3; ++q) l[q] = 2.0 * vh * h[q] - v[q];
+      double nl = dot3(n, l);
+      if (nl > 0.0) {
+        equirect_lookup(c->env, c->We, c->He, l, L);
+        for (int q = 0; q < 3; ++q) sum[q] += L[q] * nl;
+        wsum += nl;
+      }
+    }
+    for (int q = 0; q < 3; ++q) c->out[t * 3 + q] = sum[q] / wsum;
+  }
+}
+
+static int level_dim(int d, int m) {
+  int r = d >> m;
+  return r < 1 ? 1 : r;
+}
+
+/* Texels of level `level` (1 <= level < M) of the chain over env (He*We*4 doubles). */
+int or_prefilter(const double* env, int We, int He, int M, int N, int level, const int* texels,
+                 long n, double* out, int threads) {
+  if (!env || !out || M < 2 || level < 1 || level >= M || N < 1) return 1;
+  pre_ctx c = {env, We, He, M, N, level, level_dim(We, level), level_dim(He, level), texels, out};
+  long cnt = texels ? n : (long)c.Wl * c.Hl;
+  or_parallel_for(cnt, threads, pre_body, &c);
+  return 0;
+}
+
+/* ------------------------------------------------------------------------------------------ */
+/* A4: G-buffer decode                                                                          */
+/* Decoded layout, 9 doubles per pixel: albedo rgb (linear), metal, normal xyz, rough, depth.   */
+/* ------------------------------------------------------------------------------------------ */
+/* IEEE binary16 bits -> value, from the format's definition. */
+static double half_to_double(uint16_t h) {
+  int s = (h >> 15) & 1, e = (h >> 10) & 31, f = h & 1023;
+  double v;
+  if (e == 0)
+    v = ldexp((double)f, -24);
+  else if (e == 31)
+    v = f ? NAN : INFINITY;
+  else
+    v = ldexp(1024.0 + f, e - 25);
+  return s ? -v : v;
+}
+/* sRGB electro-optical transfer (IEC 61966-2-1) for code c / 255. */
+static double srgb_decode(double x) {
+  return x <= 0.04045 ? x / 12.92 : pow((x + 0.055) / 1.055, 2.4);
+}
+
+/* Compact form of Table 1: rt0 RGBA8 sRGB albedo + weight, rt1 2 x FP16 octahedral normal
+ * (Cigolle et al. 2014), rt2 2 x UNORM8 (metal, rough), rt3 FP32 depth. */
+int or_decode_compact(const uint8_t* rt0, const uint16_t* rt1, const uint8_t* rt2,
+                      const float* depth, long npx, double* gb) {
+  for (long p = 0; p < npx; ++p) {
+    double* o = gb + p * 9;
+    for (int c = 0; c < 3; ++c) o[c] = srgb_decode(rt0[p * 4 + c] / 255.0);
+    o[3] = rt2[p * 2 + 0] / 255.0;
+    double x = half_to_double(rt1[p * 2 + 0]), y = half_to_double(rt1[p * 2 + 1]);
+    double z = 1.0 - fabs(x) - fabs(y);
+    if (z < 0.0) {
+      double nx = (1.0 - fabs(y)) * (x >= 0.0 ? 1.0 : -1.0);
+      double ny = (1.0 - fabs(x)) * (y >= 0.0 ? 1.0 : -1.0);
+      x = nx;
+      y = ny;
+    }
+    o[4] = x;
+    o[5] = y;
+    o[6] = z;
+    o[7] = rt2[p * 2 + 1] / 255.0;
+    o[8] = depth[p];
+  }
+  return 0;
+}
+
+/* ------------------------------------------------------------------------------------------ */
+/* camera: pixel rays and position from depth (Sec. 4: position is not stored)                  */
+/* ------------------------------------------------------------------------------------------ */
+typedef struct {
+  double v2w[16]; /* column-major */
+  double fov_y;
+  int W, H;
+} or_camera;
+
+static void view_ray(const or_camera* cam, double x, double y, double* r) {
+  double t = tan(0.5 * cam->fov_y), aspect = (double)cam->W / cam->H;
+  r[0] = (2.0 * x / cam->W - 1.0) * t * aspect;
+  r[1] = (1.0 - 2.0 * y / cam->H) * t;
+  r[2] = -1.0;
+}
+static void rot_apply(const or_camera* cam, const double* a, double* b) {
+  for (int i = 0; i < 3; ++i) b[i] = cam->v2w[i] * a[0] + cam->v2w[4 + i] * a[1] + cam->v2w[8 + i] * a[2];
+}
+static void rot_apply_t(const or_camera* cam, const double* a, double* b) {
+  for (int i = 0; i < 3; ++i)
+    b[i] = cam->v2w[4 * i + 0] * a[0] + cam->v2w[4 * i + 1] * a[1] + cam->v2w[4 * i + 2] * a[2];
+}
+static int is_surface(double e) { return e > 0.0 && e < INFINITY; }
+
+/* ------------------------------------------------------------------------------------------ */
+/* A5 / A6: SSAO (Sec. 5.2)                                                                     */
+/* ------------------------------------------------------------------------------------------ */
+typedef struct {
+  int K, scale, blur_radius;
+  double radius, bias, sigma_s, sigma_z;
+  const double* kernel; /* K*3 */
+  const double* noise;  /* 16*2 */
+} or_ssao_params;
+
+static double smoothstep01(double x) {
+  x = clampd(x, 0.0, 1.0);
+  return x * x * (3.0 - 2.0 * x);
+}
+
+/* Occlusion of one sample against depth pixel (ix, iy), or -1 when nothing is there. */
+static double occ_at(const double* gb, const or_camera* cam, const or_ssao_params* sp, long ix,
+                     long iy, double eP, double eS) {
+  if (ix < 0 || iy < 0 || ix >= cam->W || iy >= cam->H) return 0.0;
+  double eb = gb[(iy * cam->W + ix) * 9 + 8];
+  if (!is_surface(eb)) return 0.0;
+  if (!(eb <= eS - sp->bias)) return 0.0;
+  return smoothstep01(sp->radius / fabs(eP - eb));
+}
+
+#define OR_TIE_PX 2e-3
+#define OR_TIE_DEPTH 1e-5
+
+/* Raw AO of AO texel (i, j); lo/hi bound the value over every outcome of a pixel-boundary or
+ * depth-comparison decision that lies within rounding distance of its threshold. */
+static void ssao_raw_texel(const double* gb, const or_camera* cam, const or_ssao_params* sp,
+                           int i, int j, double* ao, double* lo, double* hi) {
+  long X0 = (long)sp->scale * i, Y0 = (long)sp->scale * j;
+  const double* g = gb + (Y0 * cam->W + X0) * 9;
+  double eP = g[8];
+  if (!is_surface(eP)) {
+    *ao = *lo = *hi = 1.0;
+    return;
+  }
+  double r[3], P[3], nw[3] = {g[4], g[5], g[6]}, n[3];
+  view_ray(cam, X0 + 0.5, Y0 + 0.5, r);
+  for (int q = 0; q < 3; ++q) P[q] = eP * r[q];
+  normalize3(nw);
+  rot_apply_t(cam, nw, n);
+  /* Tangent frame: the tiled noise vector made orthogonal to n (Gram-Schmidt). */
+  const double* nz = sp->noise + ((j % 4) * 4 + (i % 4)) * 2;
+  double rv[3] = {nz[0], nz[1], 0.0}, t[3], b[3];
+  double rn = dot3(rv, n);
+  for (int q = 0; q < 3; ++q) t[q] = rv[q] - n[q] * rn;
+  double tl = sqrt(dot3(t, t));
+  int frame_tie = fabs(tl - 1e-4) < 1e-6;
+  if (tl < 1e-4) {
+    onb_duff(n, t, b);
+  } else {
+    for (int q = 0; q < 3; ++q) t[q] /= tl;
+    cross3(n, t, b);
+  }
+  double tA = tan(0.5 * cam->fov_y), aspect = (double)cam->W / cam->H;
+  double sum = 0.0, sum_lo = 0.0, sum_hi = 0.0;
+  for (int k = 0; k < sp->K; ++k) {
+    const double* ks = sp->kernel + k * 3;
+    double S[3];
+    for (int q = 0; q < 3; ++q) S[q] = P[q] + sp->radius * (t[q] * ks[0] + b[q] * ks[1] + n[q] * ks[2]);
+    double eS = -S[2];
+    double occ = 0.0, olo, ohi;
+    if (eS <= 0.0) {
+      olo = ohi = 0.0;
+      if (eS > -OR_TIE_DEPTH) olo = 0.0, ohi = 1.0;
+    } else {
+      double x = ((S[0] / eS) / (tA * aspect) + 1.0) * 0.5 * cam->W;
+      double y = (1.0 - (S[1] / eS) / tA) * 0.5 * cam->H;
+      long ix = (long)floor(x), iy = (long)floor(y);
+      occ = occ_at(gb, cam, sp, ix, iy, eP, eS);
+      olo = ohi = occ;
+      /* candidate pixels: the nominal one, plus the neighbour across a boundary in reach */
+      long cx[2] = {ix, ix}, cy[2] = {iy, iy};
+      double fx = x - floor(x), fy = y - floor(y);
+      if (fx < OR_TIE_PX) cx[1] = ix - 1;
+      if (fx > 1.0 - OR_TIE_PX) cx[1] = ix + 1;
+      if (fy < OR_TIE_PX) cy[1] = iy - 1;
+      if (fy > 1.0 - OR_TIE_PX) cy[1] = iy + 1;
+      for (int a = 0; a < 2; ++a)
+        for (int c = 0; c < 2; ++c) {
+          long px = cx[a], py = cy[c];
+          double o = occ_at(gb, cam, sp, px, py, eP, eS);
+          if (o < olo) olo = o;
+          if (o > ohi) ohi = o;
+          if (px >= 0 && py >= 0 && px < cam->W && py < cam->H) {
+            double eb = gb[(py * cam->W + px) * 9 + 8];
+            if (is_surface(eb) && fabs(eb - (eS - sp->bias)) <= OR_TIE_DEPTH * (eS > 1.0 ? eS : 1.0)) {
+              double full = smoothstep01(sp->radius / fabs(eP - eb));
+              if (0.0 < olo) olo = 0.0;
+              if (full > ohi) ohi = full;
+            }
+          }
+        }
+    }
+    sum += occ;
+    sum_lo += olo;
+    sum_hi += ohi;
+  }
+  *ao = 1.0 - sum / sp->K;
+  *lo = 1.0 - sum_hi / sp->K;
+  *hi = 1.0 - sum_lo / sp->K;
+  if (frame_tie) {
+    *lo = 0.0;
+    *hi = 1.0;
+  }
+}
+
+typedef struct {
+  const double* gb;
+  const or_camera* cam;
+  const or_ssao_params* sp;
+  int mode, Wa, Ha;
+  const int* texels;
+  double *ao, *lo, *hi;
+} ssao_ctx;
+
+static void ssao_body(void* p, long i0, long i1) {
+  ssao_ctx* c = (ssao_ctx*)p;
+  const or_ssao_params* sp = c->sp;
+  for (long t = i0; t < i1; ++t) {
+    long idx = c->texels ? c->texels[t] : t;
+    int i = (int)(idx % c->Wa), j = (int)(idx / c->Wa);
+    if (c->mode == 0 || sp->blur_radius == 0) {
+      ssao_raw_texel(c->gb, c->cam, sp, i, j, &c->ao[t], &c->lo[t], &c->hi[t]);
+      continue;
+    }
+    /* Bilateral blur of the raw AO: Gaussian in AO texels times exp(-|e_q - e_p| / (sz e_p)). */
+    double ep = c->gb[(((long)sp->scale * j) * c->cam->W + (long)sp->scale * i) * 9 + 8];
+    if (!is_surface(ep)) {
+      c->ao[t] = c->lo[t] = c->hi[t] = 1.0;
+      continue;
+    }
+    double num = 0.0, nlo = 0.0, nhi = 0.0, den = 0.0;
+    for (int dy = -sp->blur_radius; dy <= sp->blur_radius; ++dy)
+      for (int dx = -sp->blur_radius; dx <= sp->blur_radius; ++dx) {
+        int qi = i + dx, qj = j + dy;
+        if (qi < 0 || qj < 0 || qi >= c->Wa || qj >= c->Ha) continue;
+        double eq = c->gb[(((long)sp->scale * qj) * c->cam->W + (long)sp->scale * qi) * 9 + 8];
+        if (!is_surface(eq)) continue;
+        double w = exp(-(dx * dx + dy * dy) / (2.0 * sp->sigma_s * sp->sigma_s)) *
+                   exp(-fabs(eq - ep) / (sp->sigma_z * ep));
+        double a, l, h;
+        ssao_raw_texel(c->gb, c->cam, sp, qi, qj, &a, &l, &h);
+        num += w * a;
+        nlo += w * l;
+        nhi += w * h;
+        den += w;
+      }
+    c->ao[t] = num / den;
+    c->lo[t] = nlo / den;
+    c->hi[t] = nhi / den;
+  }
+}
+
+/* mode 0: raw AO, mode 1: blurred AO.  texels: indices j*Wa+i of the AO image (NULL = all).
+ * ao/lo/hi: n doubles each. */
+int or_ssao(const double* gb, const or_camera* cam, const or_ssao_params* sp, int mode,
+            const int* texels, long n, double* ao, double* lo, double* hi, int threads) {
+  if (!gb || !cam || !sp || sp->K < 1 || (sp->scale != 1 && sp->scale != 2)) return 1;
+  int Wa = (cam->W + sp->scale - 1) / sp->scale, Ha = (cam->H + sp->scale - 1) / sp->scale;
+  ssao_ctx c = {gb, cam, sp, mode, Wa, Ha, texels, ao, lo, hi};
+  long cnt = texels ? n : (long)Wa * Ha;
+  or_parallel_for(cnt, threads, ssao_body, &c);
+  return 0;
+}
+
+/* ------------------------------------------------------------------------------------------ */
+/* A7-A10: compose (direct lights + split-sum IBL + background)                                 */
+/* ------------------------------------------------------------------------------------------ */
+#define OR_MAX_LEVELS 16
+typedef struct {
+  const double* irr; /* Hi*Wi*4 */
+  int Wi, Hi;
+  int M;
+  const double* level[OR_MAX_LEVELS]; /* each Hl*Wl*4 */
+  int Wl[OR_MAX_LEVELS], Hl[OR_MAX_LEVELS];
+  const double* lut; /* S*S*2 */
+  int S;
+} or_ibl;
+
+enum { OR_DIRECT = 1, OR_IBL = 2, OR_MULTI = 4, OR_DIFFUSE_ONLY = 8 };
+
+static void lut_bilinear(const or_ibl* ib, double mu, double r, double* A, double* B) {
+  int S = ib->S;
+  double x = mu * S - 0.5, y = r * S - 0.5;
+  double x0 = floor(x), y0 = floor(y), fx = x - x0, fy = y - y0;
+  long i0 = (long)clampd(x0, 0, S - 1), i1 = (long)clampd(x0 + 1, 0, S - 1);
+  long j0 = (long)clampd(y0, 0, S - 1), j1 = (long)clampd(y0 + 1, 0, S - 1);
+  for (int c = 0; c < 2; ++c) {
+    double a = ib->lut[(j0 * S + i0) * 2 + c], b = ib->lut[(j0 * S + i1) * 2 + c];
+    double p = ib->lut[(j1 * S + i0) * 2 + c], q = ib->lut[(j1 * S + i1) * 2 + c];
+    double v = (1 - fy) * ((1 - fx) * a + fx * b) + fy * ((1 - fx) * p + fx * q);
+    if (c == 0) *A = v; else *B = v;
+  }
+}
+
+typedef struct {
+  const double* gb;
+  const or_camera* cam;
+  const double* lights; /* N*7: pos xyz, intensity, color rgb */
+  int NL;
+  const or_ibl* ibl;
+  const double* ao;
+  int Wa, Ha, ao_scale;
+  int flags;
+  const long* pixels;
+  double* out;
+} shade_ctx;
+
+static void shade_pixel(const shade_ctx* c, long pix, double* out) {
+  const or_camera* cam = c->cam;
+  int x = (int)(pix % cam->W), y = (int)(pix / cam->W);
+  const double* g = c->gb + pix * 9;
+  double r[3], dw[3], eye[3] = {cam->v2w[12], cam->v2w[13], cam->v2w[14]};
+  view_ray(cam, x + 0.5, y + 0.5, r);
+  rot_apply(cam, r, dw);
+  double e = g[8];
+  out[0] = out[1] = out[2] = 0.0;
+  if (!is_surface(e)) {
+    /* A9: background shows the environment along the view ray. */
+    if ((c->flags & OR_IBL) && c->ibl) equirect_lookup(c->ibl->level[0], c->ibl->Wl[0], c->ibl->Hl[0], dw, out);
+    return;
+  }
+  double P[3], v[3], n[3] = {g[4], g[5], g[6]};
+  for (int q = 0; q < 3; ++q) P[q] = eye[q] + e * dw[q];
+  for (int q = 0; q < 3; ++q) v[q] = eye[q] - P[q];
+  normalize3(v);
+  normalize3(n);
+  double albedo[3] = {g[0], g[1], g[2]};
+  double metal = clampd(g[3], 0.0, 1.0), rough = clampd(g[7], OR_ROUGH_MIN, 1.0);
+  double nv_raw = dot3(n, v), nv = nv_raw > OR_NV_MIN ? nv_raw : OR_NV_MIN;
+  int diffuse_only = (c->flags & OR_DIFFUSE_ONLY) != 0;
+  double F0[3], cdiff[3];
+  for (int q = 0; q < 3; ++q) {
+    F0[q] = 0.04 * (1.0 - metal) + albedo[q] * metal;
+    cdiff[q] = albedo[q] * (1.0 - metal);
+  }
+  /* A7: direct lighting, Eq. 1 restricted to point lights. */
+  if (c->flags & OR_DIRECT) {
+    double alpha = rough * rough, k = (rough + 1.0) * (rough + 1.0) / 8.0;
+    for (int i = 0; i < c->NL; ++i) {
+      const double* Lt = c->lights + i * 7;
+      double lv[3] = {Lt[0] - P[0], Lt[1] - P[1], Lt[2] - P[2]};
+      double d2 = dot3(lv, lv);
+      double l[3] = {lv[0], lv[1], lv[2]};
+      normalize3(l);
+      double nl = dot3(n, l);
+      if (!(nl > 0.0)) continue;
+      double rad[3] = {Lt[3] * Lt[4] / d2, Lt[3] * Lt[5] / d2, Lt[3] * Lt[6] / d2};
+      if (diffuse_only) {
+        for (int q = 0; q < 3; ++q) out[q] += albedo[q] / OR_PI * rad[q] * nl;
+        continue;
+      }
+      double h[3] = {l[0] + v[0], l[1] + v[1], l[2] + v[2]};
+      normalize3(h);
+      double nh = dot3(n, h), vh = dot3(v, h);
+      double D = ggx_D(nh, alpha);
+      double G = smith_schlick_G1(nl, k) * smith_schlick_G1(nv, k);
+      double fc = pow(1.0 - vh, 5.0);
+      for (int q = 0; q < 3; ++q) {
+        double F = F0[q] + (1.0 - F0[q]) * fc;
+        double spec = D * G * F / (4.0 * nl * nv);
+        double diff = (1.0 - F) * cdiff[q] / OR_PI;
+        out[q] += (diff + spec) * rad[q] * nl;
+      }
+    }
+  }
+  /* A8: split-sum ambient term, optionally with multiple scattering. */
+  if ((c->flags & OR_IBL) && c->ibl) {
+    const or_ibl* ib = c->ibl;
+    double aoval = 1.0;
+    if (c->ao) {
+      long ai = x / c->ao_scale, aj = y / c->ao_scale;
+      aoval = c->ao[aj * c->Wa + ai];
+    }
+    double irr[3];
+    equirect_lookup(ib->irr, ib->Wi, ib->Hi, n, irr);
+    if (diffuse_only) {
+      for (int q = 0; q < 3; ++q) out[q] += albedo[q] * irr[q] * aoval;
+      return;
+    }
+    double R[3];
+    for (int q = 0; q < 3; ++q) R[q] = 2.0 * nv_raw * n[q] - v[q];
+    double pref[3];
+    double lod = rough * (ib->M - 1);
+    int l0 = (int)floor(lod);
+    if (l0 > ib->M - 1) l0 = ib->M - 1;
+    int l1 = l0 + 1 < ib->M ? l0 + 1 : ib->M - 1;
+    double tl = lod - l0, p0[3], p1[3];
+    equirect_lookup(ib->level[l0], ib->Wl[l0], ib->Hl[l0], R, p0);
+    equirect_lookup(ib->level[l1], ib->Wl[l1], ib->Hl[l1], R, p1);
+    for (int q = 0; q < 3; ++q) pref[q] = (1.0 - tl) * p0[q] + tl * p1[q];
+    double A, B;
+    lut_bilinear(ib, clampd(nv, 0.0, 1.0), rough, &A, &B);
+    double fcv = pow(1.0 - nv, 5.0);
+    for (int q = 0; q < 3; ++q) {
+      double Fr = (1.0 - rough > F0[q] ? 1.0 - rough : F0[q]) - F0[q];
+      double kS = F0[q] + Fr * fcv;
+      double La;
+      if (c->flags & OR_MULTI) {
+        /* Fdez-Aguera 2019: single-scatter energy plus a geometric series of bounces. */
+        double FssEss = kS * A + B;
+        double Ess = A + B, Ems = 1.0 - Ess;
+        double Favg = F0[q] + (1.0 - F0[q]) / 21.0;
+        double Fms = FssEss * Favg / (1.0 - Ems * Favg);
+        double kD = cdiff[q] * (1.0 - FssEss - Fms * Ems);
+        La = FssEss * pref[q] + (Fms * Ems + kD) * irr[q];
+      } else {
+        La = (1.0 - kS) * cdiff[q] * irr[q] + (kS * A + B) * pref[q];
+      }
+      out[q] += La * aoval;
+    }
+  }
+}
+
+static void shade_body(void* p, long i0, long i1) {
+  shade_ctx* c = (shade_ctx*)p;
+  for (long t = i0; t < i1; ++t) {
+    long pix = c->pixels ? c->pixels[t] : t;
+    shade_pixel(c, pix, c->out + t * 3);
+  }
+}
+
+/* gb: W*H*9 decoded G-buffer; lights: NL*7; ao: Ha*Wa doubles or NULL; pixels: flat indices
+ * y*W+x (NULL = all).  out: n*3 doubles of linear HDR radiance. */
+int or_shade(const double* gb, const or_camera* cam, const double* lights, int NL,
+             const or_ibl* ibl, const double* ao, int ao_scale, int flags, const long* pixels,
+             long n, double* out, int threads) {
+  if (!gb || !cam || !out || (NL > 0 && !lights)) return 1;
+  if ((flags & OR_IBL) && !ibl) return 1;
+  int s = ao_scale > 0 ? ao_scale : 1;
+  shade_ctx c = {gb, cam, lights, NL, ibl, ao, (cam->W + s - 1) / s, (cam->H + s - 1) / s, s,
+                 flags, pixels, out};
+  long cnt = pixels ? n : (long)cam->W * cam->H;
+  or_parallel_for(cnt, threads, shade_body, &c);
+  return 0;
+}
+
+/* ------------------------------------------------------------------------------------------ */
+/* A11: tone mapping and sRGB encoding (Sec. 5.4)                                               */
+/* ------------------------------------------------------------------------------------------ */
+static double aces_fit(double x) { return x * (2.51 * x + 0.03) / (x * (2.43 * x + 0.59) + 0.14); }
+static double srgb_encode(double y) { return y <= 0.0031308 ? 12.92 * y : 1.055 * pow(y, 1.0 / 2.4) - 0.055; }
+
+/* hdr: n*3 linear values; out: n*4 bytes (alpha 255); scaled: n*3 values 255*sRGB before
+ * rounding (NULL allowed). */
+int or_tonemap(const double* hdr, long n, double exposure, int op, uint8_t* out, double* scaled) {
+  for (long p = 0; p < n; ++p) {
+    for (int c = 0; c < 3; ++c) {
+      double x = exposure * hdr[p * 3 + c];
+      x = x > 0.0 ? x : 0.0;
+      double y = (op == 1) ? x / (1.0 + x) : aces_fit(x);
+      y = clampd(y, 0.0, 1.0);
+      double s = 255.0 * srgb_encode(y);
+      if (scaled) scaled[p * 3 + c] = s;
+      out[p * 4 + c] = (uint8_t)floor(s + 0.5);
+    }
+    out[p * 4 + 3] = 255;
+  }
+  return 0;
+}
+
+/* Helpers exposed for tests: the equirect mapping and the sample set. */
+void or_dir_to_uv(const double* d, double* uv) { dir_to_uv(d, &uv[0], &uv[1]); }
+void or_uv_to_dir(double u, double v, double* d) { uv_to_dir(u, v, d); }
+double or_radical_inverse2(uint32_t i) { return radical_inverse2(i); }
+void or_ggx_half_vector(double xi1, double xi2, double alpha, const double* n, double* h) {
+  ggx_half_vector(xi1, xi2, alpha, n, h);
+}
+void or_equirect_lookup(const double* map, int W, int H, const double* d, double* out) {
+  equirect_lookup(map, W, H, d, out);
+}

@@ -1,0 +1,375 @@
+"""Seeded synthetic inputs shared by the oracle and the CUDA path.
+
+This module produces *inputs only*: scenes (spheres on a ground plane, materials, point lights,
+a pinhole camera), their ray-cast G-buffers in the FP32 and compact layouts of the paper's
+Table 1, analytic HDR environment maps, SSAO sample kernels and rotation noise, and synthetic
+AO / HDR fields for unit tests.  It contains none of the shading method's arithmetic (no BRDF,
+no IBL, no SSAO, no tone mapping) and imports neither `oracle` nor the CUDA package.
+
+Everything is computed in float64 with numpy and rounded once to the stored type, from a
+PCG32 generator (O'Neill 2014, the XSH-RR 64/32 variant) implemented here, so the same seed
+gives the same bytes on every machine.
+
+The scene recipe stands in for the paper's meshes (Sec. 7 uses a 23 M-face statue and a
+scanned head, neither available): S spheres of radius U[0.2, 1] resting on the plane y = 0 with
+centres x, z ~ U[-F, F], F = 5 sqrt(S / 16); albedo U[0,1]^3, metalness 0 or 1 with p = 0.5,
+roughness U[0.05, 1]; lights in [-F, F] x [3, 3 + 2F] x [-F, F] with intensity U[1, 50], white;
+camera at (0, 0.6 F, 1.6 F) looking at the origin with a 60 degree vertical field of view.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+
+__all__ = [
+    "PCG32", "Scene", "make_scene", "camera_matrix", "raycast_gbuffer", "encode_compact",
+    "make_env", "make_ssao_kernel", "make_ssao_noise", "make_ao_field", "make_hdr_field",
+    "GBuffer", "CONFIGS",
+]
+
+_MASK64 = (1 << 64) - 1
+
+
+class PCG32:
+    """PCG-XSH-RR 64/32 (O'Neill 2014): 64-bit LCG state, 32-bit permuted output."""
+
+    MULT = 6364136223846793005
+
+    def __init__(self, seed: int, stream: int = 54):
+        self.state = 0
+        self.inc = ((stream << 1) | 1) & _MASK64
+        self.next_u32()
+        self.state = (self.state + (seed & _MASK64)) & _MASK64
+        self.next_u32()
+
+    def next_u32(self) -> int:
+        old = self.state
+        self.state = (old * self.MULT + self.inc) & _MASK64
+        xorshifted = (((old >> 18) ^ old) >> 27) & 0xFFFFFFFF
+        rot = old >> 59
+        return ((xorshifted >> rot) | (xorshifted << ((-rot) & 31))) & 0xFFFFFFFF
+
+    def uniform(self, lo: float = 0.0, hi: float = 1.0) -> float:
+        """Uniform in [lo, hi) from 53 random bits."""
+        hi_bits = self.next_u32() >> 5
+        lo_bits = self.next_u32() >> 6
+        u = (hi_bits * 67108864.0 + lo_bits) / 9007199254740992.0
+        return lo + (hi - lo) * u
+
+    def uniforms(self, n: int, lo: float = 0.0, hi: float = 1.0) -> np.ndarray:
+        return np.array([self.uniform(lo, hi) for _ in range(n)], dtype=np.float64)
+
+
+@dataclass
+class Scene:
+    """Analytic scene: spheres on a finite ground square plus point lights and a camera."""
+
+    width: int
+    height: int
+    F: float
+    centers: np.ndarray      # (S, 3) float64
+    radii: np.ndarray        # (S,)
+    albedo: np.ndarray       # (S + 1, 3): spheres then the ground plane
+    metal: np.ndarray        # (S + 1,)
+    rough: np.ndarray        # (S + 1,)
+    lights: np.ndarray       # (N_L, 8) float32: pos.xyz, intensity, color.rgb, pad
+    view_to_world: np.ndarray  # (4, 4) float64, columns right, up, back, eye
+    fov_y: float
+    ground_half: float = field(default=0.0)
+
+    def camera_array(self) -> np.ndarray:
+        """Column-major float32[16] view_to_world, as the C ABI takes it."""
+        return np.asarray(self.view_to_world, dtype=np.float32).T.reshape(-1).copy()
+
+
+def camera_matrix(eye, target, up=(0.0, 1.0, 0.0)) -> np.ndarray:
+    eye = np.asarray(eye, np.float64)
+    fwd = np.asarray(target, np.float64) - eye
+    fwd /= np.linalg.norm(fwd)
+    right = np.cross(fwd, np.asarray(up, np.float64))
+    right /= np.linalg.norm(right)
+    upv = np.cross(right, fwd)
+    m = np.eye(4)
+    m[:3, 0] = right
+    m[:3, 1] = upv
+    m[:3, 2] = -fwd
+    m[:3, 3] = eye
+    return m
+
+
+def make_scene(seed: int, width: int, height: int, n_spheres: int, n_lights: int,
+               fov_deg: float = 60.0) -> Scene:
+    rng = PCG32(seed)
+    S = n_spheres
+    F = 5.0 * math.sqrt(max(S, 1) / 16.0)
+    centers = np.zeros((S, 3))
+    radii = np.zeros(S)
+    for s in range(S):
+        r = rng.uniform(0.2, 1.0)
+        x = rng.uniform(-F, F)
+        z = rng.uniform(-F, F)
+        centers[s] = (x, r, z)
+        radii[s] = r
+    nm = S + 1
+    albedo = np.zeros((nm, 3))
+    metal = np.zeros(nm)
+    rough = np.zeros(nm)
+    for i in range(nm):
+        albedo[i] = rng.uniforms(3)
+        metal[i] = 1.0 if rng.uniform() < 0.5 else 0.0
+        rough[i] = rng.uniform(0.05, 1.0)
+    lights = np.zeros((n_lights, 8), np.float32)
+    for i in range(n_lights):
+        lights[i, 0] = rng.uniform(-F, F)
+        lights[i, 1] = rng.uniform(3.0, 3.0 + 2.0 * F)
+        lights[i, 2] = rng.uniform(-F, F)
+        lights[i, 3] = rng.uniform(1.0, 50.0)
+        lights[i, 4:7] = 1.0
+    v2w = camera_matrix((0.0, 0.6 * F, 1.6 * F), (0.0, 0.0, 0.0))
+    return Scene(width, height, F, centers, radii, albedo, metal, rough, lights, v2w,
+                 math.radians(fov_deg), ground_half=8.0 * F)
+
+
+def _pixel_rays(width: int, height: int, fov_y: float, y0: int = 0, y1: int | None = None):
+    """View-space ray (px, py, -1) of every pixel centre in rows [y0, y1)."""
+    y1 = height if y1 is None else y1
+    t = math.tan(0.5 * fov_y)
+    aspect = width / height
+    xs = (2.0 * (np.arange(width) + 0.5) / width - 1.0) * t * aspect
+    ys = (1.0 - 2.0 * (np.arange(y0, y1) + 0.5) / height) * t
+    px, py = np.meshgrid(xs, ys)
+    return px, py
+
+
+@dataclass
+class GBuffer:
+    """FP32 G-buffer of Table 1's content: rt0 (albedo, metal), rt1 (normal, rough), depth."""
+
+    rt0: np.ndarray  # (H, W, 4) float32
+    rt1: np.ndarray  # (H, W, 4) float32
+    depth: np.ndarray  # (H, W) float32, +inf where the ray misses
+
+
+def raycast_gbuffer(scene: Scene, width: int | None = None, height: int | None = None) -> GBuffer:
+    """Ray-cast the analytic scene through every pixel centre (float64, stored float32).
+
+    Eye depth e is the hit parameter along the view ray (px, py, -1), i.e. -z of the view-space
+    hit point.  Spheres are culled per pixel by their projected bounding box.
+    """
+    W = scene.width if width is None else width
+    H = scene.height if height is None else height
+    px, py = _pixel_rays(W, H, scene.fov_y)
+    R = scene.view_to_world[:3, :3]
+    eye = scene.view_to_world[:3, 3]
+    dx = R[0, 0] * px + R[0, 1] * py - R[0, 2]
+    dy = R[1, 0] * px + R[1, 1] * py - R[1, 2]
+    dz = R[2, 0] * px + R[2, 1] * py - R[2, 2]
+    best = np.full((H, W), np.inf)
+    mat = np.full((H, W), -1, np.int64)
+    nrm = np.zeros((H, W, 3))
+    # Ground square y = 0, |x|, |z| <= ground_half.
+    with np.errstate(divide="ignore", invalid="ignore"):
+        tp = np.where(dy < 0.0, -eye[1] / dy, np.inf)
+    hx = eye[0] + tp * dx
+    hz = eye[2] + tp * dz
+    gh = scene.ground_half
+    hit = np.isfinite(tp) & (tp > 0) & (np.abs(hx) <= gh) & (np.abs(hz) <= gh)
+    best = np.where(hit, tp, best)
+    mat = np.where(hit, len(scene.radii), mat)
+    nrm[hit] = (0.0, 1.0, 0.0)
+    tanh = math.tan(0.5 * scene.fov_y)
+    f_px = 0.5 * H / tanh
+    w2v = np.linalg.inv(scene.view_to_world)
+    for s in range(len(scene.radii)):
+        c = scene.centers[s]
+        r = scene.radii[s]
+        cv = w2v[:3, :3] @ c + w2v[:3, 3]
+        zc = -cv[2]
+        if zc - r > 1e-3:
+            # The sphere lies inside its view-space bounding cube, whose projection is the
+            # hull of the 8 projected corners: a conservative pixel rectangle.
+            cx = np.array([cv[0] - r, cv[0] + r])[:, None, None]
+            cy = np.array([cv[1] - r, cv[1] + r])[None, :, None]
+            cz = np.array([zc - r, zc + r])[None, None, :]
+            xs = (cx / cz) * f_px + 0.5 * W
+            ys = (-cy / cz) * f_px + 0.5 * H
+            xa = int(max(0, math.floor(xs.min()) - 1))
+            xb = int(min(W, math.ceil(xs.max()) + 2))
+            ya = int(max(0, math.floor(ys.min()) - 1))
+            yb = int(min(H, math.ceil(ys.max()) + 2))
+            if xa >= xb or ya >= yb:
+                continue
+        elif zc + r < 0:
+            continue
+        else:
+            xa, xb, ya, yb = 0, W, 0, H
+        sdx, sdy, sdz = dx[ya:yb, xa:xb], dy[ya:yb, xa:xb], dz[ya:yb, xa:xb]
+        ox, oy, oz = eye - c
+        a = sdx * sdx + sdy * sdy + sdz * sdz
+        b = sdx * ox + sdy * oy + sdz * oz
+        cc = ox * ox + oy * oy + oz * oz - r * r
+        disc = b * b - a * cc
+        ok = disc >= 0.0
+        sq = np.sqrt(np.where(ok, disc, 0.0))
+        t = (-b - sq) / a
+        sub = best[ya:yb, xa:xb]
+        take = ok & (t > 1e-6) & (t < sub)
+        if not take.any():
+            continue
+        sub[take] = t[take]
+        mat[ya:yb, xa:xb][take] = s
+        hxs = eye[0] + t * sdx - c[0]
+        hys = eye[1] + t * sdy - c[1]
+        hzs = eye[2] + t * sdz - c[2]
+        n3 = np.stack([hxs, hys, hzs], -1) / r
+        n3 /= np.linalg.norm(n3, axis=-1, keepdims=True)
+        nrm[ya:yb, xa:xb][take] = n3[take]
+    rt0 = np.zeros((H, W, 4), np.float32)
+    rt1 = np.zeros((H, W, 4), np.float32)
+    lit = mat >= 0
+    m = mat[lit]
+    rt0[lit, :3] = scene.albedo[m]
+    rt0[lit, 3] = scene.metal[m]
+    n32 = nrm[lit]
+    rt1[lit, :3] = n32
+    rt1[lit, 3] = scene.rough[m]
+    depth = best.astype(np.float32)
+    depth[~lit] = np.inf
+    return GBuffer(rt0, rt1, depth)
+
+
+def _srgb_encode8(x: np.ndarray) -> np.ndarray:
+    """Linear [0,1] -> sRGB 8-bit code (IEC 61966-2-1 transfer, round to nearest)."""
+    x = np.clip(x, 0.0, 1.0)
+    y = np.where(x <= 0.0031308, 12.92 * x, 1.055 * np.power(x, 1.0 / 2.4) - 0.055)
+    return np.floor(255.0 * y + 0.5).astype(np.uint8)
+
+
+def _oct_encode(n: np.ndarray) -> np.ndarray:
+    """Octahedral projection of unit vectors (Cigolle et al. 2014), z-up octahedron."""
+    s = np.abs(n[..., 0]) + np.abs(n[..., 1]) + np.abs(n[..., 2])
+    s = np.where(s == 0.0, 1.0, s)
+    p = n[..., :2] / s[..., None]
+    neg = n[..., 2] < 0.0
+    sgn = np.where(p >= 0.0, 1.0, -1.0)
+    folded = (1.0 - np.abs(p[..., ::-1])) * sgn
+    return np.where(neg[..., None], folded, p)
+
+
+@dataclass
+class CompactGBuffer:
+    rt0: np.ndarray  # (H, W, 4) uint8: sRGB albedo, weight
+    rt1: np.ndarray  # (H, W, 2) float16: octahedral normal
+    rt2: np.ndarray  # (H, W, 2) uint8: metal, rough
+    depth: np.ndarray  # (H, W) float32
+
+
+def encode_compact(g: GBuffer) -> CompactGBuffer:
+    """Compact layout (Table 1 widths, FP16 octahedral normals): 14 bytes per pixel."""
+    H, W = g.depth.shape
+    rt0 = np.zeros((H, W, 4), np.uint8)
+    rt0[..., :3] = _srgb_encode8(g.rt0[..., :3].astype(np.float64))
+    rt0[..., 3] = 255
+    oct_ = _oct_encode(g.rt1[..., :3].astype(np.float64))
+    rt1 = oct_.astype(np.float16)  # round to nearest even
+    rt2 = np.zeros((H, W, 2), np.uint8)
+    rt2[..., 0] = np.floor(255.0 * np.clip(g.rt0[..., 3].astype(np.float64), 0, 1) + 0.5)
+    rt2[..., 1] = np.floor(255.0 * np.clip(g.rt1[..., 3].astype(np.float64), 0, 1) + 0.5)
+    return CompactGBuffer(rt0, rt1, rt2, g.depth.copy())
+
+
+def _texel_dirs(W: int, H: int):
+    """World direction of every equirect texel centre (inverse of the u, v convention)."""
+    u = (np.arange(W) + 0.5) / W
+    v = (np.arange(H) + 0.5) / H
+    uu, vv = np.meshgrid(u, v)
+    phi = 2.0 * math.pi * (uu - 0.5)
+    theta = math.pi * vv
+    return np.stack([np.sin(theta) * np.sin(phi), np.cos(theta), -np.sin(theta) * np.cos(phi)], -1)
+
+
+def make_env(seed: int, width: int, height: int, n_suns: int = 2, peak: float = 100.0,
+             uniform: tuple | None = None) -> np.ndarray:
+    """Analytic sky: gradient from ground colour to sky blue plus Gaussian sun lobes
+    peak * exp(-theta^2 / (2 sigma^2)), sigma ~ U[2, 6] degrees, elevation ~ U[10, 70] degrees.
+    Returns float32 (H, W, 4) with alpha 1.  `uniform=(r, g, b)` gives a constant map."""
+    if uniform is not None:
+        env = np.empty((height, width, 4), np.float32)
+        env[..., :3] = np.asarray(uniform, np.float32)
+        env[..., 3] = 1.0
+        return env
+    rng = PCG32(seed, stream=7)
+    d = _texel_dirs(width, height)
+    t = 0.5 * (d[..., 1:2] + 1.0)
+    lo = np.array([0.3, 0.25, 0.2])
+    hi = np.array([0.25, 0.45, 0.9])
+    col = lo + (hi - lo) * t
+    for _ in range(n_suns):
+        el = math.radians(rng.uniform(10.0, 70.0))
+        az = rng.uniform(0.0, 2.0 * math.pi)
+        sig = math.radians(rng.uniform(2.0, 6.0))
+        sd = np.array([math.cos(el) * math.sin(az), math.sin(el), -math.cos(el) * math.cos(az)])
+        ct = np.clip(d @ sd, -1.0, 1.0)
+        th = np.arccos(ct)
+        col = col + peak * np.exp(-th * th / (2.0 * sig * sig))[..., None]
+    env = np.empty((height, width, 4), np.float32)
+    env[..., :3] = col
+    env[..., 3] = 1.0
+    return env
+
+
+def make_ssao_kernel(seed: int, K: int) -> np.ndarray:
+    """Hemisphere sample offsets: normalize(U(-1,1), U(-1,1), U(0.05,1)) * U(0,1) * lerp(0.1, 1,
+    (s/K)^2).  float32 (K, 4), w = 0."""
+    rng = PCG32(seed, stream=11)
+    k = np.zeros((K, 4), np.float32)
+    for s in range(K):
+        v = np.array([rng.uniform(-1, 1), rng.uniform(-1, 1), rng.uniform(0.05, 1.0)])
+        v /= np.linalg.norm(v)
+        sc = (s / K) ** 2
+        v *= rng.uniform() * (0.1 + 0.9 * sc)
+        k[s, :3] = v
+    return k
+
+
+def make_ssao_noise(seed: int) -> np.ndarray:
+    """4x4 unit rotation vectors (cos phi, sin phi), phi ~ U[0, 2 pi).  float32 (16, 2)."""
+    rng = PCG32(seed, stream=13)
+    n = np.zeros((16, 2), np.float32)
+    for i in range(16):
+        phi = rng.uniform(0.0, 2.0 * math.pi)
+        n[i] = (math.cos(phi), math.sin(phi))
+    return n
+
+
+def make_ao_field(seed: int, width: int, height: int) -> np.ndarray:
+    """Synthetic AO image U[0.3, 1] (input for compose tests)."""
+    g = np.random.Generator(np.random.PCG64(seed))
+    return (0.3 + 0.7 * g.random((height, width))).astype(np.float32)
+
+
+def make_hdr_field(seed: int, width: int, height: int) -> np.ndarray:
+    """Synthetic HDR RGBA32F image, log-uniform over [1e-4, 1e3] with exact 0 and 1 entries."""
+    g = np.random.Generator(np.random.PCG64(seed))
+    x = np.exp(g.uniform(math.log(1e-4), math.log(1e3), (height, width, 4)))
+    x[..., 3] = 1.0
+    flat = x.reshape(-1, 4)
+    flat[::97, :3] = 0.0
+    flat[1::89, :3] = 1.0
+    return x.astype(np.float32)
+
+
+# Workload shapes (seeds are 1000 * config + view).
+CONFIGS = {
+    "small": dict(width=256, height=256, spheres=16, lights=4, env=(128, 64), levels=6,
+                  prefilter_samples=256, lut=32, lut_samples=256, irr=(32, 16), ssao_k=16,
+                  radius=0.5, blur=3, seed=0),
+    "full": dict(width=1920, height=1080, spheres=200, lights=64, env=(2048, 1024), levels=8,
+                 prefilter_samples=1024, lut=64, lut_samples=1024, irr=(32, 16), ssao_k=32,
+                 radius=0.5, blur=3, seed=1000),
+    "uhd_compact": dict(width=3840, height=2160, spheres=200, lights=64, env=(2048, 1024),
+                        levels=8, prefilter_samples=1024, lut=64, lut_samples=1024,
+                        irr=(32, 16), ssao_k=32, radius=0.5, blur=3, seed=3000),
+}
