@@ -1,0 +1,449 @@
+"""Benchmark of the deferred PBR shading pass on GB300.
+
+One step renders one synthetic 1920x1080 frame (200 spheres on a ground plane, 64 point lights,
+2048x1024 HDR environment with an 8-level GGX chain of 1024 samples per texel and a 64x64 BRDF
+table, SSAO with 32 samples at half resolution plus a 7x7 bilateral blur, ACES + sRGB):
+    epbr_ssao_raw -> epbr_ssao_blur -> epbr_shade_tonemap (HDR RGBA32F + RGBA8)
+The lighting set is precomputed once per environment (as the paper does on load) and stays
+resident; its cost is reported separately as precompute_ms.
+
+Prints one JSON line.  --impl reference times the FP64 CPU oracle on host cores instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+WORKLOAD = "full"
+METRIC = "shaded Mpixels/s"
+L2_FLUSH_BYTES = 256 << 20  # larger than the 129 MB L2
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="epbr", choices=["epbr", "reference"])
+    ap.add_argument("--workload", default=WORKLOAD, choices=sorted(synth.CONFIGS))
+    ap.add_argument("--cpu-seconds", type=float, default=12.0, help="CPU-baseline time budget")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("LOCAL_RANK", 0)), int(os.environ.get("WORLD_SIZE", 1))
+
+
+def workload_inputs(name: str):
+    c = synth.CONFIGS[name]
+    sc = synth.make_scene(c["seed"], c["width"], c["height"], c["spheres"], c["lights"])
+    g = synth.raycast_gbuffer(sc)
+    env = synth.make_env(synth.CONFIGS["full"]["seed"] if name == "uhd_compact" else c["seed"], *c["env"])
+    k = synth.make_ssao_kernel(c["seed"], c["ssao_k"])
+    nz = synth.make_ssao_noise(c["seed"])
+    return c, sc, g, env, k, nz
+
+
+def config_dict(c, name, extra=None):
+    d = {"workload": f"{name}: {c['width']}x{c['height']}, {c['spheres']} spheres + plane, {c['lights']} lights, "
+                     f"env {c['env'][0]}x{c['env'][1]} (M={c['levels']}, N_s={c['prefilter_samples']}, "
+                     f"LUT {c['lut']}^2), SSAO {c['ssao_k']} + {2 * c['blur'] + 1}x{2 * c['blur'] + 1} blur",
+         "pixels_per_view": c["width"] * c["height"],
+         "gbuffer": "compact 14 B/px" if name == "uhd_compact" else "fp32 36 B/px",
+         "hdr": "RGBA16F" if name == "uhd_compact" else "RGBA32F",
+         "step": "ssao_raw + ssao_blur + shade_tonemap per frame; lighting set precomputed once",
+         "l2": "flushed between timed steps (256 MB write)",
+         "parallelism": "independent views per GPU (no collective)"}
+    if extra:
+        d.update(extra)
+    return d
+
+
+# ------------------------------------------------------------------------------------------
+# algorithmic work of the compose kernel (per-unit figures)
+# ------------------------------------------------------------------------------------------
+FLOP_LIGHT_TEST = 20     # L = p - P, |L|^2, n.l test
+FLOP_LIGHT_LIT = 70      # the rest of Eq. 1 for a light with n.l > 0
+FLOP_IBL = 250           # split-sum ambient term with multiple scattering
+FLOP_BACKGROUND = 40     # environment lookup of a background pixel
+
+
+def compose_flops(sc, g, n_lights) -> tuple[float, dict]:
+    """Algorithmic FP32 FLOPs of one compose launch: per surface pixel, 20 per light for the
+    visibility test, 70 more per light with n.l > 0, 250 for IBL; 40 per background pixel."""
+    depth = g.depth
+    surf = np.isfinite(depth)
+    H, W = depth.shape
+    t = math.tan(0.5 * sc.fov_y)
+    xs = (2.0 * (np.arange(W) + 0.5) / W - 1.0) * t * W / H
+    ys = (1.0 - 2.0 * (np.arange(H) + 0.5) / H) * t
+    R, eye = sc.view_to_world[:3, :3], sc.view_to_world[:3, 3]
+    lit = 0
+    rows = 64
+    for y0 in range(0, H, rows):
+        ys_ = ys[y0:y0 + rows]
+        px, py = np.meshgrid(xs, ys_)
+        m = surf[y0:y0 + rows]
+        e = depth[y0:y0 + rows][m].astype(np.float64)
+        r = np.stack([px[m], py[m], -np.ones_like(e)], -1)
+        P = eye + e[:, None] * (r @ R.T)
+        n = g.rt1[y0:y0 + rows][m][:, :3].astype(np.float64)
+        for L in sc.lights[:n_lights]:
+            lit += int(np.count_nonzero(np.einsum("ij,ij->i", L[:3] - P, n) > 0))
+    ns = int(surf.sum())
+    nb = int(surf.size - ns)
+    flops = ns * n_lights * FLOP_LIGHT_TEST + lit * FLOP_LIGHT_LIT + ns * FLOP_IBL + nb * FLOP_BACKGROUND
+    return float(flops), {"surface_px": ns, "background_px": nb, "lit_pairs": lit}
+
+
+# ------------------------------------------------------------------------------------------
+# clocks during the timed region
+# ------------------------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv") if os.path.isdir(
+            os.path.join(ROOT, "gpurun_out")) else f"/tmp/epbr_clocks_{os.getpid()}.csv"
+
+    def __enter__(self):
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                                         stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+        self.f.close()
+
+    def summary(self):
+        try:
+            lines = [l.strip() for l in open(self.path) if l.strip()]
+        except OSError:
+            return None
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in lines:
+            p = [x.strip() for x in l.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                mx.append(float(p[2]))
+            except ValueError:
+                continue
+            for nme, v in zip(names, p[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nme)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def kernel_traffic(kernel: str, src_files):
+    """DRAM bytes per launch from the committed ncu summary, or None when the kernel sources
+    changed since the counters were taken."""
+    path = os.path.join(ROOT, "profiles", f"{kernel}_traffic.json")
+    try:
+        d = json.load(open(path))
+    except (OSError, ValueError):
+        return None
+    h = hashlib.sha256()
+    for f in src_files:
+        h.update(open(os.path.join(ROOT, f), "rb").read())
+    if d.get("sources_sha256") != h.hexdigest():
+        return None
+    return d.get("dram_bytes_per_launch")
+
+
+SHADE_SOURCES = ["paper_2012_03325_gb300/csrc/shade.cu", "paper_2012_03325_gb300/csrc/epbr_internal.cuh"]
+
+
+def sources_sha(files=SHADE_SOURCES):
+    h = hashlib.sha256()
+    for f in files:
+        h.update(open(os.path.join(ROOT, f), "rb").read())
+    return h.hexdigest()
+
+
+# ------------------------------------------------------------------------------------------
+# CPU oracle baseline
+# ------------------------------------------------------------------------------------------
+def oracle_frame_rate(c, sc, g, env, k, nz, seconds: float, oracle_ibl=None, threads: int = 0):
+    """The FP64 oracle's per-frame path (blurred SSAO, compose, tone map) on horizontal bands of
+    the frame until `seconds` elapse; returns (Mpixels/s, cores, sample description)."""
+    import oracle
+    W, H = c["width"], c["height"]
+    if oracle_ibl is None:
+        # a lighting set with the workload's shapes; its values do not change the per-frame cost
+        oracle_ibl = oracle.IblSet(np.ones((c["irr"][1], c["irr"][0], 3)),
+                                   [np.ones((max(1, c["env"][1] >> m), max(1, c["env"][0] >> m), 3))
+                                    for m in range(c["levels"])], np.full((c["lut"], c["lut"], 2), 0.5))
+    if "compact" in c.get("name", ""):
+        cg = synth.encode_compact(g)
+        gb = oracle.decode_compact(cg.rt0, cg.rt1, cg.rt2, cg.depth)
+    else:
+        gb = oracle.decode_fp32(g.rt0, g.rt1, g.depth)
+    cam = oracle.camera(sc.camera_array(), sc.fov_y, W, H)
+    cores = oracle.num_threads(threads)
+    band = 16
+    px_done, t0 = 0, time.perf_counter()
+    y0 = H // 3
+    while time.perf_counter() - t0 < seconds and px_done < W * H:
+        ys = np.arange(y0, min(H, y0 + band))
+        texels = np.unique((ys // 2)[:, None] * ((W + 1) // 2) + np.arange((W + 1) // 2)[None, :]).astype(np.int32)
+        ao, _, _ = oracle.ssao(gb, cam, K=c["ssao_k"], scale=2, radius=c["radius"], bias=0.05 * c["radius"],
+                               blur_radius=c["blur"], sigma_s=2.0, sigma_z=0.1, kernel=k, noise=nz, blurred=True,
+                               texels=texels, threads=threads)
+        ao_img = np.ones(((H + 1) // 2, (W + 1) // 2))
+        ao_img.reshape(-1)[texels] = ao
+        pixels = (ys[:, None] * W + np.arange(W)[None, :]).reshape(-1)
+        hdr = oracle.shade(gb, cam, sc.lights, oracle_ibl, 7, ao=ao_img, ao_scale=2, pixels=pixels, threads=threads)
+        oracle.tonemap(hdr)
+        px_done += pixels.size
+        y0 = (y0 + band) % H
+    dt = time.perf_counter() - t0
+    return px_done / dt / 1e6, cores, f"{px_done} px in {px_done // W} full-width rows ({dt:.1f} s wall)"
+
+
+def run_reference(args):
+    rank, _, world = dist_env()
+    if rank != 0:
+        return
+    name = args.workload
+    c, sc, g, env, k, nz = workload_inputs(name)
+    c = dict(c, name=name)
+    # warm-up: a short oracle pass
+    for _ in range(args.warmup):
+        oracle_frame_rate(c, sc, g, env, k, nz, 0.2)
+    per_step = []
+    samples = []
+    for _ in range(args.steps):
+        rate, cores, sample = oracle_frame_rate(c, sc, g, env, k, nz, max(0.5, args.cpu_seconds / max(args.steps, 1)))
+        per_step.append(rate)
+        samples.append(sample)
+    value = statistics.mean(per_step)
+    ms = c["width"] * c["height"] / (value * 1e6) * 1e3
+    line = {"metric": METRIC, "value": value, "unit": "Mpixels/s", "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": config_dict(c, name, {"note": "oracle on host cores, bounded band sample per step"}),
+            "cpu_baseline": {"value": value, "unit": "Mpixels/s", "cores": cores, "kind": "oracle",
+                             "sample": samples[0]},
+            "e2e": {"value": value, "unit": "Mpixels/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "gpu_launches": 0}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------------------------------
+# GPU arm
+# ------------------------------------------------------------------------------------------
+def run_gpu(args):
+    import torch
+    import torch.distributed as dist
+
+    import paper_2012_03325_gb300 as ep
+
+    rank, local_rank, world = dist_env()
+    if world > 1:
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    name = args.workload
+    c, sc, g, env, k, nz = workload_inputs(name)
+    compact = name == "uhd_compact"
+    W, H = c["width"], c["height"]
+    stream = torch.cuda.Stream(device=dev)
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    if compact:
+        cg = synth.encode_compact(g)
+        host_rts = [cg.rt0, cg.rt1, cg.rt2, cg.depth]
+    else:
+        host_rts = [g.rt0, g.rt1, None, g.depth]
+    dev_rts = [t(a) if a is not None else None for a in host_rts]
+    gb = ep.GBuffer.compact(*dev_rts) if compact else ep.GBuffer.fp32(dev_rts[0], dev_rts[1], dev_rts[3])
+    cam = ep.camera(sc.camera_array(), sc.fov_y, W, H)
+    lights = t(sc.lights)
+    env_t = t(env)
+    params = ep.ibl_params(c["levels"], c["prefilter_samples"], c["lut"], c["lut_samples"], *c["irr"])
+    ibl = ep.Ibl(params, env.shape[1], env.shape[0], device=dev)
+    ws_ibl = torch.empty(ep.epbr_precompute_ibl_workspace_size(params, env.shape[1], env.shape[0]) + 256,
+                         dtype=torch.uint8, device=dev)
+    # precompute once (timed separately)
+    with torch.cuda.stream(stream):
+        for _ in range(2):
+            ep.epbr_precompute_ibl(env_t, ibl, ws_ibl, stream=stream)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ep.epbr_precompute_ibl(env_t, ibl, ws_ibl, stream=stream)
+        e1.record(stream)
+    stream.synchronize()
+    precompute_ms = e0.elapsed_time(e1)
+
+    sp = ep.SsaoParams(t(k), t(nz), radius=c["radius"], scale=2, blur_radius=c["blur"])
+    Ha, Wa = sp.ao_shape(W, H)
+    ao_raw = torch.empty(Ha, Wa, device=dev)
+    ao = torch.empty(Ha, Wa, device=dev)
+    hdr_fmt = ep.EPBR_HDR_RGBA16F if compact else ep.EPBR_HDR_RGBA32F
+    hdr = torch.empty(H, W, 4, dtype=torch.float16 if compact else torch.float32, device=dev)
+    ldr = torch.empty(H, W, 4, dtype=torch.uint8, device=dev)
+    shp = ep.shade_params(ep.EPBR_SHADE_ALL, ao, 2)
+    tp = ep.tonemap_params(1.0, ep.EPBR_TONEMAP_ACES)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+
+    ev_shade = []
+
+    def step(record=False):
+        ep.epbr_ssao_raw(gb, cam, sp, ao_raw, stream=stream)
+        ep.epbr_ssao_blur(gb, sp, ao_raw, ao, stream=stream)
+        if record:
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+        ep.epbr_shade_tonemap(gb, cam, lights, ibl, shp, hdr, hdr_fmt, tp, ldr, stream=stream)
+        if record:
+            b.record(stream)
+            ev_shade.append((a, b))
+
+    launches_per_step = 3
+    with torch.cuda.stream(stream):
+        for _ in range(max(3, args.warmup)):
+            step()
+            flush.zero_()
+    stream.synchronize()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    wall0 = time.perf_counter()
+    with ClockSampler(local_rank) as clk:
+        with torch.cuda.stream(stream):
+            for i in range(args.steps):
+                flush.zero_()  # L2 flush, outside the timed events
+                ev[i][0].record(stream)
+                step(record=True)
+                ev[i][1].record(stream)
+        stream.synchronize()
+        torch.cuda.synchronize()
+    wall = time.perf_counter() - wall0
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_ms = sum(step_ms)
+    shade_ms = statistics.mean(a.elapsed_time(b) for a, b in ev_shade)
+    if world > 1:
+        tt = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        total_ms = float(tt.item())
+        dist.barrier()
+
+    # end to end through the C ABI with host buffers: pinned G-buffer + lights in, RGBA8 out
+    pinned = [torch.from_numpy(np.ascontiguousarray(a)).pin_memory() if a is not None else None for a in host_rts]
+    lights_h = torch.from_numpy(sc.lights).pin_memory()
+    ldr_h = torch.empty(H, W, 4, dtype=torch.uint8).pin_memory()
+    h2d = sum(p.numel() * p.element_size() for p in pinned if p is not None) + lights_h.numel() * 4
+    d2h = ldr_h.numel()
+
+    def e2e_step():
+        for p, d in zip(pinned, dev_rts):
+            if p is not None:
+                d.copy_(p, non_blocking=True)
+        lights.copy_(lights_h, non_blocking=True)
+        step()
+        ldr_h.copy_(ldr, non_blocking=True)
+
+    with torch.cuda.stream(stream):
+        for _ in range(3):
+            e2e_step()
+    stream.synchronize()
+    e2e_ms = []
+    with torch.cuda.stream(stream):
+        for _ in range(args.steps):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            e2e_step()
+            b.record(stream)
+            e2e_ms.append((a, b))
+    stream.synchronize()
+    e2e_total = sum(a.elapsed_time(b) for a, b in e2e_ms)
+    if world > 1:
+        tt = torch.tensor([e2e_total], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        e2e_total = float(tt.item())
+
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return
+    px = W * H * args.steps * world
+    value = px / (total_ms * 1e-3) / 1e6
+    e2e_value = px / (e2e_total * 1e-3) / 1e6
+    clocks = clk.summary()
+    props = torch.cuda.get_device_properties(dev)
+    sms = props.multi_processor_count
+    flops, counts = compose_flops(sc, g, c["lights"])
+    clock_mhz = clocks["sm_mhz"] if clocks else 2070.0
+    peak_tflops = sms * 128 * 2 * clock_mhz * 1e6 / 1e12
+    achieved = flops / (shade_ms * 1e-3) / 1e12
+    traffic = kernel_traffic("k_shade", SHADE_SOURCES) if not compact else None
+    roofline = {"bound": "alu", "kernel": "k_shade (compose + fused tone map)", "achieved": achieved,
+                "peak": peak_tflops, "unit": "TFLOP/s", "frac": achieved / peak_tflops, "traffic": traffic,
+                "peak_basis": f"{sms} SMs x 128 FP32 lanes x 2 FLOP x {clock_mhz:.0f} MHz "
+                              f"({'median SM clock sampled during the timed region' if clocks else 'max clock, no samples'})",
+                "shade_ms": shade_ms, "flops_per_launch": flops, **counts}
+    line = {"metric": METRIC, "value": value, "unit": "Mpixels/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": config_dict(c, name, {"precompute_ms": precompute_ms,
+                                            "median_step_ms": statistics.median(step_ms),
+                                            "wall_s": wall}),
+            "roofline": roofline,
+            "e2e": {"value": e2e_value, "unit": "Mpixels/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "gpu_launches": launches_per_step * args.steps,
+            "clocks": clocks}
+    if not args.no_cpu_baseline and world == 1:
+        rate, cores, sample = oracle_frame_rate(dict(c, name=name), sc, g, env, k, nz, args.cpu_seconds)
+        line["cpu_baseline"] = {"value": rate, "unit": "Mpixels/s", "cores": cores, "kind": "oracle",
+                                "sample": sample}
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

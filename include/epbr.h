@@ -281,11 +281,22 @@ typedef struct epbr_tonemap_params {
   int32_t op;      /* EPBR_TONEMAP_ACES (Narkowicz 2015 fit) or EPBR_TONEMAP_REINHARD x/(1+x) */
 } epbr_tonemap_params;
 
-/* out = round_half_up(255 * sRGB_OETF(clamp(op(exposure * hdr.rgb), 0, 1))), alpha 255.
+/* out = round_half_up(255 * sRGB_OETF(clamp(op(x), 0, 1))), alpha 255, where
+ * x = clamp(exposure * hdr.rgb, 0, 1e6) (NaN counts as 0; both operators are saturated long
+ * before 1e6, and the clamp keeps +inf from turning the ACES ratio into NaN).
  * `hdr` DEVICE RGBA32F/RGBA16F, `out` DEVICE uchar4. */
 epbr_status epbr_tonemap(const void* hdr, int32_t hdr_format, int32_t width, int32_t height,
                          int64_t hdr_pitch, const epbr_tonemap_params* params, uint8_t* out,
                          int64_t out_pitch, void* stream);
+
+/* epbr_shade with the tone map fused into its epilogue: the 8-bit image is always written,
+ * the HDR image only when `hdr` is not NULL.  With RGBA32F the result equals epbr_shade
+ * followed by epbr_tonemap; with RGBA16F the tone map reads the FP32 value before rounding. */
+epbr_status epbr_shade_tonemap(const epbr_gbuffer* gbuffer, const epbr_camera* camera,
+                               const epbr_light* lights, int32_t num_lights, const epbr_ibl* ibl,
+                               const epbr_shade_params* params, void* hdr, int32_t hdr_format,
+                               int64_t hdr_pitch, const epbr_tonemap_params* tonemap,
+                               uint8_t* ldr, int64_t ldr_pitch, void* stream);
 
 #ifdef __cplusplus
 }

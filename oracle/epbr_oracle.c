@@ -773,8 +773,11 @@ static double srgb_encode(double y) { return y <= 0.0031308 ? 12.92 * y : 1.055 
 int or_tonemap(const double* hdr, long n, double exposure, int op, uint8_t* out, double* scaled) {
   for (long p = 0; p < n; ++p) {
     for (int c = 0; c < 3; ++c) {
+      /* Input clamp to [0, 1e6] (NaN -> 0): both operators saturate long before 1e6, and
+       * the ACES ratio of +inf would be NaN.  A reading; Sec. 5.4 names only the operators. */
       double x = exposure * hdr[p * 3 + c];
       x = x > 0.0 ? x : 0.0;
+      x = x < 1e6 ? x : 1e6;
       double y = (op == 1) ? x / (1.0 + x) : aces_fit(x);
       y = clampd(y, 0.0, 1.0);
       double s = 255.0 * srgb_encode(y);

@@ -1,0 +1,275 @@
+"""epbr — GB300-native deferred physically-based shading (EasyPBR, arXiv 2012.03325).
+
+Thin binding over libepbr.so (include/epbr.h).  Each `epbr_*` function here has the name of the
+C entry point it calls and only marshals torch tensors into pointers, pitches and the current
+CUDA stream; every step of the computation runs in the library's CUDA kernels.  PyTorch
+supplies device memory and streams.
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+import torch
+
+from . import _ffi as F
+from ._ffi import (EPBR_GBUFFER_COMPACT, EPBR_GBUFFER_FP32, EPBR_HDR_RGBA16F, EPBR_HDR_RGBA32F,  # noqa: F401
+                   EPBR_SHADE_ALL, EPBR_SHADE_DIFFUSE_ONLY, EPBR_SHADE_DIRECT, EPBR_SHADE_IBL,
+                   EPBR_SHADE_MULTISCATTER, EPBR_TONEMAP_ACES, EPBR_TONEMAP_REINHARD)
+
+
+class EpbrError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"epbr status {status}: {message}")
+        self.status = status
+
+
+def lib():
+    return F.load()
+
+
+def _check(st: int):
+    if st != F.EPBR_OK:
+        raise EpbrError(st, lib().epbr_last_error().decode())
+
+
+def _stream(stream) -> int:
+    if stream is None:
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def _dev(t: torch.Tensor, dtype=None, name="tensor") -> int:
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if dtype is not None and t.dtype != dtype:
+        raise ValueError(f"{name} must be {dtype}, got {t.dtype}")
+    return t.data_ptr()
+
+
+def _pitch(t: torch.Tensor, texel_elems: int) -> int:
+    """Row pitch in bytes of an (H, W[, C]) tensor whose rows are dense."""
+    if t.dim() >= 2:
+        inner = t[0].is_contiguous()
+        if not inner:
+            raise ValueError("rows of image tensors must be contiguous")
+        return t.stride(0) * t.element_size()
+    raise ValueError("image tensors need at least 2 dims")
+
+
+class GBuffer:
+    """Owns references to the render-target tensors and their epbr_gbuffer struct."""
+
+    def __init__(self, fmt: int, rts, W: int, H: int):
+        self.tensors = rts
+        s = F.epbr_gbuffer()
+        s.format, s.width, s.height = fmt, W, H
+        for i, t in enumerate(rts):
+            if t is not None:
+                s.rt[i] = _dev(t, name=f"rt[{i}]")
+                s.pitch[i] = _pitch(t, 1)
+        self.struct = s
+
+    @classmethod
+    def fp32(cls, rt0: torch.Tensor, rt1: torch.Tensor, depth: torch.Tensor) -> "GBuffer":
+        H, W = depth.shape
+        for t, n in ((rt0, "rt0"), (rt1, "rt1"), (depth, "depth")):
+            _dev(t, torch.float32, n)
+        return cls(F.EPBR_GBUFFER_FP32, [rt0, rt1, None, depth], W, H)
+
+    @classmethod
+    def compact(cls, rt0: torch.Tensor, rt1: torch.Tensor, rt2: torch.Tensor, depth: torch.Tensor) -> "GBuffer":
+        H, W = depth.shape
+        _dev(rt0, torch.uint8, "rt0")
+        _dev(rt1, torch.float16, "rt1")
+        _dev(rt2, torch.uint8, "rt2")
+        _dev(depth, torch.float32, "depth")
+        return cls(F.EPBR_GBUFFER_COMPACT, [rt0, rt1, rt2, depth], W, H)
+
+
+def camera(view_to_world_colmajor, fov_y: float, W: int, H: int) -> F.epbr_camera:
+    c = F.epbr_camera()
+    for i, v in enumerate(list(view_to_world_colmajor)):
+        c.view_to_world[i] = float(v)
+    c.fov_y, c.width, c.height = float(fov_y), int(W), int(H)
+    return c
+
+
+def ibl_params(num_levels: int, prefilter_samples: int, lut_size: int, lut_samples: int, irr_width: int,
+               irr_height: int) -> F.epbr_ibl_params:
+    return F.epbr_ibl_params(num_levels, prefilter_samples, lut_size, lut_samples, irr_width, irr_height)
+
+
+class Ibl:
+    """A lighting set: one device buffer (torch uint8) laid out by epbr_ibl_layout."""
+
+    def __init__(self, params: F.epbr_ibl_params, env_w: int, env_h: int, device="cuda"):
+        n = C.c_size_t()
+        _check(lib().epbr_ibl_layout(C.byref(params), env_w, env_h, None, C.byref(n), None))
+        self.buffer = torch.empty(n.value + 256, dtype=torch.uint8, device=device)
+        base = (self.buffer.data_ptr() + 255) & ~255
+        self.struct = F.epbr_ibl()
+        _check(lib().epbr_ibl_layout(C.byref(params), env_w, env_h, C.c_void_p(base), C.byref(n),
+                                     C.byref(self.struct)))
+        self.params = params
+        self.env_w, self.env_h = env_w, env_h
+        self._base = base
+
+    def _view(self, ptr: int, shape, dtype=torch.float32) -> torch.Tensor:
+        off = ptr - self.buffer.data_ptr()
+        nbytes = 1
+        for s in shape:
+            nbytes *= s
+        nbytes *= torch.tensor([], dtype=dtype).element_size()
+        return self.buffer[off:off + nbytes].view(dtype).view(*shape)
+
+    def irradiance(self) -> torch.Tensor:
+        s = self.struct
+        return self._view(s.irradiance, (s.irr_height, s.irr_width, 4))
+
+    def lut(self) -> torch.Tensor:
+        s = self.struct
+        return self._view(s.lut, (s.lut_size, s.lut_size, 2))
+
+    def level(self, m: int) -> torch.Tensor:
+        s = self.struct
+        return self._view(s.level[m], (s.level_height[m], s.level_width[m], 4))
+
+
+def env_struct(env: torch.Tensor) -> F.epbr_env:
+    _dev(env, torch.float32, "env")
+    if not env.is_contiguous() or env.dim() != 3 or env.shape[2] != 4:
+        raise ValueError("env must be a contiguous (H, W, 4) float32 tensor")
+    return F.epbr_env(env.data_ptr(), env.shape[1], env.shape[0])
+
+
+def epbr_precompute_ibl_workspace_size(params: F.epbr_ibl_params, env_w: int, env_h: int) -> int:
+    n = C.c_size_t()
+    _check(lib().epbr_precompute_ibl_workspace_size(C.byref(params), env_w, env_h, C.byref(n)))
+    return n.value
+
+
+def _workspace(nbytes: int, device) -> torch.Tensor:
+    return torch.empty(max(nbytes, 16) + 256, dtype=torch.uint8, device=device)
+
+
+def _aligned(ws: torch.Tensor) -> int:
+    return (ws.data_ptr() + 255) & ~255
+
+
+def epbr_precompute_ibl(env: torch.Tensor, ibl: Ibl, workspace: torch.Tensor | None = None, stream=None):
+    e = env_struct(env)
+    need = epbr_precompute_ibl_workspace_size(ibl.params, e.width, e.height)
+    ws = workspace if workspace is not None else _workspace(need, env.device)
+    _check(lib().epbr_precompute_ibl(C.byref(e), C.byref(ibl.params), C.byref(ibl.struct), _aligned(ws),
+                                     ws.numel() - (_aligned(ws) - ws.data_ptr()), _stream(stream)))
+    return ibl
+
+
+def epbr_brdf_lut(S: int, N: int, out: torch.Tensor, stream=None):
+    _dev(out, torch.float32, "lut")
+    _check(lib().epbr_brdf_lut(S, N, out.data_ptr(), _stream(stream)))
+
+
+def epbr_irradiance(env: torch.Tensor, Wi: int, Hi: int, out: torch.Tensor, workspace=None, stream=None):
+    e = env_struct(env)
+    _dev(out, torch.float32, "out")
+    n = C.c_size_t()
+    p = ibl_params(1, 1, 1, 1, Wi, Hi)
+    _check(lib().epbr_precompute_ibl_workspace_size(C.byref(p), e.width, e.height, C.byref(n)))
+    ws = workspace if workspace is not None else _workspace(n.value, env.device)
+    _check(lib().epbr_irradiance(C.byref(e), Wi, Hi, out.data_ptr(), _aligned(ws),
+                                 ws.numel() - (_aligned(ws) - ws.data_ptr()), _stream(stream)))
+
+
+def epbr_prefilter(env: torch.Tensor, N: int, ibl: Ibl, stream=None):
+    e = env_struct(env)
+    _check(lib().epbr_prefilter(C.byref(e), N, C.byref(ibl.struct), _stream(stream)))
+
+
+class SsaoParams:
+    """epbr_ssao_params plus the device tensors it points at."""
+
+    def __init__(self, kernel: torch.Tensor, noise: torch.Tensor, radius: float = 0.5, bias: float | None = None,
+                 scale: int = 2, blur_radius: int = 3, sigma_s: float = 2.0, sigma_z: float = 0.1):
+        _dev(kernel, torch.float32, "kernel")
+        _dev(noise, torch.float32, "noise")
+        self.kernel, self.noise = kernel.contiguous(), noise.contiguous()
+        b = 0.05 * radius if bias is None else bias
+        self.struct = F.epbr_ssao_params(kernel.shape[0], scale, radius, b, blur_radius, sigma_s, sigma_z, 0,
+                                         self.kernel.data_ptr(), self.noise.data_ptr())
+
+    def ao_shape(self, W: int, H: int):
+        s = self.struct.scale
+        return ((H + s - 1) // s, (W + s - 1) // s)
+
+
+def epbr_ssao_raw(g: GBuffer, cam: F.epbr_camera, p: SsaoParams, ao: torch.Tensor, stream=None):
+    _dev(ao, torch.float32, "ao")
+    _check(lib().epbr_ssao_raw(C.byref(g.struct), C.byref(cam), C.byref(p.struct), ao.data_ptr(),
+                               _pitch(ao, 1), _stream(stream)))
+
+
+def epbr_ssao_blur(g: GBuffer, p: SsaoParams, ao_in: torch.Tensor, ao_out: torch.Tensor, stream=None):
+    _dev(ao_in, torch.float32, "ao_in")
+    _dev(ao_out, torch.float32, "ao_out")
+    _check(lib().epbr_ssao_blur(C.byref(g.struct), C.byref(p.struct), ao_in.data_ptr(), _pitch(ao_in, 1),
+                                ao_out.data_ptr(), _pitch(ao_out, 1), _stream(stream)))
+
+
+def epbr_ssao(g: GBuffer, cam: F.epbr_camera, p: SsaoParams, ao: torch.Tensor, workspace=None, stream=None):
+    _dev(ao, torch.float32, "ao")
+    n = C.c_size_t()
+    _check(lib().epbr_ssao_workspace_size(C.byref(g.struct), C.byref(p.struct), C.byref(n)))
+    ws = workspace if workspace is not None else _workspace(n.value, ao.device)
+    _check(lib().epbr_ssao(C.byref(g.struct), C.byref(cam), C.byref(p.struct), ao.data_ptr(), _pitch(ao, 1),
+                           _aligned(ws), ws.numel() - (_aligned(ws) - ws.data_ptr()), _stream(stream)))
+
+
+def shade_params(flags: int = EPBR_SHADE_ALL, ao: torch.Tensor | None = None, ao_scale: int = 2):
+    sp = F.epbr_shade_params(flags, ao_scale, None, 0)
+    if ao is not None:
+        sp.ao = _dev(ao, torch.float32, "ao")
+        sp.ao_pitch = _pitch(ao, 1)
+    return sp
+
+
+def _lights(lights: torch.Tensor | None):
+    if lights is None or lights.numel() == 0:
+        return None, 0
+    _dev(lights, torch.float32, "lights")
+    if lights.dim() != 2 or lights.shape[1] != 8 or not lights.is_contiguous():
+        raise ValueError("lights must be a contiguous (N, 8) float32 tensor")
+    return lights.data_ptr(), lights.shape[0]
+
+
+def epbr_shade(g: GBuffer, cam: F.epbr_camera, lights: torch.Tensor | None, ibl: Ibl | None,
+               params: F.epbr_shade_params, hdr: torch.Tensor, hdr_format: int = EPBR_HDR_RGBA32F, stream=None):
+    lp, nl = _lights(lights)
+    _dev(hdr, name="hdr")
+    _check(lib().epbr_shade(C.byref(g.struct), C.byref(cam), lp, nl, C.byref(ibl.struct) if ibl else None,
+                            C.byref(params), hdr.data_ptr(), hdr_format, _pitch(hdr, 1), _stream(stream)))
+
+
+def tonemap_params(exposure: float = 1.0, op: int = EPBR_TONEMAP_ACES) -> F.epbr_tonemap_params:
+    return F.epbr_tonemap_params(exposure, op)
+
+
+def epbr_shade_tonemap(g: GBuffer, cam: F.epbr_camera, lights, ibl: Ibl | None, params: F.epbr_shade_params,
+                       hdr: torch.Tensor | None, hdr_format: int, tp: F.epbr_tonemap_params, ldr: torch.Tensor,
+                       stream=None):
+    lp, nl = _lights(lights)
+    _dev(ldr, torch.uint8, "ldr")
+    hp, hpitch = (None, 0) if hdr is None else (_dev(hdr, name="hdr"), _pitch(hdr, 1))
+    _check(lib().epbr_shade_tonemap(C.byref(g.struct), C.byref(cam), lp, nl, C.byref(ibl.struct) if ibl else None,
+                                    C.byref(params), hp, hdr_format, hpitch, C.byref(tp), ldr.data_ptr(),
+                                    _pitch(ldr, 1), _stream(stream)))
+
+
+def epbr_tonemap(hdr: torch.Tensor, hdr_format: int, tp: F.epbr_tonemap_params, out: torch.Tensor, stream=None):
+    _dev(hdr, name="hdr")
+    _dev(out, torch.uint8, "out")
+    H, W = hdr.shape[0], hdr.shape[1]
+    _check(lib().epbr_tonemap(hdr.data_ptr(), hdr_format, W, H, _pitch(hdr, 1), C.byref(tp), out.data_ptr(),
+                              _pitch(out, 1), _stream(stream)))

@@ -1,0 +1,135 @@
+"""ctypes mirror of include/epbr.h: structs, constants and prototypes of libepbr.so.
+
+Loading fails loudly (ImportError / RuntimeError) when the library is missing: there is no
+CPU or PyTorch fallback for any entry point.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libepbr.so")
+
+# status codes
+EPBR_OK = 0
+EPBR_ERR_INVALID_ARG = 1
+EPBR_ERR_UNSUPPORTED = 2
+EPBR_ERR_CUDA = 3
+EPBR_ERR_NO_MEMORY = 4
+EPBR_ERR_ADMISSION = 5
+EPBR_ERR_TIMEOUT = 6
+EPBR_ERR_DEVICE_STATUS = 7
+
+EPBR_GBUFFER_FP32 = 0
+EPBR_GBUFFER_COMPACT = 1
+EPBR_MAX_LEVELS = 16
+EPBR_SHADE_DIRECT = 1
+EPBR_SHADE_IBL = 2
+EPBR_SHADE_MULTISCATTER = 4
+EPBR_SHADE_DIFFUSE_ONLY = 8
+EPBR_SHADE_ALL = 7
+EPBR_HDR_RGBA32F = 0
+EPBR_HDR_RGBA16F = 1
+EPBR_TONEMAP_ACES = 0
+EPBR_TONEMAP_REINHARD = 1
+
+
+class epbr_camera(C.Structure):
+    _fields_ = [("view_to_world", C.c_float * 16), ("fov_y", C.c_float), ("width", C.c_int32),
+                ("height", C.c_int32)]
+
+
+class epbr_light(C.Structure):
+    _fields_ = [("pos", C.c_float * 3), ("intensity", C.c_float), ("color", C.c_float * 3),
+                ("pad", C.c_float)]
+
+
+class epbr_gbuffer(C.Structure):
+    _fields_ = [("format", C.c_int32), ("width", C.c_int32), ("height", C.c_int32),
+                ("reserved", C.c_int32), ("rt", C.c_void_p * 4), ("pitch", C.c_int64 * 4)]
+
+
+class epbr_env(C.Structure):
+    _fields_ = [("texels", C.c_void_p), ("width", C.c_int32), ("height", C.c_int32)]
+
+
+class epbr_ibl_params(C.Structure):
+    _fields_ = [("num_levels", C.c_int32), ("prefilter_samples", C.c_int32), ("lut_size", C.c_int32),
+                ("lut_samples", C.c_int32), ("irr_width", C.c_int32), ("irr_height", C.c_int32)]
+
+
+class epbr_ibl(C.Structure):
+    _fields_ = [("irradiance", C.c_void_p), ("irr_width", C.c_int32), ("irr_height", C.c_int32),
+                ("lut", C.c_void_p), ("lut_size", C.c_int32), ("num_levels", C.c_int32),
+                ("level", C.c_void_p * EPBR_MAX_LEVELS), ("level_width", C.c_int32 * EPBR_MAX_LEVELS),
+                ("level_height", C.c_int32 * EPBR_MAX_LEVELS)]
+
+
+class epbr_ssao_params(C.Structure):
+    _fields_ = [("num_samples", C.c_int32), ("scale", C.c_int32), ("radius", C.c_float),
+                ("bias", C.c_float), ("blur_radius", C.c_int32), ("sigma_s", C.c_float),
+                ("sigma_z", C.c_float), ("reserved", C.c_int32), ("kernel", C.c_void_p),
+                ("noise", C.c_void_p)]
+
+
+class epbr_shade_params(C.Structure):
+    _fields_ = [("flags", C.c_uint32), ("ao_scale", C.c_int32), ("ao", C.c_void_p), ("ao_pitch", C.c_int64)]
+
+
+class epbr_tonemap_params(C.Structure):
+    _fields_ = [("exposure", C.c_float), ("op", C.c_int32)]
+
+
+P = C.POINTER
+vp, i32, i64, sz = C.c_void_p, C.c_int32, C.c_int64, C.c_size_t
+
+# name -> argtypes; every entry point returns epbr_status (int32)
+PROTOTYPES = {
+    "epbr_ibl_layout": [P(epbr_ibl_params), i32, i32, vp, P(sz), P(epbr_ibl)],
+    "epbr_precompute_ibl_workspace_size": [P(epbr_ibl_params), i32, i32, P(sz)],
+    "epbr_precompute_ibl": [P(epbr_env), P(epbr_ibl_params), P(epbr_ibl), vp, sz, vp],
+    "epbr_brdf_lut": [i32, i32, vp, vp],
+    "epbr_irradiance": [P(epbr_env), i32, i32, vp, vp, sz, vp],
+    "epbr_prefilter": [P(epbr_env), i32, P(epbr_ibl), vp],
+    "epbr_ssao_size": [P(epbr_gbuffer), P(epbr_ssao_params), P(i32), P(i32)],
+    "epbr_ssao_workspace_size": [P(epbr_gbuffer), P(epbr_ssao_params), P(sz)],
+    "epbr_ssao_raw": [P(epbr_gbuffer), P(epbr_camera), P(epbr_ssao_params), vp, i64, vp],
+    "epbr_ssao_blur": [P(epbr_gbuffer), P(epbr_ssao_params), vp, i64, vp, i64, vp],
+    "epbr_ssao": [P(epbr_gbuffer), P(epbr_camera), P(epbr_ssao_params), vp, i64, vp, sz, vp],
+    "epbr_shade": [P(epbr_gbuffer), P(epbr_camera), vp, i32, P(epbr_ibl), P(epbr_shade_params), vp, i32,
+                   i64, vp],
+    "epbr_shade_tonemap": [P(epbr_gbuffer), P(epbr_camera), vp, i32, P(epbr_ibl), P(epbr_shade_params), vp,
+                           i32, i64, P(epbr_tonemap_params), vp, i64, vp],
+    "epbr_tonemap": [vp, i32, i32, i32, i64, P(epbr_tonemap_params), vp, i64, vp],
+}
+OTHER = {"epbr_last_error": ([], C.c_char_p), "epbr_version": ([], C.c_char_p)}
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Loads libepbr.so (building it first if it is absent or stale)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    from . import build as _build
+    if not _build.up_to_date():
+        _build.build()
+    if not os.path.exists(path):
+        raise ImportError(f"libepbr.so not found at {path}: build it with paper_2012_03325_gb300/build.py")
+    lib = C.CDLL(path)
+    for name, args in PROTOTYPES.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = C.c_int32
+    for name, (args, res) in OTHER.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = res
+    _lib = lib
+    return lib
+
+
+def exported_names():
+    return list(PROTOTYPES) + list(OTHER)

@@ -1,0 +1,193 @@
+// Internal device and host helpers shared by the libepbr translation units.
+#pragma once
+
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/epbr.h"
+
+namespace epbr {
+
+// ------------------------------------------------------------------------------------------
+// host: error reporting (thread-local message, see abi.cu)
+// ------------------------------------------------------------------------------------------
+epbr_status fail(epbr_status code, const char* fmt, ...);
+epbr_status ok();
+// Checks cudaGetLastError after launches; returns EPBR_ERR_CUDA with `what` on failure.
+epbr_status check_launch(const char* what);
+int num_sms();
+
+constexpr float kPi = 3.14159265358979323846f;
+constexpr float kInvPi = 0.318309886183790671538f;
+constexpr float kInv2Pi = 0.159154943091895335769f;
+constexpr float kRoughMin = 0.045f;
+constexpr float kNvMin = 1e-4f;
+
+// ------------------------------------------------------------------------------------------
+// device: small vector algebra on float3
+// ------------------------------------------------------------------------------------------
+__device__ __forceinline__ float3 f3(float x, float y, float z) { return make_float3(x, y, z); }
+__device__ __forceinline__ float3 operator+(float3 a, float3 b) { return f3(a.x + b.x, a.y + b.y, a.z + b.z); }
+__device__ __forceinline__ float3 operator-(float3 a, float3 b) { return f3(a.x - b.x, a.y - b.y, a.z - b.z); }
+__device__ __forceinline__ float3 operator*(float3 a, float s) { return f3(a.x * s, a.y * s, a.z * s); }
+__device__ __forceinline__ float3 operator*(float s, float3 a) { return f3(a.x * s, a.y * s, a.z * s); }
+__device__ __forceinline__ float3 mul3(float3 a, float3 b) { return f3(a.x * b.x, a.y * b.y, a.z * b.z); }
+__device__ __forceinline__ float dot3(float3 a, float3 b) { return fmaf(a.x, b.x, fmaf(a.y, b.y, a.z * b.z)); }
+__device__ __forceinline__ float3 cross3(float3 a, float3 b) {
+  return f3(fmaf(a.y, b.z, -a.z * b.y), fmaf(a.z, b.x, -a.x * b.z), fmaf(a.x, b.y, -a.y * b.x));
+}
+__device__ __forceinline__ float3 normalize3(float3 a) { return a * rsqrtf(dot3(a, a)); }
+__device__ __forceinline__ float clamp01(float x) { return fminf(fmaxf(x, 0.0f), 1.0f); }
+__device__ __forceinline__ float3 xyz(float4 a) { return f3(a.x, a.y, a.z); }
+
+// Camera in device-friendly form: rotation rows/columns, eye, per-pixel ray scale.
+struct CamDev {
+  float r[9];   // view_to_world rotation, r[3*i + j] = row i, column j
+  float eye[3];
+  float sx, sy;  // px = (2 (x + 0.5) / W - 1) * sx, py = (1 - 2 (y + 0.5) / H) * sy
+  int W, H;
+};
+
+__host__ inline CamDev make_cam(const epbr_camera& c) {
+  CamDev d;
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) d.r[3 * i + j] = c.view_to_world[4 * j + i];
+  d.eye[0] = c.view_to_world[12];
+  d.eye[1] = c.view_to_world[13];
+  d.eye[2] = c.view_to_world[14];
+  double t = tan(0.5 * (double)c.fov_y);
+  d.sy = (float)t;
+  d.sx = (float)(t * (double)c.width / (double)c.height);
+  d.W = c.width;
+  d.H = c.height;
+  return d;
+}
+
+// View-space ray (px, py, -1) of the centre of pixel (x, y).
+__device__ __forceinline__ float3 view_ray(const CamDev& c, int x, int y) {
+  float px = fmaf(2.0f * (x + 0.5f), 1.0f / c.W, -1.0f) * c.sx;
+  float py = fmaf(-2.0f * (y + 0.5f), 1.0f / c.H, 1.0f) * c.sy;
+  return f3(px, py, -1.0f);
+}
+__device__ __forceinline__ float3 rot(const CamDev& c, float3 a) {
+  return f3(fmaf(c.r[0], a.x, fmaf(c.r[1], a.y, c.r[2] * a.z)),
+            fmaf(c.r[3], a.x, fmaf(c.r[4], a.y, c.r[5] * a.z)),
+            fmaf(c.r[6], a.x, fmaf(c.r[7], a.y, c.r[8] * a.z)));
+}
+__device__ __forceinline__ float3 rot_t(const CamDev& c, float3 a) {
+  return f3(fmaf(c.r[0], a.x, fmaf(c.r[3], a.y, c.r[6] * a.z)),
+            fmaf(c.r[1], a.x, fmaf(c.r[4], a.y, c.r[7] * a.z)),
+            fmaf(c.r[2], a.x, fmaf(c.r[5], a.y, c.r[8] * a.z)));
+}
+__device__ __forceinline__ bool is_surface(float e) { return e > 0.0f && e < __int_as_float(0x7f800000); }
+
+// ------------------------------------------------------------------------------------------
+// device: equirect environment maps
+// ------------------------------------------------------------------------------------------
+struct MapDev {
+  const float4* texels;
+  int W, H;
+};
+
+__device__ __forceinline__ void dir_to_uv(float3 d, float& u, float& v) {
+  u = fmaf(atan2f(d.x, -d.z), kInv2Pi, 0.5f);
+  v = atan2f(sqrtf(fmaf(d.x, d.x, d.z * d.z)), d.y) * kInvPi;
+}
+
+// Bilinear read at (u, v): wrap in u, clamp in v.
+__device__ __forceinline__ float3 equirect_bilinear(const MapDev m, float u, float v) {
+  float x = fmaf(u, (float)m.W, -0.5f), y = fmaf(v, (float)m.H, -0.5f);
+  float x0 = floorf(x), y0 = floorf(y);
+  float fx = x - x0, fy = y - y0;
+  int ix = (int)x0, iy = (int)y0;
+  int i0 = ix < 0 ? ix + m.W : (ix >= m.W ? ix - m.W : ix);
+  int i1 = i0 + 1 == m.W ? 0 : i0 + 1;
+  int j0 = min(max(iy, 0), m.H - 1), j1 = min(max(iy + 1, 0), m.H - 1);
+  const float4* r0 = m.texels + (size_t)j0 * m.W;
+  const float4* r1 = m.texels + (size_t)j1 * m.W;
+  float4 a = __ldg(r0 + i0), b = __ldg(r0 + i1), p = __ldg(r1 + i0), q = __ldg(r1 + i1);
+  float3 top = xyz(a) + fx * (xyz(b) - xyz(a));
+  float3 bot = xyz(p) + fx * (xyz(q) - xyz(p));
+  return top + fy * (bot - top);
+}
+
+__device__ __forceinline__ float3 equirect_lookup(const MapDev m, float3 d) {
+  float u, v;
+  dir_to_uv(d, u, v);
+  return equirect_bilinear(m, u, v);
+}
+
+// Branchless orthonormal basis (Duff et al., JCGT 2017) around unit n.
+__device__ __forceinline__ void onb(float3 n, float3& t, float3& b) {
+  float s = copysignf(1.0f, n.z);
+  float a = -1.0f / (s + n.z);
+  float c = n.x * n.y * a;
+  t = f3(fmaf(s * n.x * n.x, a, 1.0f), s * c, -s * n.x);
+  b = f3(c, fmaf(n.y * n.y, a, s), -n.y);
+}
+
+// Kahan-compensated accumulator.
+struct Kahan {
+  float s = 0.0f, c = 0.0f;
+  __device__ __forceinline__ void add(float x) {
+    float y = x - c;
+    float t = s + y;
+    c = (t - s) - y;
+    s = t;
+  }
+};
+
+// G-buffer in kernel-argument form.
+struct GbufDev {
+  const char* rt[4];
+  long long pitch[4];
+  int W, H;
+};
+
+__host__ inline GbufDev make_gbuf(const epbr_gbuffer& g) {
+  GbufDev d;
+  for (int i = 0; i < 4; ++i) {
+    d.rt[i] = (const char*)g.rt[i];
+    d.pitch[i] = g.pitch[i];
+  }
+  d.W = g.width;
+  d.H = g.height;
+  return d;
+}
+
+__device__ __forceinline__ float gb_depth(const GbufDev& g, int x, int y) {
+  return __ldg((const float*)(g.rt[3] + (size_t)y * g.pitch[3]) + x);
+}
+
+// Octahedral unit-vector decode (Cigolle et al. 2014).
+__device__ __forceinline__ float3 oct_decode(__half2 h) {
+  float2 p = __half22float2(h);
+  float x = p.x, y = p.y;
+  float z = 1.0f - fabsf(x) - fabsf(y);
+  if (z < 0.0f) {
+    float nx = (1.0f - fabsf(y)) * (x >= 0.0f ? 1.0f : -1.0f);
+    float ny = (1.0f - fabsf(x)) * (y >= 0.0f ? 1.0f : -1.0f);
+    x = nx;
+    y = ny;
+  }
+  return normalize3(f3(x, y, z));
+}
+
+template <int FMT>
+__device__ __forceinline__ float3 gb_normal(const GbufDev& g, int x, int y) {
+  if (FMT == EPBR_GBUFFER_FP32) {
+    float4 n = __ldg((const float4*)(g.rt[1] + (size_t)y * g.pitch[1]) + x);
+    return normalize3(xyz(n));
+  } else {
+    unsigned int bits = __ldg((const unsigned int*)(g.rt[1] + (size_t)y * g.pitch[1]) + x);
+    return oct_decode(*reinterpret_cast<const __half2*>(&bits));
+  }
+}
+
+// Validation helpers shared by the entry points.
+epbr_status validate_gbuffer(const epbr_gbuffer* g, bool need_material);
+epbr_status validate_camera(const epbr_camera* c, const epbr_gbuffer* g);
+epbr_status validate_env(const epbr_env* e);
+
+}  // namespace epbr

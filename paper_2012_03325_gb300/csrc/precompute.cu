@@ -1,0 +1,315 @@
+// Image-based lighting precompute (paper Sec. 3.1; split sum of Karis 2013):
+//   k_brdf_lut          BRDF integration table (A, B), one warp per texel, Kahan + shuffles
+//   k_irradiance_part   exact-quadrature irradiance, per-block partial sums over a slice of
+//                       source texels staged in shared memory
+//   k_irradiance_final  sums the partials in a fixed order (deterministic) and normalises
+//   k_prefilter         GGX-prefiltered levels 1..M-1, one thread per output texel
+#include <algorithm>
+
+#include "epbr_internal.cuh"
+
+namespace epbr {
+
+// Hammersley point k of N: (k / N, radical_inverse_2(k)).  For k < 2^24 the mirrored bits fit
+// the float mantissa, so xi2 is exact.
+__device__ __forceinline__ float hammersley_xi2(unsigned k) {
+  return __uint2float_rn(__brev(k)) * 2.3283064365386963e-10f;
+}
+
+// GGX half vector in the frame (t, b, n): phi = 2 pi xi1, cos^2 = (1 - xi2) / d,
+// sin^2 = alpha^2 xi2 / d with d = 1 + (alpha^2 - 1) xi2 (sin^2 taken directly, which avoids
+// the cancellation of 1 - cos^2 near the lobe centre).
+__device__ __forceinline__ float3 ggx_half(float xi1, float xi2, float a2, float3 t, float3 b, float3 n) {
+  float inv = 1.0f / fmaf(a2 - 1.0f, xi2, 1.0f);
+  float ct = sqrtf((1.0f - xi2) * inv);
+  float st = sqrtf(a2 * xi2 * inv);
+  float sp, cp;
+  sincospif(2.0f * xi1, &sp, &cp);
+  return t * (st * cp) + b * (st * sp) + n * ct;
+}
+
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// ------------------------------------------------------------------------------------------
+// BRDF integration table
+// ------------------------------------------------------------------------------------------
+__global__ void k_brdf_lut(int S, int N, float2* __restrict__ lut) {
+  int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  int lane = threadIdx.x & 31;
+  if (warp >= S * S) return;
+  int i = warp % S, j = warp / S;
+  float mu = (i + 0.5f) / S, r = (j + 0.5f) / S;
+  float alpha = r * r, a2 = alpha * alpha, k = 0.5f * alpha;
+  float3 v = f3(sqrtf(fmaf(-mu, mu, 1.0f)), 0.0f, mu);
+  float nv = mu;
+  float g1v = nv / fmaf(nv, 1.0f - k, k);
+  Kahan A, B;
+  const float3 t = f3(1, 0, 0), b = f3(0, 1, 0), n = f3(0, 0, 1);
+  float invN = 1.0f / N;
+  for (int s = lane; s < N; s += 32) {
+    float3 h = ggx_half(s * invN, hammersley_xi2((unsigned)s), a2, t, b, n);
+    float vh = dot3(v, h);
+    float nl = fmaf(2.0f * vh, h.z, -v.z);
+    if (nl > 0.0f) {
+      float g = g1v * nl / fmaf(nl, 1.0f - k, k);
+      float gvis = g * vh / (h.z * nv);
+      float x = 1.0f - vh, x2 = x * x;
+      float fc = x2 * x2 * x;
+      A.add((1.0f - fc) * gvis);
+      B.add(fc * gvis);
+    }
+  }
+  float a = warp_sum(A.s - A.c), bb = warp_sum(B.s - B.c);
+  if (lane == 0) lut[warp] = make_float2(a * invN, bb * invN);
+}
+
+// ------------------------------------------------------------------------------------------
+// Irradiance: sum_t L_t max(n.d_t, 0) Omega_t / sum_t max(n.d_t, 0) Omega_t
+// ------------------------------------------------------------------------------------------
+constexpr int kIrrThreads = 256;
+constexpr int kIrrOutPerThread = 4;  // outputs per thread and pass: 1024 per pass
+constexpr int kIrrTile = 512;        // source texels staged per step
+constexpr int kIrrTexelsPerBlock = 1024;
+constexpr int kIrrMaxBlocks = 608;
+
+int irr_blocks(int We, int He) {
+  long long n = (long long)We * He;
+  long long b = (n + kIrrTexelsPerBlock - 1) / kIrrTexelsPerBlock;
+  return (int)std::min<long long>(std::max<long long>(b, 1), kIrrMaxBlocks);
+}
+
+size_t irr_workspace_bytes(int We, int He, int Wi, int Hi) {
+  return (size_t)irr_blocks(We, He) * Wi * Hi * sizeof(float4);
+}
+
+// Unit direction of the centre of texel (i, j) of a W x H equirect map.
+__device__ __forceinline__ float3 texel_dir(int i, int j, int W, int H) {
+  float st, ct, sp, cp;
+  sincospif((j + 0.5f) / H, &st, &ct);
+  sincospif(2.0f * ((i + 0.5f) / W) - 1.0f, &sp, &cp);
+  return f3(st * sp, ct, -st * cp);
+}
+
+__global__ void __launch_bounds__(kIrrThreads) k_irradiance_part(const float4* __restrict__ env, int We,
+                                                                 int He, int Wi, int Hi,
+                                                                 float4* __restrict__ part) {
+  __shared__ float4 s_dir[kIrrTile];  // d.xyz, Omega
+  __shared__ float4 s_rad[kIrrTile];  // L.rgb
+  long long ntex = (long long)We * He;
+  long long per = (ntex + gridDim.x - 1) / gridDim.x;
+  long long t0 = per * blockIdx.x;
+  long long t1 = t0 + per < ntex ? t0 + per : ntex;
+  int nout = Wi * Hi;
+  // Omega of row y = (2 pi / W)(cos(pi y / H) - cos(pi (y + 1) / H))
+  //               = (4 pi / W) sin(pi (y + 0.5) / H) sin(pi / (2 H))   (product form)
+  float row_k = 4.0f * kPi / We * sinpif(0.5f / He);
+  for (int og = 0; og < nout; og += kIrrThreads * kIrrOutPerThread) {
+    float3 n[kIrrOutPerThread];
+    Kahan acc[kIrrOutPerThread][4];
+#pragma unroll
+    for (int r = 0; r < kIrrOutPerThread; ++r) {
+      int o = og + r * kIrrThreads + threadIdx.x;
+      n[r] = o < nout ? texel_dir(o % Wi, o / Wi, Wi, Hi) : f3(0, 0, 0);
+    }
+    for (long long base = t0; base < t1; base += kIrrTile) {
+      int cnt = (int)(t1 - base < kIrrTile ? t1 - base : kIrrTile);
+      __syncthreads();
+      for (int q = threadIdx.x; q < cnt; q += kIrrThreads) {
+        long long t = base + q;
+        int x = (int)(t % We), y = (int)(t / We);
+        float3 d = texel_dir(x, y, We, He);
+        float om = row_k * sinpif((y + 0.5f) / He);
+        s_dir[q] = make_float4(d.x, d.y, d.z, om);
+        s_rad[q] = __ldg(env + t);
+      }
+      __syncthreads();
+      for (int q = 0; q < cnt; ++q) {
+        float4 dd = s_dir[q];
+        float4 L = s_rad[q];
+#pragma unroll
+        for (int r = 0; r < kIrrOutPerThread; ++r) {
+          float w = fmaxf(fmaf(n[r].x, dd.x, fmaf(n[r].y, dd.y, n[r].z * dd.z)), 0.0f) * dd.w;
+          acc[r][0].add(L.x * w);
+          acc[r][1].add(L.y * w);
+          acc[r][2].add(L.z * w);
+          acc[r][3].add(w);
+        }
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < kIrrOutPerThread; ++r) {
+      int o = og + r * kIrrThreads + threadIdx.x;
+      if (o < nout)
+        part[(size_t)blockIdx.x * nout + o] =
+            make_float4(acc[r][0].s - acc[r][0].c, acc[r][1].s - acc[r][1].c,
+                        acc[r][2].s - acc[r][2].c, acc[r][3].s - acc[r][3].c);
+    }
+  }
+}
+
+__global__ void k_irradiance_final(const float4* __restrict__ part, int nblocks, int nout,
+                                   float4* __restrict__ out) {
+  int o = blockIdx.x * blockDim.x + threadIdx.x;
+  if (o >= nout) return;
+  Kahan s[4];
+  for (int b = 0; b < nblocks; ++b) {
+    float4 p = part[(size_t)b * nout + o];
+    s[0].add(p.x);
+    s[1].add(p.y);
+    s[2].add(p.z);
+    s[3].add(p.w);
+  }
+  float den = s[3].s - s[3].c;
+  float inv = 1.0f / den;
+  out[o] = make_float4((s[0].s - s[0].c) * inv, (s[1].s - s[1].c) * inv, (s[2].s - s[2].c) * inv, 1.0f);
+}
+
+// ------------------------------------------------------------------------------------------
+// Prefiltered levels 1..M-1 in one launch
+// ------------------------------------------------------------------------------------------
+struct ChainDev {
+  int M;
+  int nlev;                       // levels written: 1..M-1
+  long long off[EPBR_MAX_LEVELS + 1];  // texel prefix sums over levels 1..M-1
+  int W[EPBR_MAX_LEVELS], H[EPBR_MAX_LEVELS];
+  float4* dst[EPBR_MAX_LEVELS];
+};
+
+__global__ void __launch_bounds__(256) k_prefilter(MapDev src, ChainDev ch, int N) {
+  long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (gid >= ch.off[ch.nlev]) return;
+  int li = 0;
+  while (gid >= ch.off[li + 1]) ++li;
+  int m = li + 1;
+  long long t = gid - ch.off[li];
+  int W = ch.W[m], H = ch.H[m];
+  int i = (int)(t % W), j = (int)(t / W);
+  float3 n = texel_dir(i, j, W, H);
+  float r = (float)m / (float)(ch.M - 1);
+  float a2 = r * r * r * r;
+  float3 tt, bb;
+  onb(n, tt, bb);
+  Kahan acc[4];
+  float invN = 1.0f / N;
+  for (int s = 0; s < N; ++s) {
+    float3 h = ggx_half(s * invN, hammersley_xi2((unsigned)s), a2, tt, bb, n);
+    float nh = dot3(n, h);
+    float nl = fmaf(2.0f * nh, nh, -1.0f);  // n.l with v = n, l = 2 (n.h) h - n
+    if (nl > 0.0f) {
+      float3 l = (2.0f * nh) * h - n;
+      float3 L = equirect_lookup(src, l);
+      acc[0].add(L.x * nl);
+      acc[1].add(L.y * nl);
+      acc[2].add(L.z * nl);
+      acc[3].add(nl);
+    }
+  }
+  float inv = 1.0f / (acc[3].s - acc[3].c);
+  ch.dst[m][t] = make_float4((acc[0].s - acc[0].c) * inv, (acc[1].s - acc[1].c) * inv,
+                             (acc[2].s - acc[2].c) * inv, 1.0f);
+}
+
+static epbr_status validate_ibl_for(const epbr_ibl* ibl, int We, int He) {
+  if (!ibl) return fail(EPBR_ERR_INVALID_ARG, "ibl is NULL");
+  if (ibl->num_levels < 1 || ibl->num_levels > EPBR_MAX_LEVELS)
+    return fail(EPBR_ERR_INVALID_ARG, "ibl->num_levels %d invalid", ibl->num_levels);
+  for (int m = 0; m < ibl->num_levels; ++m) {
+    int w = std::max(1, We >> m), h = std::max(1, He >> m);
+    if (!ibl->level[m] || ibl->level_width[m] != w || ibl->level_height[m] != h)
+      return fail(EPBR_ERR_INVALID_ARG, "ibl level %d does not match the env (%dx%d expected)", m, w, h);
+    if ((uintptr_t)ibl->level[m] % 16) return fail(EPBR_ERR_INVALID_ARG, "ibl level %d not 16-byte aligned", m);
+  }
+  return EPBR_OK;
+}
+
+}  // namespace epbr
+
+using namespace epbr;
+
+extern "C" epbr_status epbr_brdf_lut(int32_t S, int32_t N, float* lut, void* stream) {
+  if (S < 1 || S > 4096 || N < 1 || N > (1 << 24) || !lut)
+    return fail(EPBR_ERR_INVALID_ARG, "brdf_lut: size %d / samples %d / pointer invalid", S, N);
+  if ((uintptr_t)lut % 8) return fail(EPBR_ERR_INVALID_ARG, "brdf_lut: lut not 8-byte aligned");
+  long long threads = (long long)S * S * 32;
+  int blocks = (int)((threads + 255) / 256);
+  k_brdf_lut<<<blocks, 256, 0, (cudaStream_t)stream>>>(S, N, (float2*)lut);
+  epbr_status st = check_launch("k_brdf_lut");
+  return st ? st : ok();
+}
+
+extern "C" epbr_status epbr_precompute_ibl_workspace_size(const epbr_ibl_params* p, int32_t We,
+                                                          int32_t He, size_t* bytes) {
+  if (!p || !bytes) return fail(EPBR_ERR_INVALID_ARG, "params or bytes is NULL");
+  if (We < 1 || He < 1 || p->irr_width < 1 || p->irr_height < 1)
+    return fail(EPBR_ERR_INVALID_ARG, "sizes must be positive");
+  *bytes = irr_workspace_bytes(We, He, p->irr_width, p->irr_height);
+  return ok();
+}
+
+extern "C" epbr_status epbr_irradiance(const epbr_env* env, int32_t Wi, int32_t Hi, float* out,
+                                       void* ws, size_t ws_bytes, void* stream) {
+  epbr_status st = validate_env(env);
+  if (st) return st;
+  if (Wi < 1 || Hi < 1 || Wi > 4096 || Hi > 4096 || !out)
+    return fail(EPBR_ERR_INVALID_ARG, "irradiance: output %dx%d or pointer invalid", Wi, Hi);
+  if ((uintptr_t)out % 16) return fail(EPBR_ERR_INVALID_ARG, "irradiance: out not 16-byte aligned");
+  size_t need = irr_workspace_bytes(env->width, env->height, Wi, Hi);
+  if (!ws || ws_bytes < need || (uintptr_t)ws % 16)
+    return fail(EPBR_ERR_NO_MEMORY, "irradiance: workspace needs %zu bytes (16-byte aligned), got %zu", need,
+                ws ? ws_bytes : (size_t)0);
+  int nb = irr_blocks(env->width, env->height);
+  cudaStream_t s = (cudaStream_t)stream;
+  k_irradiance_part<<<nb, kIrrThreads, 0, s>>>((const float4*)env->texels, env->width, env->height, Wi,
+                                               Hi, (float4*)ws);
+  if ((st = check_launch("k_irradiance_part"))) return st;
+  int nout = Wi * Hi;
+  k_irradiance_final<<<(nout + 255) / 256, 256, 0, s>>>((const float4*)ws, nb, nout, (float4*)out);
+  if ((st = check_launch("k_irradiance_final"))) return st;
+  return ok();
+}
+
+extern "C" epbr_status epbr_prefilter(const epbr_env* env, int32_t N, const epbr_ibl* ibl, void* stream) {
+  epbr_status st = validate_env(env);
+  if (st) return st;
+  if ((st = validate_ibl_for(ibl, env->width, env->height))) return st;
+  if (N < 1 || N > (1 << 24)) return fail(EPBR_ERR_INVALID_ARG, "prefilter: samples %d invalid", N);
+  cudaStream_t s = (cudaStream_t)stream;
+  if (cudaMemcpyAsync(ibl->level[0], env->texels, (size_t)env->width * env->height * 16,
+                      cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+    return fail(EPBR_ERR_CUDA, "prefilter: level-0 copy failed: %s", cudaGetErrorString(cudaGetLastError()));
+  if (ibl->num_levels < 2) return ok();
+  ChainDev ch;
+  ch.M = ibl->num_levels;
+  ch.nlev = ibl->num_levels - 1;
+  ch.off[0] = 0;
+  for (int m = 0; m < EPBR_MAX_LEVELS; ++m) {
+    ch.W[m] = ibl->level_width[m];
+    ch.H[m] = ibl->level_height[m];
+    ch.dst[m] = (float4*)ibl->level[m];
+  }
+  for (int li = 0; li < ch.nlev; ++li) ch.off[li + 1] = ch.off[li] + (long long)ch.W[li + 1] * ch.H[li + 1];
+  MapDev src{(const float4*)env->texels, env->width, env->height};
+  long long total = ch.off[ch.nlev];
+  k_prefilter<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(src, ch, N);
+  if ((st = check_launch("k_prefilter"))) return st;
+  return ok();
+}
+
+extern "C" epbr_status epbr_precompute_ibl(const epbr_env* env, const epbr_ibl_params* p, const epbr_ibl* ibl,
+                                           void* ws, size_t ws_bytes, void* stream) {
+  epbr_status st = validate_env(env);
+  if (st) return st;
+  if (!p) return fail(EPBR_ERR_INVALID_ARG, "params is NULL");
+  if ((st = validate_ibl_for(ibl, env->width, env->height))) return st;
+  if (ibl->num_levels != p->num_levels || ibl->lut_size != p->lut_size || ibl->irr_width != p->irr_width ||
+      ibl->irr_height != p->irr_height || !ibl->lut || !ibl->irradiance)
+    return fail(EPBR_ERR_INVALID_ARG, "ibl layout does not match params");
+  if ((st = epbr_brdf_lut(p->lut_size, p->lut_samples, ibl->lut, stream))) return st;
+  if ((st = epbr_irradiance(env, p->irr_width, p->irr_height, ibl->irradiance, ws, ws_bytes, stream))) return st;
+  if ((st = epbr_prefilter(env, p->prefilter_samples, ibl, stream))) return st;
+  return ok();
+}

@@ -1,0 +1,218 @@
+// Screen-space ambient occlusion (paper Sec. 5.2: normal-oriented hemisphere of Bavoil &
+// Sainz 2008, at half resolution, then a bilateral blur).
+//   k_ssao_raw   one thread per AO texel; the K kernel offsets sit in shared memory and the
+//                depth taps go through the read-only cache
+//   k_ssao_blur  one thread per AO texel; (2R+1)^2 depth-aware taps
+#include "epbr_internal.cuh"
+
+namespace epbr {
+
+constexpr int kMaxSsaoSamples = 256;
+
+struct SsaoDev {
+  int K, scale, R;
+  float radius, bias, sigma_s, sigma_z;
+  const float4* kernel;
+  const float2* noise;
+};
+
+__device__ __forceinline__ float smoothstep01(float x) {
+  x = clamp01(x);
+  return x * x * (3.0f - 2.0f * x);
+}
+
+template <int FMT>
+__global__ void __launch_bounds__(256) k_ssao_raw(GbufDev g, CamDev cam, SsaoDev p, float* __restrict__ ao,
+                                                  long long ao_pitch, int Wa, int Ha) {
+  __shared__ float4 s_kernel[kMaxSsaoSamples];
+  int tid = threadIdx.y * blockDim.x + threadIdx.x;
+  for (int k = tid; k < p.K; k += blockDim.x * blockDim.y) s_kernel[k] = __ldg(p.kernel + k);
+  __syncthreads();
+  int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y;
+  if (i >= Wa || j >= Ha) return;
+  float* out = (float*)((char*)ao + (size_t)j * ao_pitch) + i;
+  int X0 = p.scale * i, Y0 = p.scale * j;
+  float e = gb_depth(g, X0, Y0);
+  if (!is_surface(e)) {
+    *out = 1.0f;
+    return;
+  }
+  float3 P = e * view_ray(cam, X0, Y0);
+  float3 n = rot_t(cam, gb_normal<FMT>(g, X0, Y0));
+  float2 nz = __ldg(p.noise + ((j & 3) * 4 + (i & 3)));
+  float3 rv = f3(nz.x, nz.y, 0.0f);
+  float3 t = rv - n * dot3(rv, n), b;
+  float tl = sqrtf(dot3(t, t));
+  if (tl < 1e-4f) {
+    onb(n, t, b);
+  } else {
+    t = t * (1.0f / tl);
+    b = cross3(n, t);
+  }
+  float ix_scale = 0.5f * cam.W / cam.sx, iy_scale = 0.5f * cam.H / cam.sy;
+  float occ = 0.0f;
+  for (int k = 0; k < p.K; ++k) {
+    float4 ks = s_kernel[k];
+    float3 S = P + p.radius * (t * ks.x + b * ks.y + n * ks.z);
+    float eS = -S.z;
+    if (!(eS > 0.0f)) continue;
+    float inv = 1.0f / eS;
+    float x = fmaf(S.x * inv, ix_scale, 0.5f * cam.W);
+    float y = fmaf(-S.y * inv, iy_scale, 0.5f * cam.H);
+    if (!(x >= 0.0f && x < (float)cam.W && y >= 0.0f && y < (float)cam.H)) continue;
+    int ix = min((int)x, cam.W - 1), iy = min((int)y, cam.H - 1);
+    float eb = gb_depth(g, ix, iy);
+    if (!is_surface(eb)) continue;
+    if (eb <= eS - p.bias) occ += smoothstep01(p.radius / fabsf(e - eb));
+  }
+  *out = 1.0f - occ / p.K;
+}
+
+template <int FMT>
+__global__ void __launch_bounds__(256) k_ssao_blur(GbufDev g, SsaoDev p, const float* __restrict__ in,
+                                                   long long in_pitch, float* __restrict__ out,
+                                                   long long out_pitch, int Wa, int Ha) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y;
+  if (i >= Wa || j >= Ha) return;
+  float* o = (float*)((char*)out + (size_t)j * out_pitch) + i;
+  float ep = gb_depth(g, p.scale * i, p.scale * j);
+  if (!is_surface(ep)) {
+    *o = 1.0f;
+    return;
+  }
+  float ks = 1.0f / (2.0f * p.sigma_s * p.sigma_s);
+  float kz = 1.0f / (p.sigma_z * ep);
+  float num = 0.0f, den = 0.0f;
+  for (int dy = -p.R; dy <= p.R; ++dy) {
+    int qj = j + dy;
+    if (qj < 0 || qj >= Ha) continue;
+    const float* row = (const float*)((const char*)in + (size_t)qj * in_pitch);
+    for (int dx = -p.R; dx <= p.R; ++dx) {
+      int qi = i + dx;
+      if (qi < 0 || qi >= Wa) continue;
+      float eq = gb_depth(g, p.scale * qi, p.scale * qj);
+      if (!is_surface(eq)) continue;
+      float w = expf(-fmaf((float)(dx * dx + dy * dy), ks, fabsf(eq - ep) * kz));
+      num = fmaf(w, __ldg(row + qi), num);
+      den += w;
+    }
+  }
+  *o = num / den;
+}
+
+static epbr_status validate_ssao(const epbr_ssao_params* p) {
+  if (!p) return fail(EPBR_ERR_INVALID_ARG, "ssao params is NULL");
+  if (p->num_samples < 1 || p->num_samples > kMaxSsaoSamples)
+    return fail(EPBR_ERR_INVALID_ARG, "ssao num_samples %d outside [1, %d]", p->num_samples, kMaxSsaoSamples);
+  if (p->scale != 1 && p->scale != 2) return fail(EPBR_ERR_INVALID_ARG, "ssao scale must be 1 or 2");
+  if (!(p->radius > 0.0f) || !(p->bias >= 0.0f) || !(p->sigma_s > 0.0f) || !(p->sigma_z > 0.0f))
+    return fail(EPBR_ERR_INVALID_ARG, "ssao radius/bias/sigmas invalid");
+  if (p->blur_radius < 0 || p->blur_radius > 8) return fail(EPBR_ERR_INVALID_ARG, "ssao blur_radius outside [0, 8]");
+  if (!p->kernel || !p->noise || (uintptr_t)p->kernel % 16 || (uintptr_t)p->noise % 8)
+    return fail(EPBR_ERR_INVALID_ARG, "ssao kernel/noise NULL or misaligned");
+  return EPBR_OK;
+}
+
+static SsaoDev make_ssao(const epbr_ssao_params* p) {
+  SsaoDev d;
+  d.K = p->num_samples;
+  d.scale = p->scale;
+  d.R = p->blur_radius;
+  d.radius = p->radius;
+  d.bias = p->bias;
+  d.sigma_s = p->sigma_s;
+  d.sigma_z = p->sigma_z;
+  d.kernel = (const float4*)p->kernel;
+  d.noise = (const float2*)p->noise;
+  return d;
+}
+
+static void ao_dims(const epbr_gbuffer* g, const epbr_ssao_params* p, int* w, int* h) {
+  *w = (g->width + p->scale - 1) / p->scale;
+  *h = (g->height + p->scale - 1) / p->scale;
+}
+
+static epbr_status check_ao_buffer(const void* ao, int64_t pitch, int Wa, const char* what) {
+  if (!ao || (uintptr_t)ao % 4 || pitch < (int64_t)Wa * 4 || pitch % 4)
+    return fail(EPBR_ERR_INVALID_ARG, "%s: AO buffer NULL, misaligned or pitch too small", what);
+  return EPBR_OK;
+}
+
+}  // namespace epbr
+
+using namespace epbr;
+
+extern "C" epbr_status epbr_ssao_size(const epbr_gbuffer* g, const epbr_ssao_params* p, int32_t* w, int32_t* h) {
+  epbr_status st = validate_gbuffer(g, false);
+  if (st) return st;
+  if ((st = validate_ssao(p))) return st;
+  if (!w || !h) return fail(EPBR_ERR_INVALID_ARG, "output pointers NULL");
+  ao_dims(g, p, w, h);
+  return ok();
+}
+
+extern "C" epbr_status epbr_ssao_workspace_size(const epbr_gbuffer* g, const epbr_ssao_params* p, size_t* bytes) {
+  int w, h;
+  epbr_status st = epbr_ssao_size(g, p, &w, &h);
+  if (st) return st;
+  if (!bytes) return fail(EPBR_ERR_INVALID_ARG, "bytes is NULL");
+  *bytes = (size_t)w * h * 4;
+  return ok();
+}
+
+extern "C" epbr_status epbr_ssao_raw(const epbr_gbuffer* g, const epbr_camera* cam, const epbr_ssao_params* p,
+                                     float* ao, int64_t ao_pitch, void* stream) {
+  epbr_status st = validate_gbuffer(g, false);
+  if (st) return st;
+  if ((st = validate_camera(cam, g))) return st;
+  if ((st = validate_ssao(p))) return st;
+  int Wa, Ha;
+  ao_dims(g, p, &Wa, &Ha);
+  if ((st = check_ao_buffer(ao, ao_pitch, Wa, "ssao_raw"))) return st;
+  dim3 blk(32, 8), grd((Wa + 31) / 32, (Ha + 7) / 8);
+  GbufDev gd = make_gbuf(*g);
+  CamDev cd = make_cam(*cam);
+  SsaoDev sd = make_ssao(p);
+  cudaStream_t s = (cudaStream_t)stream;
+  if (g->format == EPBR_GBUFFER_FP32)
+    k_ssao_raw<EPBR_GBUFFER_FP32><<<grd, blk, 0, s>>>(gd, cd, sd, ao, ao_pitch, Wa, Ha);
+  else
+    k_ssao_raw<EPBR_GBUFFER_COMPACT><<<grd, blk, 0, s>>>(gd, cd, sd, ao, ao_pitch, Wa, Ha);
+  if ((st = check_launch("k_ssao_raw"))) return st;
+  return ok();
+}
+
+extern "C" epbr_status epbr_ssao_blur(const epbr_gbuffer* g, const epbr_ssao_params* p, const float* in,
+                                      int64_t in_pitch, float* out, int64_t out_pitch, void* stream) {
+  epbr_status st = validate_gbuffer(g, false);
+  if (st) return st;
+  if ((st = validate_ssao(p))) return st;
+  int Wa, Ha;
+  ao_dims(g, p, &Wa, &Ha);
+  if ((st = check_ao_buffer(in, in_pitch, Wa, "ssao_blur in"))) return st;
+  if ((st = check_ao_buffer(out, out_pitch, Wa, "ssao_blur out"))) return st;
+  if (in == out) return fail(EPBR_ERR_INVALID_ARG, "ssao_blur: in and out must differ");
+  dim3 blk(32, 8), grd((Wa + 31) / 32, (Ha + 7) / 8);
+  GbufDev gd = make_gbuf(*g);
+  SsaoDev sd = make_ssao(p);
+  cudaStream_t s = (cudaStream_t)stream;
+  if (g->format == EPBR_GBUFFER_FP32)
+    k_ssao_blur<EPBR_GBUFFER_FP32><<<grd, blk, 0, s>>>(gd, sd, in, in_pitch, out, out_pitch, Wa, Ha);
+  else
+    k_ssao_blur<EPBR_GBUFFER_COMPACT><<<grd, blk, 0, s>>>(gd, sd, in, in_pitch, out, out_pitch, Wa, Ha);
+  if ((st = check_launch("k_ssao_blur"))) return st;
+  return ok();
+}
+
+extern "C" epbr_status epbr_ssao(const epbr_gbuffer* g, const epbr_camera* cam, const epbr_ssao_params* p,
+                                 float* ao, int64_t ao_pitch, void* ws, size_t ws_bytes, void* stream) {
+  int Wa, Ha;
+  epbr_status st = epbr_ssao_size(g, p, &Wa, &Ha);
+  if (st) return st;
+  if (p->blur_radius == 0) return epbr_ssao_raw(g, cam, p, ao, ao_pitch, stream);
+  size_t need = (size_t)Wa * Ha * 4;
+  if (!ws || ws_bytes < need || (uintptr_t)ws % 4)
+    return fail(EPBR_ERR_NO_MEMORY, "ssao: workspace needs %zu bytes, got %zu", need, ws ? ws_bytes : (size_t)0);
+  if ((st = epbr_ssao_raw(g, cam, p, (float*)ws, (int64_t)Wa * 4, stream))) return st;
+  return epbr_ssao_blur(g, p, (const float*)ws, (int64_t)Wa * 4, ao, ao_pitch, stream);
+}

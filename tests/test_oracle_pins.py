@@ -526,3 +526,8 @@ def test_brdf_geometry_term_isolated():
         f2 = oracle.brdf(n, l2, v2, a, 1.0, rough) * (l2 @ n) * (v2 @ n)
         exp = g1(l1 @ n) * g1(v1 @ n) / (g1(l2 @ n) * g1(v2 @ n))
         assert np.allclose(f1 / f2, exp, rtol=1e-12)
+
+
+def test_tonemap_infinite_input_saturates():
+    out, _ = oracle.tonemap(np.array([[np.inf, 1e30, 2e6]]), 1.0, 0)
+    assert (out[0, :3] == 255).all()
