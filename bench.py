@@ -36,8 +36,8 @@ L2_FLUSH_BYTES = 256 << 20  # larger than the 129 MB L2
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
-    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="epbr", choices=["epbr", "reference"])
     ap.add_argument("--workload", default=WORKLOAD, choices=sorted(synth.CONFIGS))
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="CPU-baseline time budget")
@@ -115,28 +115,39 @@ def compose_flops(sc, g, n_lights) -> tuple[float, dict]:
 # clocks during the timed region
 # ------------------------------------------------------------------------------------------
 class ClockSampler:
-    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+    """nvidia-smi sampled every 50 ms in the background; summary() keeps the samples whose
+    timestamps fall inside the window set by mark_start()/mark_end()."""
+    FIELDS = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
     def __init__(self, gpu_index: int):
         self.idx = gpu_index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv") if os.path.isdir(
-            os.path.join(ROOT, "gpurun_out")) else f"/tmp/epbr_clocks_{os.getpid()}.csv"
+        self.t0 = self.t1 = None
+        out = os.path.join(ROOT, "gpurun_out")
+        self.path = os.path.join(out if os.path.isdir(out) else "/tmp", f"clocks_{os.getpid()}.csv")
 
     def __enter__(self):
+        self.f = open(self.path, "w")
         try:
-            self.f = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.FIELDS}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                                          "--format=csv,noheader,nounits", "-lms", "50"], stdout=self.f,
                                          stderr=subprocess.DEVNULL)
+            time.sleep(0.5)  # let the sampler start before the timed region
         except (OSError, FileNotFoundError):
             self.proc = None
         return self
 
+    def mark_start(self):
+        self.t0 = time.time()
+
+    def mark_end(self):
+        self.t1 = time.time()
+
     def __exit__(self, *a):
         if self.proc:
+            time.sleep(0.1)
             self.proc.terminate()
             try:
                 self.proc.wait(timeout=5)
@@ -145,6 +156,7 @@ class ClockSampler:
         self.f.close()
 
     def summary(self):
+        import datetime as dt
         try:
             lines = [l.strip() for l in open(self.path) if l.strip()]
         except OSError:
@@ -153,14 +165,18 @@ class ClockSampler:
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         for l in lines:
             p = [x.strip() for x in l.split(",")]
-            if len(p) < 9:
+            if len(p) < 10:
                 continue
             try:
-                sm.append(float(p[1]))
-                mx.append(float(p[2]))
+                ts = dt.datetime.strptime(p[0], "%Y/%m/%d %H:%M:%S.%f").timestamp()
+                clk, cmax = float(p[2]), float(p[3])
             except ValueError:
                 continue
-            for nme, v in zip(names, p[5:9]):
+            if self.t0 is not None and not (self.t0 - 0.06 <= ts <= (self.t1 or ts) + 0.06):
+                continue
+            sm.append(clk)
+            mx.append(cmax)
+            for nme, v in zip(names, p[6:10]):
                 if v.lower().startswith("active"):
                     reasons.add(nme)
         if not sm:
@@ -343,8 +359,9 @@ def run_gpu(args):
         dist.barrier()
     torch.cuda.synchronize()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    wall0 = time.perf_counter()
     with ClockSampler(local_rank) as clk:
+        clk.mark_start()
+        wall0 = time.perf_counter()
         with torch.cuda.stream(stream):
             for i in range(args.steps):
                 flush.zero_()  # L2 flush, outside the timed events
@@ -353,7 +370,8 @@ def run_gpu(args):
                 ev[i][1].record(stream)
         stream.synchronize()
         torch.cuda.synchronize()
-    wall = time.perf_counter() - wall0
+        wall = time.perf_counter() - wall0
+        clk.mark_end()
     step_ms = [a.elapsed_time(b) for a, b in ev]
     total_ms = sum(step_ms)
     shade_ms = statistics.mean(a.elapsed_time(b) for a, b in ev_shade)

@@ -180,7 +180,8 @@ epbr_status epbr_brdf_lut(int32_t lut_size, int32_t num_samples, float* lut, voi
 /* Diffuse irradiance map: for output texel direction n,
  *   out(n) = sum_t L_t max(n.d_t, 0) Omega_t / sum_t max(n.d_t, 0) Omega_t
  * over every source texel t (exact row solid angle Omega_t), i.e. E(n)/pi as a ratio
- * estimator, exact for a uniform environment.  `out` is DEVICE float4[irr_h][irr_w].
+ * estimator, exact for a uniform environment (0 where no texel centre lies in the hemisphere
+ * of n, which only maps of one or two columns allow).  `out` is DEVICE float4[irr_h][irr_w].
  * `workspace` as for epbr_precompute_ibl. */
 epbr_status epbr_irradiance(const epbr_env* env, int32_t irr_width, int32_t irr_height,
                             float* out, void* workspace, size_t workspace_bytes, void* stream);

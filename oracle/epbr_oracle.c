@@ -284,7 +284,9 @@ static void irr_body(void* p, long i0, long i1) {
         den += w;
       }
     }
-    for (int q = 0; q < 3; ++q) c->out[t * 3 + q] = num[q] / den;
+    /* A direction whose hemisphere holds no texel centre (maps of one or two columns) makes
+     * the ratio 0/0; it is defined as 0 (no light arrives).  A reading: Sec. 3.1 is silent. */
+    for (int q = 0; q < 3; ++q) c->out[t * 3 + q] = den > 0.0 ? num[q] / den : 0.0;
   }
 }
 

@@ -127,6 +127,29 @@ __device__ __forceinline__ void onb(float3 n, float3& t, float3& b) {
   b = f3(c, fmaf(n.y * n.y, a, s), -n.y);
 }
 
+// Hardware approximations with denormal flushing (one MUFU instruction each, no fix-up code):
+// relative error ~2^-22, far inside the 1e-4 tolerance of the method.
+__device__ __forceinline__ float rsqrt_ftz(float x) {
+  float r;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+__device__ __forceinline__ float rcp_ftz(float x) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+__device__ __forceinline__ float ex2_ftz(float x) {
+  float r;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+__device__ __forceinline__ float lg2_ftz(float x) {
+  float r;
+  asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+
 // Kahan-compensated accumulator.
 struct Kahan {
   float s = 0.0f, c = 0.0f;

@@ -164,7 +164,7 @@ __global__ void k_irradiance_final(const float4* __restrict__ part, int nblocks,
     s[3].add(p.w);
   }
   float den = s[3].s - s[3].c;
-  float inv = 1.0f / den;
+  float inv = den > 0.0f ? 1.0f / den : 0.0f;  // no texel centre in the hemisphere: 0
   out[o] = make_float4((s[0].s - s[0].c) * inv, (s[1].s - s[1].c) * inv, (s[2].s - s[2].c) * inv, 1.0f);
 }
 

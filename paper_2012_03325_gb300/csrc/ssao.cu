@@ -2,7 +2,8 @@
 // Sainz 2008, at half resolution, then a bilateral blur).
 //   k_ssao_raw   one thread per AO texel; the K kernel offsets sit in shared memory and the
 //                depth taps go through the read-only cache
-//   k_ssao_blur  one thread per AO texel; (2R+1)^2 depth-aware taps
+//   k_ssao_blur  one thread per AO texel; (2R+1)^2 depth-aware taps read from a shared-memory
+//                tile of AO values and depths with an R-texel halo
 #include "epbr_internal.cuh"
 
 namespace epbr {
@@ -56,44 +57,65 @@ __global__ void __launch_bounds__(256) k_ssao_raw(GbufDev g, CamDev cam, SsaoDev
     float3 S = P + p.radius * (t * ks.x + b * ks.y + n * ks.z);
     float eS = -S.z;
     if (!(eS > 0.0f)) continue;
-    float inv = 1.0f / eS;
+    float inv = rcp_ftz(eS);
     float x = fmaf(S.x * inv, ix_scale, 0.5f * cam.W);
     float y = fmaf(-S.y * inv, iy_scale, 0.5f * cam.H);
     if (!(x >= 0.0f && x < (float)cam.W && y >= 0.0f && y < (float)cam.H)) continue;
     int ix = min((int)x, cam.W - 1), iy = min((int)y, cam.H - 1);
     float eb = gb_depth(g, ix, iy);
     if (!is_surface(eb)) continue;
-    if (eb <= eS - p.bias) occ += smoothstep01(p.radius / fabsf(e - eb));
+    if (eb <= eS - p.bias) occ += smoothstep01(p.radius * rcp_ftz(fabsf(e - eb)));
   }
   *out = 1.0f - occ / p.K;
 }
 
+// Blur tile: 32x8 AO texels plus a halo of R <= 8 texels, AO values and the depths of their
+// source pixels staged in shared memory (taps outside the image are staged as background).
+constexpr int kBlurBX = 32, kBlurBY = 8, kBlurMaxR = 8;
+constexpr int kBlurTW = kBlurBX + 2 * kBlurMaxR, kBlurTH = kBlurBY + 2 * kBlurMaxR;
+
 template <int FMT>
-__global__ void __launch_bounds__(256) k_ssao_blur(GbufDev g, SsaoDev p, const float* __restrict__ in,
-                                                   long long in_pitch, float* __restrict__ out,
-                                                   long long out_pitch, int Wa, int Ha) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y;
+__global__ void __launch_bounds__(kBlurBX* kBlurBY) k_ssao_blur(GbufDev g, SsaoDev p, const float* __restrict__ in,
+                                                                long long in_pitch, float* __restrict__ out,
+                                                                long long out_pitch, int Wa, int Ha) {
+  __shared__ float s_ao[kBlurTH][kBlurTW];
+  __shared__ float s_e[kBlurTH][kBlurTW];
+  const int R = p.R;
+  const int tw = kBlurBX + 2 * R, th = kBlurBY + 2 * R;
+  const int i0 = blockIdx.x * kBlurBX - R, j0 = blockIdx.y * kBlurBY - R;
+  const float inf = __int_as_float(0x7f800000);
+  for (int q = threadIdx.y * kBlurBX + threadIdx.x; q < tw * th; q += kBlurBX * kBlurBY) {
+    int ty = q / tw, tx = q - ty * tw;
+    int qi = i0 + tx, qj = j0 + ty;
+    float a = 0.0f, e = inf;
+    if (qi >= 0 && qi < Wa && qj >= 0 && qj < Ha) {
+      a = __ldg((const float*)((const char*)in + (size_t)qj * in_pitch) + qi);
+      e = gb_depth(g, p.scale * qi, p.scale * qj);
+    }
+    s_ao[ty][tx] = a;
+    s_e[ty][tx] = e;
+  }
+  __syncthreads();
+  int i = blockIdx.x * kBlurBX + threadIdx.x, j = blockIdx.y * kBlurBY + threadIdx.y;
   if (i >= Wa || j >= Ha) return;
   float* o = (float*)((char*)out + (size_t)j * out_pitch) + i;
-  float ep = gb_depth(g, p.scale * i, p.scale * j);
+  float ep = s_e[threadIdx.y + R][threadIdx.x + R];
   if (!is_surface(ep)) {
     *o = 1.0f;
     return;
   }
-  float ks = 1.0f / (2.0f * p.sigma_s * p.sigma_s);
-  float kz = 1.0f / (p.sigma_z * ep);
+  // w = exp(-(dx^2 + dy^2) / (2 sigma_s^2)) * exp(-|e_q - e_p| / (sigma_z e_p)), one exponential
+  float ks = -1.4426950408889634f / (2.0f * p.sigma_s * p.sigma_s);
+  float kz = -1.4426950408889634f / (p.sigma_z * ep);
   float num = 0.0f, den = 0.0f;
-  for (int dy = -p.R; dy <= p.R; ++dy) {
-    int qj = j + dy;
-    if (qj < 0 || qj >= Ha) continue;
-    const float* row = (const float*)((const char*)in + (size_t)qj * in_pitch);
-    for (int dx = -p.R; dx <= p.R; ++dx) {
-      int qi = i + dx;
-      if (qi < 0 || qi >= Wa) continue;
-      float eq = gb_depth(g, p.scale * qi, p.scale * qj);
+  for (int dy = -R; dy <= R; ++dy) {
+    const float* ra = &s_ao[threadIdx.y + R + dy][threadIdx.x + R];
+    const float* re = &s_e[threadIdx.y + R + dy][threadIdx.x + R];
+    for (int dx = -R; dx <= R; ++dx) {
+      float eq = re[dx];
       if (!is_surface(eq)) continue;
-      float w = expf(-fmaf((float)(dx * dx + dy * dy), ks, fabsf(eq - ep) * kz));
-      num = fmaf(w, __ldg(row + qi), num);
+      float w = exp2f(fmaf((float)(dx * dx + dy * dy), ks, fabsf(eq - ep) * kz));
+      num = fmaf(w, ra[dx], num);
       den += w;
     }
   }
@@ -192,7 +214,7 @@ extern "C" epbr_status epbr_ssao_blur(const epbr_gbuffer* g, const epbr_ssao_par
   if ((st = check_ao_buffer(in, in_pitch, Wa, "ssao_blur in"))) return st;
   if ((st = check_ao_buffer(out, out_pitch, Wa, "ssao_blur out"))) return st;
   if (in == out) return fail(EPBR_ERR_INVALID_ARG, "ssao_blur: in and out must differ");
-  dim3 blk(32, 8), grd((Wa + 31) / 32, (Ha + 7) / 8);
+  dim3 blk(kBlurBX, kBlurBY), grd((Wa + kBlurBX - 1) / kBlurBX, (Ha + kBlurBY - 1) / kBlurBY);
   GbufDev gd = make_gbuf(*g);
   SsaoDev sd = make_ssao(p);
   cudaStream_t s = (cudaStream_t)stream;

@@ -34,7 +34,8 @@ def test_brdf_lut(S, N):
     assert err.max() <= REL_TOL_FP32, err.max()
 
 
-@pytest.mark.parametrize("We,He,Wi,Hi", [(128, 64, 32, 16), (100, 37, 7, 5), (64, 32, 40, 30), (1, 1, 2, 1)])
+@pytest.mark.parametrize("We,He,Wi,Hi", [(128, 64, 32, 16), (100, 37, 7, 5), (64, 32, 40, 30), (1, 1, 1, 1),
+                                         (3, 2, 2, 1)])
 def test_irradiance(We, He, Wi, Hi):
     import synth
     env = synth.make_env(11, We, He)

@@ -531,3 +531,12 @@ def test_brdf_geometry_term_isolated():
 def test_tonemap_infinite_input_saturates():
     out, _ = oracle.tonemap(np.array([[np.inf, 1e30, 2e6]]), 1.0, 0)
     assert (out[0, :3] == 255).all()
+
+
+def test_irradiance_single_texel_map():
+    """A 1x1 map has its only texel centre at -z; the 1x1 irradiance map looks along -z and sees
+    exactly that texel."""
+    env = np.ones((1, 1, 4))
+    env[0, 0, :3] = (0.25, 0.5, 2.0)
+    out = oracle.irradiance(env, 1, 1)
+    assert np.allclose(out[0, 0], (0.25, 0.5, 2.0), rtol=1e-12)
