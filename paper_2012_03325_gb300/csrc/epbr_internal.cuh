@@ -90,9 +90,15 @@ struct MapDev {
   int W, H;
 };
 
+__device__ __forceinline__ float sqrt_ftz(float x) {
+  float r;
+  asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+
 __device__ __forceinline__ void dir_to_uv(float3 d, float& u, float& v) {
   u = fmaf(atan2f(d.x, -d.z), kInv2Pi, 0.5f);
-  v = atan2f(sqrtf(fmaf(d.x, d.x, d.z * d.z)), d.y) * kInvPi;
+  v = atan2f(sqrt_ftz(fmaf(d.x, d.x, d.z * d.z)), d.y) * kInvPi;
 }
 
 // Bilinear read at (u, v): wrap in u, clamp in v.

@@ -6,35 +6,49 @@
 //   k_tonemap  ACES / Reinhard + sRGB transfer, 8-bit output
 #include <string.h>
 
+#include <algorithm>
+
 #include "shade_core.cuh"
 
 namespace epbr {
 
 constexpr int kShadeBX = 32, kShadeBY = 8;
+#ifndef EPBR_SHADE_MIN_BLOCKS
+#define EPBR_SHADE_MIN_BLOCKS 4  // resident 256-thread blocks per SM the register budget targets
+#endif
 
+// One thread per pixel of a 32x8 tile.  The G-buffer loads are issued before the lights are
+// staged so that they are in flight during the staging barrier.  Lights are staged in chunks of
+// 256; a chunk whose lights are all monochrome takes the one-sum-per-term loop.
 template <int FMT, int HDR, bool LDR>
-__global__ void __launch_bounds__(kShadeBX* kShadeBY) k_shade(GbufDev g, CamDev cam, const float4* __restrict__ lights,
-                                                              int NL, IblDev ibl, ShadeDev p, void* hdr,
-                                                              long long hdr_pitch, uint8_t* ldr, long long ldr_pitch) {
+__global__ void __launch_bounds__(kShadeBX* kShadeBY, EPBR_SHADE_MIN_BLOCKS)
+    k_shade(GbufDev g, CamDev cam, const float4* __restrict__ lights, int NL, IblDev ibl, ShadeDev p, void* hdr,
+            long long hdr_pitch, uint8_t* ldr, long long ldr_pitch) {
   __shared__ float4 s_lights[2 * kLightChunk];
   int tid = threadIdx.y * kShadeBX + threadIdx.x;
   int x = blockIdx.x * kShadeBX + threadIdx.x, y = blockIdx.y * kShadeBY + threadIdx.y;
   bool inside = x < g.W && y < g.H;
+  PxRaw raw;
+  if (inside) raw = px_load<FMT>(g, x, y);
+  bool mono = false;
+  if (NL <= kLightChunk) mono = __syncthreads_and(stage_lights(s_lights, lights, 0, NL, tid, kShadeBX * kShadeBY));
   Px s;
-  if (inside) s = px_setup<FMT>(g, cam, x, y);
+  if (inside) s = px_decode<FMT>(raw, cam, x, y);
   bool active = inside && s.surface;
   bool diffuse_only = (p.flags & EPBR_SHADE_DIFFUSE_ONLY) != 0;
   Direct d;
   if (active) d = px_direct_begin(s);
-  // every thread takes part in staging each chunk of lights
   for (int base = 0; base < NL; base += kLightChunk) {
     int cnt = min(kLightChunk, NL - base);
-    __syncthreads();
-    stage_lights(s_lights, lights, base, cnt, tid, kShadeBX * kShadeBY);
-    __syncthreads();
+    if (NL > kLightChunk) {
+      __syncthreads();
+      mono = __syncthreads_and(stage_lights(s_lights, lights, base, cnt, tid, kShadeBX * kShadeBY));
+    }
     if (active) {
       if (diffuse_only)
         px_direct_diffuse(s, d, s_lights, cnt);
+      else if (mono)
+        px_direct_mono(s, d, s_lights, cnt);
       else
         px_direct(s, d, s_lights, cnt);
     }

@@ -44,8 +44,8 @@ struct ShadeDev {
 // clamp to [0, 1], sRGB transfer (IEC 61966-2-1), round half up to 8 bits.
 __device__ __forceinline__ unsigned tonemap_channel(float x, float exposure, int op) {
   x = fminf(fmaxf(x * exposure, 0.0f), 1e6f);
-  float y = (op == EPBR_TONEMAP_REINHARD) ? x / (1.0f + x)
-                                          : x * fmaf(2.51f, x, 0.03f) / fmaf(x, fmaf(2.43f, x, 0.59f), 0.14f);
+  float y = (op == EPBR_TONEMAP_REINHARD) ? x * rcp_ftz(1.0f + x)
+                                          : x * fmaf(2.51f, x, 0.03f) * rcp_ftz(fmaf(x, fmaf(2.43f, x, 0.59f), 0.14f));
   y = clamp01(y);
   // y^(1/2.4) as 2^(log2(y) / 2.4) (relative error ~1e-6, i.e. < 3e-4 of an 8-bit step)
   float s = y <= 0.0031308f ? 12.92f * y : fmaf(1.055f, ex2_ftz(lg2_ftz(y) * (1.0f / 2.4f)), -0.055f);
@@ -108,32 +108,51 @@ struct Px {
   bool surface;
 };
 
+// Raw G-buffer texel of one pixel, loaded before it is decoded (lets the loads of a block be in
+// flight while its lights are staged).
+struct PxRaw {
+  float e;
+  float4 a, b;  // FP32: rt0, rt1.  COMPACT: a.x = rt0 bits, a.y = rt1 bits, a.z = rt2 bits
+};
+
 template <int FMT>
-__device__ __forceinline__ Px px_setup(const GbufDev& g, const CamDev& cam, int x, int y) {
+__device__ __forceinline__ PxRaw px_load(const GbufDev& g, int x, int y) {
+  PxRaw r;
+  r.e = gb_depth(g, x, y);
+  if (FMT == EPBR_GBUFFER_FP32) {
+    r.a = __ldg((const float4*)(g.rt[0] + (size_t)y * g.pitch[0]) + x);
+    r.b = __ldg((const float4*)(g.rt[1] + (size_t)y * g.pitch[1]) + x);
+  } else {
+    r.a.x = __uint_as_float(__ldg((const unsigned*)(g.rt[0] + (size_t)y * g.pitch[0]) + x));
+    r.a.y = __uint_as_float(__ldg((const unsigned*)(g.rt[1] + (size_t)y * g.pitch[1]) + x));
+    r.a.z = __uint_as_float((unsigned)__ldg((const unsigned short*)(g.rt[2] + (size_t)y * g.pitch[2]) + x));
+  }
+  return r;
+}
+
+template <int FMT>
+__device__ __forceinline__ Px px_decode(const PxRaw& r, const CamDev& cam, int x, int y) {
   Px s;
-  float e = gb_depth(g, x, y);
   float3 dw = rot(cam, view_ray(cam, x, y));
   s.acc = f3(0, 0, 0);
-  s.surface = is_surface(e);
-  s.v = normalize3(dw) * -1.0f;  // v = (eye - P) / |eye - P| with P = eye + e * dw
+  s.surface = is_surface(r.e);
+  s.v = dw * -rsqrt_ftz(dot3(dw, dw));  // v = (eye - P) / |eye - P| with P = eye + e * dw
   if (!s.surface) {
     s.P = dw;  // background: keep the view ray for the environment lookup
     return s;
   }
-  s.P = f3(cam.eye[0], cam.eye[1], cam.eye[2]) + e * dw;
-  s.n = gb_normal<FMT>(g, x, y);
+  s.P = f3(cam.eye[0], cam.eye[1], cam.eye[2]) + r.e * dw;
   if (FMT == EPBR_GBUFFER_FP32) {
-    float4 a = __ldg((const float4*)(g.rt[0] + (size_t)y * g.pitch[0]) + x);
-    float r = __ldg((const float4*)(g.rt[1] + (size_t)y * g.pitch[1]) + x).w;
-    s.albedo = xyz(a);
-    s.metal = a.w;
-    s.rough = r;
+    s.n = normalize3(xyz(r.b));
+    s.albedo = xyz(r.a);
+    s.metal = r.a.w;
+    s.rough = r.b.w;
   } else {
-    uchar4 a = __ldg((const uchar4*)(g.rt[0] + (size_t)y * g.pitch[0]) + x);
-    uchar2 mr = __ldg((const uchar2*)(g.rt[2] + (size_t)y * g.pitch[2]) + x);
-    s.albedo = f3(c_srgb8[a.x], c_srgb8[a.y], c_srgb8[a.z]);
-    s.metal = mr.x * (1.0f / 255.0f);
-    s.rough = mr.y * (1.0f / 255.0f);
+    unsigned a = __float_as_uint(r.a.x), nb = __float_as_uint(r.a.y), mr = __float_as_uint(r.a.z);
+    s.n = oct_decode(*reinterpret_cast<const __half2*>(&nb));
+    s.albedo = f3(c_srgb8[a & 255u], c_srgb8[(a >> 8) & 255u], c_srgb8[(a >> 16) & 255u]);
+    s.metal = (mr & 255u) * (1.0f / 255.0f);
+    s.rough = (mr >> 8) * (1.0f / 255.0f);
   }
   s.metal = clamp01(s.metal);
   s.rough = fminf(fmaxf(s.rough, kRoughMin), 1.0f);
@@ -142,15 +161,26 @@ __device__ __forceinline__ Px px_setup(const GbufDev& g, const CamDev& cam, int 
   return s;
 }
 
-// Lights staged in shared memory as pairs (pos.xyz, -), (intensity * color.rgb, -).
-__device__ __forceinline__ void stage_lights(float4* s_lights, const float4* __restrict__ lights, int first,
+template <int FMT>
+__device__ __forceinline__ Px px_setup(const GbufDev& g, const CamDev& cam, int x, int y) {
+  return px_decode<FMT>(px_load<FMT>(g, x, y), cam, x, y);
+}
+
+// Lights staged in shared memory as pairs (pos.xyz, -), (intensity * color.rgb, -).  Returns
+// whether every light this thread staged is monochrome (equal colour channels); callers combine
+// the flags with __syncthreads_and to pick the monochrome loop for the chunk.
+__device__ __forceinline__ bool stage_lights(float4* s_lights, const float4* __restrict__ lights, int first,
                                              int cnt, int tid, int nthreads) {
+  bool mono = true;
   for (int q = tid; q < cnt; q += nthreads) {
     float4 a = __ldg(lights + 2 * (first + q));
     float4 c = __ldg(lights + 2 * (first + q) + 1);
     s_lights[2 * q] = make_float4(a.x, a.y, a.z, 0.0f);
-    s_lights[2 * q + 1] = make_float4(a.w * c.x, a.w * c.y, a.w * c.z, 0.0f);
+    float4 ic = make_float4(a.w * c.x, a.w * c.y, a.w * c.z, 0.0f);
+    s_lights[2 * q + 1] = ic;
+    mono = mono && ic.x == ic.y && ic.y == ic.z;
   }
+  return mono;
 }
 
 // Direct light of one pixel, accumulated over chunks of staged lights.  With
@@ -158,9 +188,12 @@ __device__ __forceinline__ void stage_lights(float4* s_lights, const float4* __r
 // the contribution w Ic_c [cdiff_c/pi (1 - F_c) + spec F_c] of a light (w = (n.l)/d^2) is
 //   Ic_c [K_c (w (1 - fc)) + F0_c (w spec) + (1 - F0_c)(w spec fc)],  K_c = cdiff_c/pi (1 - F0_c),
 // so the loop keeps three sums per channel of Ic_c times light scalars and the per-channel
-// material factors are applied once per pixel (px_direct_end).
+// material factors are applied once per pixel (px_direct_end).  spec is accumulated without
+// its per-pixel factor alpha^2 G1(v) / (4 pi n.v), applied at the end as well.  For a chunk of
+// monochrome lights (Ic_r = Ic_g = Ic_b) the three channels share one sum each.
 struct Direct {
-  float3 sa, sb, sbf;  // sums of Ic w (1 - fc), Ic w spec, Ic w spec fc
+  float3 sa, sb, sbf;  // sums of Ic w (1 - fc), Ic w spec', Ic w spec' fc
+  float3 nxv;          // n x v: n x (l + v) = (n x L) / |L| + n x v
   float a2vv, a2, k, omk;
 };
 
@@ -171,48 +204,78 @@ __device__ __forceinline__ Direct px_direct_begin(const Px& s) {
   d.a2 = alpha * alpha;
   d.k = (s.rough + 1.0f) * (s.rough + 1.0f) * 0.125f;
   d.omk = 1.0f - d.k;
-  d.a2vv = d.a2 / (4.0f * kPi * fmaf(s.nv, d.omk, d.k));  // alpha^2 G1(v) / (4 pi n.v)
+  d.a2vv = d.a2 * rcp_ftz(4.0f * kPi * fmaf(s.nv, d.omk, d.k));  // alpha^2 G1(v) / (4 pi n.v)
+  d.nxv = cross3(s.n, s.v);
   return d;
 }
 
-// Adds `cnt` staged lights.  Guards are folded into existing FMAs: |L|^2 + 1e-30 (a light at P
-// contributes 0), |n x s|^2 + 1e-18 (keeps the GGX denominator normal when l = -v), and
-// |l + v|^2 biased by 1e-6 (>= 0 under rounding); each changes a result by < 1e-12 relative.
+// Scalar light terms shared by both loops.  Guards are folded into existing FMAs: |L|^2 + 1e-30
+// (a light at P contributes 0), |n x s|^2 + 1e-18 (keeps the GGX denominator normal when
+// l = -v), and |l + v|^2 biased by 1e-6 (>= 0 under rounding); each changes a result by less
+// than 1e-12 relative.
+struct LightTerms {
+  float a, b, bf;
+};
+
+__device__ __forceinline__ LightTerms light_terms(const Px& s, const Direct& d, float4 lp) {
+  float3 L = xyz(lp) - s.P;
+  float d2 = fmaf(L.x, L.x, fmaf(L.y, L.y, fmaf(L.z, L.z, 1e-30f)));
+  float rs = rsqrt_ftz(d2);
+  float nl = dot3(s.n, L) * rs;
+  float nlc = fmaxf(nl, 0.0f);
+  float lv = dot3(s.v, L) * rs;
+  float3 c = cross3(s.n, L) * rs + d.nxv;  // n x (l + v)
+  float c2 = fmaf(c.x, c.x, fmaf(c.y, c.y, fmaf(c.z, c.z, 1e-18f)));
+  float ns = nl + s.nv_raw;
+  float hh = fmaf(2.0f, lv, 2.000001f);
+  float den = fmaf(ns * ns, d.a2, c2);
+  float xx = fmaf(-0.5f * hh, rsqrt_ftz(hh), 1.0f);  // 1 - v.h, v.h = |l + v| / 2
+  float x2 = xx * xx, fc = x2 * x2 * xx;
+  float w = rs * rs * nlc;  // (n.l) / d^2
+  float spec = hh * hh * rcp_ftz(den * den * fmaf(nlc, d.omk, d.k));
+  LightTerms t;
+  t.a = fmaf(-w, fc, w);
+  t.b = w * spec;
+  t.bf = t.b * fc;
+  return t;
+}
+
+// Adds `cnt` staged lights with arbitrary colours.
 __device__ __forceinline__ void px_direct(const Px& s, Direct& d, const float4* s_lights, int cnt) {
   float3 sa = d.sa, sb = d.sb, sbf = d.sbf;
 #pragma unroll 4
   for (int i = 0; i < cnt; ++i) {
-    float4 lp = s_lights[2 * i], lc = s_lights[2 * i + 1];
-    float3 L = xyz(lp) - s.P;
-    float d2 = fmaf(L.x, L.x, fmaf(L.y, L.y, fmaf(L.z, L.z, 1e-30f)));
-    float rs = rsqrt_ftz(d2);
-    float nl = dot3(s.n, L) * rs;
-    float nlc = fmaxf(nl, 0.0f);
-    float lv = dot3(s.v, L) * rs;
-    float3 sv = L * rs + s.v;
-    float3 c = cross3(s.n, sv);
-    float c2 = fmaf(c.x, c.x, fmaf(c.y, c.y, fmaf(c.z, c.z, 1e-18f)));
-    float ns = nl + s.nv_raw;
-    float hh = fmaf(2.0f, lv, 2.000001f);
-    float den = fmaf(ns * ns, d.a2, c2);
-    float vh = 0.5f * hh * rsqrt_ftz(hh);
-    float xx = 1.0f - vh, x2 = xx * xx, fc = x2 * x2 * xx;
-    float spec = d.a2vv * hh * hh * rcp_ftz(den * den * fmaf(nlc, d.omk, d.k));
-    float w = rs * rs * nlc;  // (n.l) / d^2
-    float a = fmaf(-w, fc, w), b = w * spec, bf = b * fc;
-    sa.x = fmaf(lc.x, a, sa.x);
-    sa.y = fmaf(lc.y, a, sa.y);
-    sa.z = fmaf(lc.z, a, sa.z);
-    sb.x = fmaf(lc.x, b, sb.x);
-    sb.y = fmaf(lc.y, b, sb.y);
-    sb.z = fmaf(lc.z, b, sb.z);
-    sbf.x = fmaf(lc.x, bf, sbf.x);
-    sbf.y = fmaf(lc.y, bf, sbf.y);
-    sbf.z = fmaf(lc.z, bf, sbf.z);
+    float4 lc = s_lights[2 * i + 1];
+    LightTerms t = light_terms(s, d, s_lights[2 * i]);
+    sa.x = fmaf(lc.x, t.a, sa.x);
+    sa.y = fmaf(lc.y, t.a, sa.y);
+    sa.z = fmaf(lc.z, t.a, sa.z);
+    sb.x = fmaf(lc.x, t.b, sb.x);
+    sb.y = fmaf(lc.y, t.b, sb.y);
+    sb.z = fmaf(lc.z, t.b, sb.z);
+    sbf.x = fmaf(lc.x, t.bf, sbf.x);
+    sbf.y = fmaf(lc.y, t.bf, sbf.y);
+    sbf.z = fmaf(lc.z, t.bf, sbf.z);
   }
   d.sa = sa;
   d.sb = sb;
   d.sbf = sbf;
+}
+
+// Adds `cnt` staged monochrome lights (Ic_r = Ic_g = Ic_b).
+__device__ __forceinline__ void px_direct_mono(const Px& s, Direct& d, const float4* s_lights, int cnt) {
+  float sa = 0.0f, sb = 0.0f, sbf = 0.0f;
+#pragma unroll 4
+  for (int i = 0; i < cnt; ++i) {
+    float ic = s_lights[2 * i + 1].x;
+    LightTerms t = light_terms(s, d, s_lights[2 * i]);
+    sa = fmaf(ic, t.a, sa);
+    sb = fmaf(ic, t.b, sb);
+    sbf = fmaf(ic, t.bf, sbf);
+  }
+  d.sa = d.sa + f3(sa, sa, sa);
+  d.sb = d.sb + f3(sb, sb, sb);
+  d.sbf = d.sbf + f3(sbf, sbf, sbf);
 }
 
 __device__ __forceinline__ void px_direct_end(Px& s, const Direct& d) {
@@ -220,9 +283,10 @@ __device__ __forceinline__ void px_direct_end(Px& s, const Direct& d) {
                  fmaf(s.metal, s.albedo.z - 0.04f, 0.04f));
   float3 omF0 = f3(1.0f - F0.x, 1.0f - F0.y, 1.0f - F0.z);
   float3 K = mul3(s.albedo * ((1.0f - s.metal) * kInvPi), omF0);
-  s.acc.x += fmaf(K.x, d.sa.x, fmaf(F0.x, d.sb.x, omF0.x * d.sbf.x));
-  s.acc.y += fmaf(K.y, d.sa.y, fmaf(F0.y, d.sb.y, omF0.y * d.sbf.y));
-  s.acc.z += fmaf(K.z, d.sa.z, fmaf(F0.z, d.sb.z, omF0.z * d.sbf.z));
+  float3 sb = d.sb * d.a2vv, sbf = d.sbf * d.a2vv;
+  s.acc.x += fmaf(K.x, d.sa.x, fmaf(F0.x, sb.x, omF0.x * sbf.x));
+  s.acc.y += fmaf(K.y, d.sa.y, fmaf(F0.y, sb.y, omF0.y * sbf.y));
+  s.acc.z += fmaf(K.z, d.sa.z, fmaf(F0.z, sb.z, omF0.z * sbf.z));
 }
 
 // Diffuse-only variant: sum of Ic (n.l)/d^2, times albedo/pi at the end.
@@ -279,7 +343,7 @@ __device__ __forceinline__ void px_ambient(Px& s, const IblDev& ibl, unsigned fl
       float FssEss = fmaf(kS, AB.x, AB.y);
       float Ess = AB.x + AB.y, Ems = 1.0f - Ess;
       float Favg = F0a[q] + (1.0f - F0a[q]) * (1.0f / 21.0f);
-      float Fms = FssEss * Favg / (1.0f - Ems * Favg);
+      float Fms = FssEss * Favg * rcp_ftz(fmaf(-Ems, Favg, 1.0f));
       float kD = cd[q] * (1.0f - FssEss - Fms * Ems);
       la[q] = fmaf(FssEss, pr[q], (Fms * Ems + kD) * ir[q]);
     } else {
