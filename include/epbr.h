@@ -186,6 +186,25 @@ epbr_status epbr_brdf_lut(int32_t lut_size, int32_t num_samples, float* lut, voi
 epbr_status epbr_irradiance(const epbr_env* env, int32_t irr_width, int32_t irr_height,
                             float* out, void* workspace, size_t workspace_bytes, void* stream);
 
+/* Irradiance as epbr_irradiance, for callers that cannot allocate device memory: an engine or
+ * tool plugin whose host application owns the whole device-memory budget and forbids foreign
+ * allocations, or a frame loop that must not call cudaMalloc because it can synchronise the
+ * device and stall the frame.  No counterpart in the paper.
+ *  - Scratch: the per-block partial sums live in one library-owned device array of 8 MiB
+ *    (every GPU that loads the library holds it until the process exits).  A request needing
+ *    more (irr_width * irr_height * min(608, ceil(env texels / 1024)) * 16 bytes) is refused
+ *    with EPBR_ERR_INVALID_ARG and nothing is enqueued; the default 32x16 map over a
+ *    2048x1024 environment needs 4.75 MiB.
+ *  - Set-up: the first call on each device looks up the array's device address with that
+ *    device current (cudaGetSymbolAddress); make that first call before any stream capture.
+ *  - Sharing: every call on a device uses the same array, which keeps the previous call's
+ *    contents (each call writes every partial it reads, so nothing needs clearing).  Calls
+ *    whose work overlaps on the GPU (other streams, other threads) race on the array: order
+ *    them on one stream or with events.
+ * `out` is DEVICE float4[irr_h][irr_w]; no workspace argument. */
+epbr_status epbr_irradiance_noalloc(const epbr_env* env, int32_t irr_width, int32_t irr_height,
+                                    float* out, void* stream);
+
 /* Specular prefilter chain (split sum, first factor): level 0 is a copy of the source; level
  * m >= 1 with roughness r = m/(M-1), alpha = r^2 and n = v = texel direction is
  *   sum_k L(l_k) (n.l_k) / sum_k (n.l_k)  over the GGX half vectors of N Hammersley points,

@@ -183,6 +183,14 @@ def epbr_irradiance(env: torch.Tensor, Wi: int, Hi: int, out: torch.Tensor, work
                                  ws.numel() - (_aligned(ws) - ws.data_ptr()), _stream(stream)))
 
 
+def epbr_irradiance_noalloc(env: torch.Tensor, Wi: int, Hi: int, out: torch.Tensor, stream=None):
+    """epbr_irradiance without a workspace: for callers that may not allocate device memory
+    (the library's fixed 8 MiB scratch array is used instead)."""
+    e = env_struct(env)
+    _dev(out, torch.float32, "out")
+    _check(lib().epbr_irradiance_noalloc(C.byref(e), Wi, Hi, out.data_ptr(), _stream(stream)))
+
+
 def epbr_prefilter(env: torch.Tensor, N: int, ibl: Ibl, stream=None):
     e = env_struct(env)
     _check(lib().epbr_prefilter(C.byref(e), N, C.byref(ibl.struct), _stream(stream)))

@@ -91,6 +91,7 @@ PROTOTYPES = {
     "epbr_precompute_ibl": [P(epbr_env), P(epbr_ibl_params), P(epbr_ibl), vp, sz, vp],
     "epbr_brdf_lut": [i32, i32, vp, vp],
     "epbr_irradiance": [P(epbr_env), i32, i32, vp, vp, sz, vp],
+    "epbr_irradiance_noalloc": [P(epbr_env), i32, i32, vp, vp],
     "epbr_prefilter": [P(epbr_env), i32, P(epbr_ibl), vp],
     "epbr_ssao_size": [P(epbr_gbuffer), P(epbr_ssao_params), P(i32), P(i32)],
     "epbr_ssao_workspace_size": [P(epbr_gbuffer), P(epbr_ssao_params), P(sz)],

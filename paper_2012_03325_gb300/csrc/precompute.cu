@@ -5,6 +5,7 @@
 //   k_irradiance_final  sums the partials in a fixed order (deterministic) and normalises
 //   k_prefilter         GGX-prefiltered levels 1..M-1, one thread per output texel
 #include <algorithm>
+#include <mutex>
 
 #include "epbr_internal.cuh"
 
@@ -265,6 +266,69 @@ extern "C" epbr_status epbr_irradiance(const epbr_env* env, int32_t Wi, int32_t 
   cudaStream_t s = (cudaStream_t)stream;
   k_irradiance_part<<<nb, kIrrThreads, 0, s>>>((const float4*)env->texels, env->width, env->height, Wi,
                                                Hi, (float4*)ws);
+  if ((st = check_launch("k_irradiance_part"))) return st;
+  int nout = Wi * Hi;
+  k_irradiance_final<<<(nout + 255) / 256, 256, 0, s>>>((const float4*)ws, nb, nout, (float4*)out);
+  if ((st = check_launch("k_irradiance_final"))) return st;
+  return ok();
+}
+
+// ------------------------------------------------------------------------------------------
+// Irradiance for callers that cannot allocate: the per-block partial sums go to a fixed,
+// library-owned device array instead of caller workspace.
+// ------------------------------------------------------------------------------------------
+namespace epbr {
+
+constexpr size_t kStaticScratchBytes = (size_t)8 << 20;  // 8 MiB: 32x16 outputs over 608 blocks need 4.75 MiB
+static __device__ __align__(256) float4 g_irr_scratch[kStaticScratchBytes / sizeof(float4)];
+
+constexpr int kMaxDevices = 64;
+static std::mutex g_scratch_mutex;
+static void* g_scratch_addr[kMaxDevices];  // device address of g_irr_scratch, per device
+
+// Device address of g_irr_scratch on the current device.  In host code the name g_irr_scratch
+// is only a host-side handle, so the address is asked from the runtime once per device (with
+// that device current) and cached.
+static epbr_status static_scratch(void** out) {
+  int dev = -1;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return fail(EPBR_ERR_CUDA, "irradiance_noalloc: cudaGetDevice: %s", cudaGetErrorString(e));
+  if (dev < 0 || dev >= kMaxDevices) return fail(EPBR_ERR_UNSUPPORTED, "irradiance_noalloc: device %d", dev);
+  std::lock_guard<std::mutex> lock(g_scratch_mutex);
+  if (!g_scratch_addr[dev]) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_irr_scratch);
+    if (e != cudaSuccess || !p)
+      return fail(EPBR_ERR_CUDA, "irradiance_noalloc: cudaGetSymbolAddress: %s", cudaGetErrorString(e));
+    g_scratch_addr[dev] = p;
+  }
+  *out = g_scratch_addr[dev];
+  return EPBR_OK;
+}
+
+}  // namespace epbr
+
+extern "C" epbr_status epbr_irradiance_noalloc(const epbr_env* env, int32_t Wi, int32_t Hi, float* out,
+                                               void* stream) {
+  epbr_status st = validate_env(env);
+  if (st) return st;
+  if (Wi < 1 || Hi < 1 || Wi > 4096 || Hi > 4096 || !out)
+    return fail(EPBR_ERR_INVALID_ARG, "irradiance_noalloc: output %dx%d or pointer invalid", Wi, Hi);
+  if ((uintptr_t)out % 16) return fail(EPBR_ERR_INVALID_ARG, "irradiance_noalloc: out not 16-byte aligned");
+  size_t need = irr_workspace_bytes(env->width, env->height, Wi, Hi);
+  if (need > kStaticScratchBytes)
+    return fail(EPBR_ERR_INVALID_ARG,
+                "irradiance_noalloc: a %dx%d map over a %dx%d environment needs %zu bytes of scratch; the "
+                "static scratch holds %zu (use epbr_irradiance with a workspace)",
+                Wi, Hi, env->width, env->height, need, kStaticScratchBytes);
+  void* ws = nullptr;
+  if ((st = static_scratch(&ws))) return st;
+  int nb = irr_blocks(env->width, env->height);
+  cudaStream_t s = (cudaStream_t)stream;
+  // Every partial the final pass reads is written by the first pass, so the scratch needs no
+  // clearing between calls.
+  k_irradiance_part<<<nb, kIrrThreads, 0, s>>>((const float4*)env->texels, env->width, env->height, Wi, Hi,
+                                               (float4*)ws);
   if ((st = check_launch("k_irradiance_part"))) return st;
   int nout = Wi * Hi;
   k_irradiance_final<<<(nout + 255) / 256, 256, 0, s>>>((const float4*)ws, nb, nout, (float4*)out);
