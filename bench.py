@@ -201,7 +201,8 @@ def kernel_traffic(kernel: str, src_files):
     return d.get("dram_bytes_per_launch")
 
 
-SHADE_SOURCES = ["paper_2012_03325_gb300/csrc/shade.cu", "paper_2012_03325_gb300/csrc/epbr_internal.cuh"]
+SHADE_SOURCES = ["paper_2012_03325_gb300/csrc/shade.cu", "paper_2012_03325_gb300/csrc/shade_core.cuh",
+                 "paper_2012_03325_gb300/csrc/epbr_internal.cuh"]
 
 
 def sources_sha(files=SHADE_SOURCES):
