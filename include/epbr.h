@@ -318,6 +318,69 @@ epbr_status epbr_shade_tonemap(const epbr_gbuffer* gbuffer, const epbr_camera* c
                                int64_t hdr_pitch, const epbr_tonemap_params* tonemap,
                                uint8_t* ldr, int64_t ldr_pitch, void* stream);
 
+/* ---------------------------------------------------------------------------------------- */
+/* Batching: many views of uneven size in one persistent launch (a system form layered on the */
+/* pass; the paper renders one view per frame, Sec. 4)                                       */
+/* ---------------------------------------------------------------------------------------- */
+
+/* One view of a batch.  All pointers DEVICE; the G-buffer format must be the same for every
+ * view of a batch.  `ldr` (uchar4) is required, `hdr` optional (NULL). */
+typedef struct epbr_view {
+  epbr_gbuffer gbuffer;
+  epbr_camera camera;
+  const epbr_light* lights;
+  int32_t num_lights;
+  int32_t ibl_index;     /* index into the lighting sets passed with the batch */
+  void* hdr;
+  int64_t hdr_pitch;
+  uint8_t* ldr;
+  int64_t ldr_pitch;
+} epbr_view;
+
+typedef struct epbr_batch_params {
+  uint32_t flags;                  /* EPBR_SHADE_* for every view */
+  int32_t hdr_format;              /* EPBR_HDR_RGBA32F or EPBR_HDR_RGBA16F */
+  epbr_ssao_params ssao;           /* shared; scale must be 2, blur_radius <= 4, <= 64 samples */
+  epbr_tonemap_params tonemap;
+  int32_t tile_w, tile_h;          /* fused-mode pixels per tile: 64x32, 128x32 or 64x64;
+                                      0 = 64x32 */
+  int32_t light_chunk;             /* fused-mode lights per shared-memory chunk, 1..256; 0 = 256 */
+} epbr_batch_params;
+
+/* Batch execution modes (a plan = mode + tile shape + light chunk):
+ *   EPBR_BATCH_FUSED   one persistent kernel; per tile of tile_w x tile_h pixels: unblurred
+ *                      SSAO with a halo, blur, compose, tone map, all in shared memory
+ *   EPBR_BATCH_STAGED  three kernels (SSAO, blur, compose + tone map), each over the tiles of
+ *                      every view, AO images in batch-owned memory */
+enum { EPBR_BATCH_FUSED = 0, EPBR_BATCH_STAGED = 1 };
+
+/* Library-owned batch: device copies of the view descriptors, the tile list and a CUDA graph
+ * (memset of the tile counter -> the fused kernel).  The views' buffers are referenced, not
+ * copied: relaunching renders whatever they hold at launch time. */
+typedef struct epbr_batch epbr_batch;
+
+/* Renders every view with the same arithmetic as epbr_ssao + epbr_shade_tonemap per view.
+ * Allocates the batch's descriptors, tile lists and (staged mode) AO images — the one place
+ * the library allocates device memory; synchronous.  Starts with the fused 64x32 plan. */
+epbr_status epbr_batch_create(const epbr_view* views, int32_t n_views, const epbr_ibl* ibls,
+                              int32_t n_ibls, const epbr_batch_params* params, epbr_batch** out);
+/* Enqueues one replay of the batch's graph on `stream`. */
+epbr_status epbr_batch_launch(epbr_batch* batch, void* stream);
+/* Times every plan (each fused tile shape x light chunk, and the staged mode) on this batch and
+ * keeps the fastest (synchronises `stream`).  With `cache_path`, a plan stored for the same
+ * batch key is reused without timing, and new results are appended as text lines
+ * "key mode tile_w tile_h chunk ms". */
+epbr_status epbr_batch_autotune(epbr_batch* batch, const char* cache_path, void* stream);
+epbr_status epbr_batch_get_plan(const epbr_batch* batch, int32_t* mode, int32_t* tile_w,
+                                int32_t* tile_h, int32_t* light_chunk);
+epbr_status epbr_batch_set_plan(epbr_batch* batch, int32_t mode, int32_t tile_w, int32_t tile_h,
+                                int32_t light_chunk);
+/* Waits for nothing: destroy only after the batch's launches have completed. */
+epbr_status epbr_batch_destroy(epbr_batch* batch);
+/* create + launch + wait for `stream` + destroy. */
+epbr_status epbr_render_batch(const epbr_view* views, int32_t n_views, const epbr_ibl* ibls,
+                              int32_t n_ibls, const epbr_batch_params* params, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -281,3 +281,75 @@ def epbr_tonemap(hdr: torch.Tensor, hdr_format: int, tp: F.epbr_tonemap_params, 
     H, W = hdr.shape[0], hdr.shape[1]
     _check(lib().epbr_tonemap(hdr.data_ptr(), hdr_format, W, H, _pitch(hdr, 1), C.byref(tp), out.data_ptr(),
                               _pitch(out, 1), _stream(stream)))
+
+
+# ------------------------------------------------------------------------------------------
+# batching: many views, one persistent launch replayed from a CUDA graph
+# ------------------------------------------------------------------------------------------
+def view(g: GBuffer, cam: F.epbr_camera, lights: torch.Tensor | None, ibl_index: int, ldr: torch.Tensor,
+         hdr: torch.Tensor | None = None) -> F.epbr_view:
+    lp, nl = _lights(lights)
+    v = F.epbr_view()
+    v.gbuffer, v.camera, v.lights, v.num_lights, v.ibl_index = g.struct, cam, lp, nl, ibl_index
+    v.ldr, v.ldr_pitch = _dev(ldr, torch.uint8, "ldr"), _pitch(ldr, 1)
+    if hdr is not None:
+        v.hdr, v.hdr_pitch = _dev(hdr, name="hdr"), _pitch(hdr, 1)
+    return v
+
+
+def batch_params(ssao: SsaoParams, flags: int = EPBR_SHADE_ALL, hdr_format: int = EPBR_HDR_RGBA32F,
+                 tp: F.epbr_tonemap_params | None = None, tile_w: int = 0, tile_h: int = 0,
+                 light_chunk: int = 0) -> F.epbr_batch_params:
+    return F.epbr_batch_params(flags, hdr_format, ssao.struct, tp or tonemap_params(), tile_w, tile_h, light_chunk)
+
+
+class Batch:
+    """epbr_batch: create / launch / autotune / destroy.  Keeps the views' tensors alive."""
+
+    def __init__(self, views, ibls, params: F.epbr_batch_params, keep=()):
+        self._keep = list(keep)
+        self.views = (F.epbr_view * len(views))(*views)
+        self.ibls = (F.epbr_ibl * len(ibls))(*[i.struct for i in ibls])
+        self._ibl_objs = list(ibls)
+        self.params = params
+        self.handle = C.c_void_p()
+        _check(lib().epbr_batch_create(self.views, len(views), self.ibls, len(ibls), C.byref(params),
+                                       C.byref(self.handle)))
+
+    def epbr_batch_launch(self, stream=None):
+        _check(lib().epbr_batch_launch(self.handle, _stream(stream)))
+
+    launch = epbr_batch_launch
+
+    def epbr_batch_autotune(self, cache_path: str | None = None, stream=None):
+        _check(lib().epbr_batch_autotune(self.handle, cache_path.encode() if cache_path else None,
+                                         _stream(stream)))
+        return self.plan()
+
+    autotune = epbr_batch_autotune
+
+    def plan(self):
+        """(mode, tile_w, tile_h, light_chunk)."""
+        md, tw, th, ch = C.c_int32(), C.c_int32(), C.c_int32(), C.c_int32()
+        _check(lib().epbr_batch_get_plan(self.handle, C.byref(md), C.byref(tw), C.byref(th), C.byref(ch)))
+        return md.value, tw.value, th.value, ch.value
+
+    def set_plan(self, mode: int, tile_w: int = 64, tile_h: int = 32, light_chunk: int = 256):
+        _check(lib().epbr_batch_set_plan(self.handle, mode, tile_w, tile_h, light_chunk))
+
+    def close(self):
+        if self.handle:
+            lib().epbr_batch_destroy(self.handle)
+            self.handle = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def epbr_render_batch(views, ibls, params: F.epbr_batch_params, stream=None):
+    arr = (F.epbr_view * len(views))(*views)
+    iarr = (F.epbr_ibl * len(ibls))(*[i.struct for i in ibls])
+    _check(lib().epbr_render_batch(arr, len(views), iarr, len(ibls), C.byref(params), _stream(stream)))

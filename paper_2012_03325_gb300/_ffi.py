@@ -33,6 +33,8 @@ EPBR_HDR_RGBA32F = 0
 EPBR_HDR_RGBA16F = 1
 EPBR_TONEMAP_ACES = 0
 EPBR_TONEMAP_REINHARD = 1
+EPBR_BATCH_FUSED = 0
+EPBR_BATCH_STAGED = 1
 
 
 class epbr_camera(C.Structure):
@@ -81,6 +83,18 @@ class epbr_tonemap_params(C.Structure):
     _fields_ = [("exposure", C.c_float), ("op", C.c_int32)]
 
 
+class epbr_view(C.Structure):
+    _fields_ = [("gbuffer", epbr_gbuffer), ("camera", epbr_camera), ("lights", C.c_void_p),
+                ("num_lights", C.c_int32), ("ibl_index", C.c_int32), ("hdr", C.c_void_p), ("hdr_pitch", C.c_int64),
+                ("ldr", C.c_void_p), ("ldr_pitch", C.c_int64)]
+
+
+class epbr_batch_params(C.Structure):
+    _fields_ = [("flags", C.c_uint32), ("hdr_format", C.c_int32), ("ssao", epbr_ssao_params),
+                ("tonemap", epbr_tonemap_params), ("tile_w", C.c_int32), ("tile_h", C.c_int32),
+                ("light_chunk", C.c_int32)]
+
+
 P = C.POINTER
 vp, i32, i64, sz = C.c_void_p, C.c_int32, C.c_int64, C.c_size_t
 
@@ -103,6 +117,13 @@ PROTOTYPES = {
     "epbr_shade_tonemap": [P(epbr_gbuffer), P(epbr_camera), vp, i32, P(epbr_ibl), P(epbr_shade_params), vp,
                            i32, i64, P(epbr_tonemap_params), vp, i64, vp],
     "epbr_tonemap": [vp, i32, i32, i32, i64, P(epbr_tonemap_params), vp, i64, vp],
+    "epbr_batch_create": [P(epbr_view), i32, P(epbr_ibl), i32, P(epbr_batch_params), P(vp)],
+    "epbr_batch_launch": [vp, vp],
+    "epbr_batch_autotune": [vp, C.c_char_p, vp],
+    "epbr_batch_get_plan": [vp, P(i32), P(i32), P(i32), P(i32)],
+    "epbr_batch_set_plan": [vp, i32, i32, i32, i32],
+    "epbr_batch_destroy": [vp],
+    "epbr_render_batch": [P(epbr_view), i32, P(epbr_ibl), i32, P(epbr_batch_params), vp],
 }
 OTHER = {"epbr_last_error": ([], C.c_char_p), "epbr_version": ([], C.c_char_p)}
 

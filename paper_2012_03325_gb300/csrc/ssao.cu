@@ -1,29 +1,15 @@
 // Screen-space ambient occlusion (paper Sec. 5.2: normal-oriented hemisphere of Bavoil &
 // Sainz 2008, at half resolution, then a bilateral blur).
 //   k_ssao_raw   one thread per AO texel; the K kernel offsets sit in shared memory and the
-//                depth taps go through the read-only cache
+//                depth taps go through the read-only cache (per-texel math in ssao_core.cuh)
 //   k_ssao_blur  one thread per AO texel; (2R+1)^2 depth-aware taps read from a shared-memory
 //                tile of AO values and depths with an R-texel halo
-#include "epbr_internal.cuh"
+#include "ssao_core.cuh"
 
 namespace epbr {
 
-constexpr int kMaxSsaoSamples = 256;
-
-struct SsaoDev {
-  int K, scale, R;
-  float radius, bias, sigma_s, sigma_z;
-  const float4* kernel;
-  const float2* noise;
-};
-
-__device__ __forceinline__ float smoothstep01(float x) {
-  x = clamp01(x);
-  return x * x * (3.0f - 2.0f * x);
-}
-
 template <int FMT>
-__global__ void __launch_bounds__(256) k_ssao_raw(GbufDev g, CamDev cam, SsaoDev p, float* __restrict__ ao,
+__global__ void __launch_bounds__(256, 4) k_ssao_raw(GbufDev g, CamDev cam, SsaoDev p, float* __restrict__ ao,
                                                   long long ao_pitch, int Wa, int Ha) {
   __shared__ float4 s_kernel[kMaxSsaoSamples];
   int tid = threadIdx.y * blockDim.x + threadIdx.x;
@@ -31,42 +17,7 @@ __global__ void __launch_bounds__(256) k_ssao_raw(GbufDev g, CamDev cam, SsaoDev
   __syncthreads();
   int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y;
   if (i >= Wa || j >= Ha) return;
-  float* out = (float*)((char*)ao + (size_t)j * ao_pitch) + i;
-  int X0 = p.scale * i, Y0 = p.scale * j;
-  float e = gb_depth(g, X0, Y0);
-  if (!is_surface(e)) {
-    *out = 1.0f;
-    return;
-  }
-  float3 P = e * view_ray(cam, X0, Y0);
-  float3 n = rot_t(cam, gb_normal<FMT>(g, X0, Y0));
-  float2 nz = __ldg(p.noise + ((j & 3) * 4 + (i & 3)));
-  float3 rv = f3(nz.x, nz.y, 0.0f);
-  float3 t = rv - n * dot3(rv, n), b;
-  float tl = sqrtf(dot3(t, t));
-  if (tl < 1e-4f) {
-    onb(n, t, b);
-  } else {
-    t = t * (1.0f / tl);
-    b = cross3(n, t);
-  }
-  float ix_scale = 0.5f * cam.W / cam.sx, iy_scale = 0.5f * cam.H / cam.sy;
-  float occ = 0.0f;
-  for (int k = 0; k < p.K; ++k) {
-    float4 ks = s_kernel[k];
-    float3 S = P + p.radius * (t * ks.x + b * ks.y + n * ks.z);
-    float eS = -S.z;
-    if (!(eS > 0.0f)) continue;
-    float inv = rcp_ftz(eS);
-    float x = fmaf(S.x * inv, ix_scale, 0.5f * cam.W);
-    float y = fmaf(-S.y * inv, iy_scale, 0.5f * cam.H);
-    if (!(x >= 0.0f && x < (float)cam.W && y >= 0.0f && y < (float)cam.H)) continue;
-    int ix = min((int)x, cam.W - 1), iy = min((int)y, cam.H - 1);
-    float eb = gb_depth(g, ix, iy);
-    if (!is_surface(eb)) continue;
-    if (eb <= eS - p.bias) occ += smoothstep01(p.radius * rcp_ftz(fabsf(e - eb)));
-  }
-  *out = 1.0f - occ / p.K;
+  ((float*)((char*)ao + (size_t)j * ao_pitch))[i] = ssao_texel<FMT>(g, cam, p, s_kernel, i, j).x;
 }
 
 // Blur tile: 32x8 AO texels plus a halo of R <= 8 texels, AO values and the depths of their
@@ -98,28 +49,8 @@ __global__ void __launch_bounds__(kBlurBX* kBlurBY) k_ssao_blur(GbufDev g, SsaoD
   __syncthreads();
   int i = blockIdx.x * kBlurBX + threadIdx.x, j = blockIdx.y * kBlurBY + threadIdx.y;
   if (i >= Wa || j >= Ha) return;
-  float* o = (float*)((char*)out + (size_t)j * out_pitch) + i;
-  float ep = s_e[threadIdx.y + R][threadIdx.x + R];
-  if (!is_surface(ep)) {
-    *o = 1.0f;
-    return;
-  }
-  // w = exp(-(dx^2 + dy^2) / (2 sigma_s^2)) * exp(-|e_q - e_p| / (sigma_z e_p)), one exponential
-  float ks = -1.4426950408889634f / (2.0f * p.sigma_s * p.sigma_s);
-  float kz = -1.4426950408889634f / (p.sigma_z * ep);
-  float num = 0.0f, den = 0.0f;
-  for (int dy = -R; dy <= R; ++dy) {
-    const float* ra = &s_ao[threadIdx.y + R + dy][threadIdx.x + R];
-    const float* re = &s_e[threadIdx.y + R + dy][threadIdx.x + R];
-    for (int dx = -R; dx <= R; ++dx) {
-      float eq = re[dx];
-      if (!is_surface(eq)) continue;
-      float w = exp2f(fmaf((float)(dx * dx + dy * dy), ks, fabsf(eq - ep) * kz));
-      num = fmaf(w, ra[dx], num);
-      den += w;
-    }
-  }
-  *o = num / den;
+  ((float*)((char*)out + (size_t)j * out_pitch))[i] =
+      ssao_blur_texel(p, &s_ao[threadIdx.y + R][threadIdx.x + R], &s_e[threadIdx.y + R][threadIdx.x + R], kBlurTW);
 }
 
 static epbr_status validate_ssao(const epbr_ssao_params* p) {

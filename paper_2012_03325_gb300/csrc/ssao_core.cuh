@@ -1,0 +1,88 @@
+// SSAO per-texel arithmetic (paper Sec. 5.2, normal-oriented hemisphere of Bavoil & Sainz
+// 2008) shared by the per-view kernels (ssao.cu) and the fused multi-view kernel (batch.cu).
+#pragma once
+
+#include "epbr_internal.cuh"
+
+namespace epbr {
+
+constexpr int kMaxSsaoSamples = 256;
+
+struct SsaoDev {
+  int K, scale, R;
+  float radius, bias, sigma_s, sigma_z;
+  const float4* kernel;
+  const float2* noise;
+};
+
+__device__ __forceinline__ float smoothstep01(float x) {
+  x = clamp01(x);
+  return x * x * (3.0f - 2.0f * x);
+}
+
+// Unblurred AO of AO texel (i, j), which uses full-resolution pixel (scale i, scale j), as
+// (AO, depth of that pixel); background pixels (depth +inf) have AO 1.  `s_kernel` holds the K
+// hemisphere offsets.
+template <int FMT>
+__device__ __forceinline__ float2 ssao_texel(const GbufDev& g, const CamDev& cam, const SsaoDev& p,
+                                             const float4* s_kernel, int i, int j) {
+  int X0 = p.scale * i, Y0 = p.scale * j;
+  float e = gb_depth(g, X0, Y0);
+  if (!is_surface(e)) return make_float2(1.0f, e);
+  float3 P = e * view_ray(cam, X0, Y0);
+  float3 n = rot_t(cam, gb_normal<FMT>(g, X0, Y0));
+  float2 nz = __ldg(p.noise + ((j & 3) * 4 + (i & 3)));
+  float3 rv = f3(nz.x, nz.y, 0.0f);
+  float3 t = rv - n * dot3(rv, n), b;
+  float tl = sqrtf(dot3(t, t));
+  if (tl < 1e-4f) {
+    onb(n, t, b);
+  } else {
+    t = t * (1.0f / tl);
+    b = cross3(n, t);
+  }
+  float ix_scale = 0.5f * cam.W / cam.sx, iy_scale = 0.5f * cam.H / cam.sy;
+  float occ = 0.0f;
+  for (int k = 0; k < p.K; ++k) {
+    float4 ks = s_kernel[k];
+    float3 S = P + p.radius * (t * ks.x + b * ks.y + n * ks.z);
+    float eS = -S.z;
+    if (!(eS > 0.0f)) continue;
+    float inv = rcp_ftz(eS);
+    float x = fmaf(S.x * inv, ix_scale, 0.5f * cam.W);
+    float y = fmaf(-S.y * inv, iy_scale, 0.5f * cam.H);
+    if (!(x >= 0.0f && x < (float)cam.W && y >= 0.0f && y < (float)cam.H)) continue;
+    int ix = min((int)x, cam.W - 1), iy = min((int)y, cam.H - 1);
+    float eb = gb_depth(g, ix, iy);
+    if (!is_surface(eb)) continue;
+    if (eb <= eS - p.bias) occ += smoothstep01(p.radius * rcp_ftz(fabsf(e - eb)));
+  }
+  return make_float2(1.0f - occ / p.K, e);
+}
+
+// Depth-aware blur of one AO texel from shared-memory tiles: `ao` and `ed` point at the
+// centre texel inside row-major tiles of row pitch `tp` that hold R texels around it (taps
+// outside the image staged as background, e = +inf).  Weight
+//   w = exp(-(dx^2 + dy^2) / (2 sigma_s^2)) * exp(-|e_q - e_p| / (sigma_z e_p)),
+// evaluated as one exponential; background centre texels return 1.
+__device__ __forceinline__ float ssao_blur_texel(const SsaoDev& p, const float* ao, const float* ed, int tp) {
+  float ep = ed[0];
+  if (!is_surface(ep)) return 1.0f;
+  float ks = -1.4426950408889634f / (2.0f * p.sigma_s * p.sigma_s);
+  float kz = -1.4426950408889634f / (p.sigma_z * ep);
+  float num = 0.0f, den = 0.0f;
+  for (int dy = -p.R; dy <= p.R; ++dy) {
+    const float* ra = ao + dy * tp;
+    const float* re = ed + dy * tp;
+    for (int dx = -p.R; dx <= p.R; ++dx) {
+      float eq = re[dx];
+      if (!is_surface(eq)) continue;
+      float w = exp2f(fmaf((float)(dx * dx + dy * dy), ks, fabsf(eq - ep) * kz));
+      num = fmaf(w, ra[dx], num);
+      den += w;
+    }
+  }
+  return num / den;
+}
+
+}  // namespace epbr

@@ -361,6 +361,23 @@ def make_hdr_field(seed: int, width: int, height: int) -> np.ndarray:
     return x.astype(np.float32)
 
 
+BATCH_RESOLUTIONS = [(512, 512), (1280, 720), (1920, 1080), (3840, 2160)]
+
+
+def batch_views(n_views: int = 64, seed: int = 2000, n_envs: int = 8):
+    """View specs of the multi-view workload: resolution uniform over BATCH_RESOLUTIONS, light
+    count log-uniform over [16, 256], environment uniform over n_envs maps; each view's scene is
+    the 200-sphere recipe with seed `seed + view`.  Returns [(W, H, n_lights, env, scene_seed)]."""
+    rng = PCG32(seed, stream=17)
+    out = []
+    for v in range(n_views):
+        W, H = BATCH_RESOLUTIONS[min(3, int(rng.uniform() * 4))]
+        nl = int(round(math.exp(rng.uniform(math.log(16.0), math.log(256.0)))))
+        env = min(n_envs - 1, int(rng.uniform() * n_envs))
+        out.append((W, H, nl, env, seed + v))
+    return out
+
+
 # Workload shapes (seeds are 1000 * config + view).
 CONFIGS = {
     "small": dict(width=256, height=256, spheres=16, lights=4, env=(128, 64), levels=6,
