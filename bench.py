@@ -39,7 +39,9 @@ def parse():
     ap.add_argument("--steps", type=int, default=2000)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="epbr", choices=["epbr", "reference"])
-    ap.add_argument("--workload", default=WORKLOAD, choices=sorted(synth.CONFIGS) + ["batch"])
+    ap.add_argument("--workload", default=WORKLOAD, choices=sorted(synth.CONFIGS) + ["batch", "serve"])
+    ap.add_argument("--serve-requests", type=int, default=300, help="requests per rate (serve workload)")
+    ap.add_argument("--serve-seconds", type=float, default=3.0, help="arrival window per rate (serve workload)")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="CPU-baseline time budget")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
@@ -562,12 +564,171 @@ def run_batch(args):
     batch.close()
 
 
+# ------------------------------------------------------------------------------------------
+# serving workload: Poisson arrivals against the continuous-batching server
+# ------------------------------------------------------------------------------------------
+SERVE_CLASSES = [(256, 256, 0.4), (512, 512, 0.3), (1920, 1080, 0.2), (3840, 2160, 0.1)]
+
+
+def _gen_serve_gbuffer(spec):
+    """One pooled G-buffer of the serving workload (spawned worker)."""
+    W, H, seed = spec
+    sc = synth.make_scene(seed, W, H, 200, 1)
+    g = synth.raycast_gbuffer(sc)
+    return g.rt0, g.rt1, g.depth, sc.camera_array(), sc.fov_y, sc.F
+
+
+def run_serve(args):
+    import multiprocessing as mp
+    import threading
+
+    variants = 3
+    specs = [(W, H, 4000 + 10 * c + v) for c, (W, H, _) in enumerate(SERVE_CLASSES) for v in range(variants)]
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(max(1, min(12, os.cpu_count() or 1))) as pool:
+        gen = list(pool.imap(_gen_serve_gbuffer, specs))
+    import torch
+
+    import paper_2012_03325_gb300 as ep
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    c1 = synth.CONFIGS["full"]
+    params = ep.ibl_params(c1["levels"], c1["prefilter_samples"], c1["lut"], c1["lut_samples"], *c1["irr"])
+    ibls, keep = [], []
+    for e in range(16):
+        env_t = torch.from_numpy(synth.make_env(4100 + e, 1024, 512)).to(dev)
+        ibls.append(ep.epbr_precompute_ibl(env_t, ep.Ibl(params, 1024, 512, device=dev)))
+        keep.append(env_t)
+    k = torch.from_numpy(synth.make_ssao_kernel(4000, 32)).to(dev)
+    nz = torch.from_numpy(synth.make_ssao_noise(4000)).to(dev)
+    sp = ep.SsaoParams(k, nz, radius=0.5, scale=2, blur_radius=3)
+    torch.cuda.synchronize()
+    pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
+    pooled = [[] for _ in SERVE_CLASSES]
+    for (W, H, seed), (rt0, rt1, depth, cam_arr, fov, F) in zip(specs, gen):
+        c = [i for i, (w, h, _) in enumerate(SERVE_CLASSES) if (w, h) == (W, H)][0]
+        pooled[c].append(([pin(rt0), pin(rt1), None, pin(depth)], ep.camera(cam_arr, fov, W, H), F))
+    del gen
+    out_pool = [[torch.empty(H, W, 4, dtype=torch.uint8).pin_memory() for _ in range(n)]
+                for (W, H, _), n in zip(SERVE_CLASSES, (160, 120, 80, 40))]
+
+    def make_requests(n, seed):
+        rng = synth.PCG32(seed, stream=23)
+        weights = np.cumsum([w for _, _, w in SERVE_CLASSES])
+        out = []
+        for i in range(n):
+            u = rng.uniform()
+            c = int(np.searchsorted(weights, u, side="right"))
+            c = min(c, len(SERVE_CLASSES) - 1)
+            rts, cam, F = pooled[c][int(rng.uniform() * variants) % variants]
+            nl = int(round(math.exp(rng.uniform(0.0, math.log(256.0)))))
+            L = np.zeros((nl, 8), np.float32)
+            for j in range(nl):
+                L[j, :4] = (rng.uniform(-F, F), rng.uniform(3, 3 + 2 * F), rng.uniform(-F, F), rng.uniform(1, 50))
+                L[j, 4:7] = 1.0
+            out.append((c, rts, cam, L, int(rng.uniform() * 16) % 16))
+        return out
+
+    def run(srv, reqs, rate):
+        """Submit with exponential gaps of mean 1/rate (rate None: all at once); wait for all."""
+        rng = np.random.default_rng(int(rate or 0) + 7)
+        free = [list(range(len(pl))) for pl in out_pool]
+        tickets, lock = [], threading.Lock()
+        results = []
+
+        def collector():
+            i = 0
+            while True:
+                with lock:
+                    if i >= len(tickets):
+                        if done_submitting[0]:
+                            return
+                        t = None
+                    else:
+                        t = tickets[i]
+                if t is None:
+                    time.sleep(0.0002)
+                    continue
+                tk, c, b, px = t
+                res = srv.wait(tk)
+                results.append((res.status, res.latency_ms, res.queue_ms, res.deferred, px, time.perf_counter()))
+                with lock:
+                    free[c].append(b)
+                i += 1
+
+        done_submitting = [False]
+        th = threading.Thread(target=collector)
+        th.start()
+        t0 = time.perf_counter()
+        t_next = t0
+        for c, rts, cam, L, env in reqs:
+            if rate:
+                t_next += rng.exponential(1.0 / rate)
+                while time.perf_counter() < t_next:
+                    pass
+            while True:
+                with lock:
+                    if free[c]:
+                        b = free[c].pop()
+                        break
+                time.sleep(0.0001)
+            r = srv.request(ep.EPBR_GBUFFER_FP32, rts, cam, L, env, out_pool[c][b])
+            tk = srv.submit(r, keep=(L,))
+            with lock:
+                tickets.append((tk, c, b, cam.width * cam.height))
+        with lock:
+            done_submitting[0] = True
+        th.join()
+        t_end = max(r[5] for r in results)
+        lat = np.array([r[1] for r in results])
+        ok_px = sum(r[4] for r in results if r[0] == 0)
+        return {"requests": len(results), "failed": sum(1 for r in results if r[0] != 0),
+                "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+                "mean_queue_ms": float(np.mean([r[2] for r in results])),
+                "deferred": int(sum(r[3] for r in results)), "mpx_s": ok_px / (t_end - t0) / 1e6,
+                "offered_req_s": rate, "achieved_req_s": len(results) / (t_end - t0)}
+
+    budget = 6 << 30
+    served = ep.Server(ibls, sp, memory_budget=budget, max_in_flight=16, num_streams=8)
+    fifo = ep.Server(ibls, sp, memory_budget=budget, max_in_flight=1, num_streams=1)
+    run(served, make_requests(20, 1), None)  # warm-up
+    run(fifo, make_requests(10, 2), None)
+    n_req = max(20, args.serve_requests)
+    rates = []
+    with ClockSampler(0) as clk:
+        clk.mark_start()
+        for rate in (10, 30, 100, 300, 1000, 2000):
+            n = int(min(n_req, max(20, rate * args.serve_seconds)))
+            rates.append(run(served, make_requests(n, 100 + rate), rate))
+        burst = run(served, make_requests(n_req, 9), None)
+        burst_fifo = run(fifo, make_requests(n_req, 9), None)
+        clk.mark_end()
+    st = served.stats()
+    served.close()
+    fifo.close()
+    line = {"metric": METRIC, "value": burst["mpx_s"], "unit": "Mpixels/s", "n_gpus": 1, "steps": len(rates),
+            "warmup": 1, "ms_per_step": None, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "serve: Poisson arrivals, resolution {256^2, 512^2, 1920x1080, 3840x2160} with "
+                                   "weights .4/.3/.2/.1, 1-256 lights (log-uniform), 16 resident 1024x512 "
+                                   "lighting sets, FP32 G-buffer from pinned host memory, RGBA8 back to host",
+                       "server": {"memory_budget": budget, "max_in_flight": 16, "streams": 8},
+                       "value": "saturation throughput: all requests submitted at once"},
+            "rates": rates, "saturation": burst, "fifo_one_at_a_time": burst_fifo,
+            "speedup_vs_fifo": burst["mpx_s"] / burst_fifo["mpx_s"],
+            "server_stats": {"admitted": st.admitted, "deferred": st.deferred, "peak_bytes": st.peak_bytes},
+            "clocks": clk.summary()}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
     elif args.workload == "batch":
         run_batch(args)
+    elif args.workload == "serve":
+        run_serve(args)
     else:
         run_gpu(args)
 

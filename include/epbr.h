@@ -381,6 +381,68 @@ epbr_status epbr_batch_destroy(epbr_batch* batch);
 epbr_status epbr_render_batch(const epbr_view* views, int32_t n_views, const epbr_ibl* ibls,
                               int32_t n_ibls, const epbr_batch_params* params, void* stream);
 
+/* ---------------------------------------------------------------------------------------- */
+/* Serving: a request loop with continuous batching (a system form layered on the pass; the   */
+/* paper's stated use is generating synthetic training images, Sec. 8.1)                     */
+/* ---------------------------------------------------------------------------------------- */
+typedef struct epbr_serve_config {
+  size_t memory_budget;         /* device bytes for admitted requests' buffers (one arena) */
+  int32_t max_in_flight;        /* requests admitted at once */
+  int32_t num_streams;          /* streams their work is spread over, 1..64 */
+  const epbr_ibl* ibls;         /* resident lighting sets; must outlive the server */
+  int32_t num_ibls;
+  uint32_t flags;               /* EPBR_SHADE_* */
+  epbr_ssao_params ssao;        /* scale must be 2; kernel/noise DEVICE pointers */
+  epbr_tonemap_params tonemap;
+} epbr_serve_config;
+
+/* One render request.  All pointers are HOST memory that must stay valid until the request's
+ * result has been collected (pinned memory lets the copies overlap other requests' work). */
+typedef struct epbr_request {
+  int32_t format;               /* EPBR_GBUFFER_FP32 or EPBR_GBUFFER_COMPACT, rows dense */
+  int32_t width, height;
+  int32_t ibl_index;            /* which resident lighting set */
+  const void* rt[4];            /* G-buffer planes as in epbr_gbuffer */
+  epbr_camera camera;
+  const epbr_light* lights;
+  int32_t num_lights;
+  int32_t reserved;
+  uint8_t* ldr_out;             /* width * height * 4 bytes, RGBA8 result */
+  double deadline_ms;           /* > 0: cancelled (EPBR_ERR_TIMEOUT) if still queued after it */
+} epbr_request;
+
+typedef struct epbr_result {
+  epbr_status status;           /* EPBR_OK, EPBR_ERR_TIMEOUT (cancelled in the queue), ... */
+  int32_t deferred;             /* 1 if admission waited for memory */
+  double queue_ms;              /* submit -> admission */
+  double latency_ms;            /* submit -> result in host memory */
+  char message[160];
+} epbr_result;
+
+typedef struct epbr_serve_stats {
+  uint64_t submitted, admitted, completed, deferred, rejected, timed_out, failed;
+  int32_t in_flight, queued;
+  size_t bytes_in_use, peak_bytes;
+} epbr_serve_stats;
+
+typedef struct epbr_server epbr_server;
+
+/* Allocates the arena and streams and starts the scheduler thread.  Requests are admitted in
+ * arrival order whenever a slot is free and the arena can hold the request's G-buffer, lights,
+ * AO images and 8-bit image; admitted requests run concurrently on the server's streams. */
+epbr_status epbr_serve_create(const epbr_serve_config* config, epbr_server** out);
+/* Device bytes a request occupies while admitted. */
+epbr_status epbr_serve_request_bytes(const epbr_request* request, size_t* bytes);
+/* Queues a request (thread-safe).  EPBR_ERR_ADMISSION when it alone exceeds the budget. */
+epbr_status epbr_serve_submit(epbr_server* server, const epbr_request* request, uint64_t* ticket);
+/* Non-blocking: *done = 1 and the result (ticket consumed) once the request has finished. */
+epbr_status epbr_serve_poll(epbr_server* server, uint64_t ticket, int32_t* done, epbr_result* out);
+/* Blocks up to timeout_ms; EPBR_ERR_TIMEOUT if the request is still running (ticket kept). */
+epbr_status epbr_serve_wait(epbr_server* server, uint64_t ticket, int32_t timeout_ms, epbr_result* out);
+epbr_status epbr_serve_get_stats(epbr_server* server, epbr_serve_stats* out);
+/* Cancels queued requests, waits for admitted ones, frees everything. */
+epbr_status epbr_serve_destroy(epbr_server* server);
+
 #ifdef __cplusplus
 }
 #endif

@@ -353,3 +353,95 @@ def epbr_render_batch(views, ibls, params: F.epbr_batch_params, stream=None):
     arr = (F.epbr_view * len(views))(*views)
     iarr = (F.epbr_ibl * len(ibls))(*[i.struct for i in ibls])
     _check(lib().epbr_render_batch(arr, len(views), iarr, len(ibls), C.byref(params), _stream(stream)))
+
+
+# ------------------------------------------------------------------------------------------
+# serving: request loop with continuous batching
+# ------------------------------------------------------------------------------------------
+def _host_ptr(a) -> int:
+    if isinstance(a, torch.Tensor):
+        if a.is_cuda:
+            raise ValueError("request buffers are host memory")
+        return a.data_ptr()
+    import numpy as np
+    if not isinstance(a, np.ndarray) or not a.flags["C_CONTIGUOUS"]:
+        raise ValueError("request buffers must be contiguous numpy arrays or CPU tensors")
+    return a.ctypes.data
+
+
+class Server:
+    """epbr_server.  submit() keeps the request's host buffers alive until its result is taken."""
+
+    def __init__(self, ibls, ssao: SsaoParams, memory_budget: int, max_in_flight: int = 8, num_streams: int = 4,
+                 flags: int = EPBR_SHADE_ALL, tp: F.epbr_tonemap_params | None = None):
+        self._ibl_objs = list(ibls)
+        self._ibls = (F.epbr_ibl * len(ibls))(*[i.struct for i in ibls])
+        self._ssao = ssao
+        cfg = F.epbr_serve_config(memory_budget, max_in_flight, num_streams, C.cast(self._ibls, C.c_void_p),
+                                  len(ibls), flags, ssao.struct, tp or tonemap_params())
+        self.handle = C.c_void_p()
+        _check(lib().epbr_serve_create(C.byref(cfg), C.byref(self.handle)))
+        self._live = {}
+
+    @staticmethod
+    def request(fmt: int, rts, cam: F.epbr_camera, lights, ibl_index: int, ldr_out, deadline_ms: float = 0.0):
+        r = F.epbr_request()
+        r.format, r.width, r.height, r.ibl_index = fmt, cam.width, cam.height, ibl_index
+        for i, a in enumerate(rts):
+            if a is not None:
+                r.rt[i] = _host_ptr(a)
+        r.camera = cam
+        n = 0 if lights is None else len(lights)
+        r.lights = _host_ptr(lights) if n else None
+        r.num_lights = n
+        r.ldr_out = _host_ptr(ldr_out)
+        r.deadline_ms = deadline_ms
+        return r
+
+    def request_bytes(self, r: F.epbr_request) -> int:
+        n = C.c_size_t()
+        _check(lib().epbr_serve_request_bytes(C.byref(r), C.byref(n)))
+        return n.value
+
+    def epbr_serve_submit(self, r: F.epbr_request, keep=()) -> int:
+        t = C.c_uint64()
+        _check(lib().epbr_serve_submit(self.handle, C.byref(r), C.byref(t)))
+        self._live[t.value] = (r, keep)
+        return t.value
+
+    submit = epbr_serve_submit
+
+    def epbr_serve_wait(self, ticket: int, timeout_ms: int = 60000) -> F.epbr_result:
+        res = F.epbr_result()
+        _check(lib().epbr_serve_wait(self.handle, ticket, timeout_ms, C.byref(res)))
+        self._live.pop(ticket, None)
+        return res
+
+    wait = epbr_serve_wait
+
+    def epbr_serve_poll(self, ticket: int):
+        res, done = F.epbr_result(), C.c_int32()
+        _check(lib().epbr_serve_poll(self.handle, ticket, C.byref(done), C.byref(res)))
+        if done.value:
+            self._live.pop(ticket, None)
+            return res
+        return None
+
+    poll = epbr_serve_poll
+
+    def stats(self) -> F.epbr_serve_stats:
+        st = F.epbr_serve_stats()
+        _check(lib().epbr_serve_get_stats(self.handle, C.byref(st)))
+        return st
+
+    def close(self):
+        if self.handle:
+            lib().epbr_serve_destroy(self.handle)
+            self.handle = C.c_void_p()
+            self._live.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

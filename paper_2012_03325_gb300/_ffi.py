@@ -95,6 +95,30 @@ class epbr_batch_params(C.Structure):
                 ("light_chunk", C.c_int32)]
 
 
+class epbr_serve_config(C.Structure):
+    _fields_ = [("memory_budget", C.c_size_t), ("max_in_flight", C.c_int32), ("num_streams", C.c_int32),
+                ("ibls", C.c_void_p), ("num_ibls", C.c_int32), ("flags", C.c_uint32), ("ssao", epbr_ssao_params),
+                ("tonemap", epbr_tonemap_params)]
+
+
+class epbr_request(C.Structure):
+    _fields_ = [("format", C.c_int32), ("width", C.c_int32), ("height", C.c_int32), ("ibl_index", C.c_int32),
+                ("rt", C.c_void_p * 4), ("camera", epbr_camera), ("lights", C.c_void_p), ("num_lights", C.c_int32),
+                ("reserved", C.c_int32), ("ldr_out", C.c_void_p), ("deadline_ms", C.c_double)]
+
+
+class epbr_result(C.Structure):
+    _fields_ = [("status", C.c_int32), ("deferred", C.c_int32), ("queue_ms", C.c_double),
+                ("latency_ms", C.c_double), ("message", C.c_char * 160)]
+
+
+class epbr_serve_stats(C.Structure):
+    _fields_ = [("submitted", C.c_uint64), ("admitted", C.c_uint64), ("completed", C.c_uint64),
+                ("deferred", C.c_uint64), ("rejected", C.c_uint64), ("timed_out", C.c_uint64),
+                ("failed", C.c_uint64), ("in_flight", C.c_int32), ("queued", C.c_int32),
+                ("bytes_in_use", C.c_size_t), ("peak_bytes", C.c_size_t)]
+
+
 P = C.POINTER
 vp, i32, i64, sz = C.c_void_p, C.c_int32, C.c_int64, C.c_size_t
 
@@ -124,6 +148,13 @@ PROTOTYPES = {
     "epbr_batch_set_plan": [vp, i32, i32, i32, i32],
     "epbr_batch_destroy": [vp],
     "epbr_render_batch": [P(epbr_view), i32, P(epbr_ibl), i32, P(epbr_batch_params), vp],
+    "epbr_serve_create": [P(epbr_serve_config), P(vp)],
+    "epbr_serve_request_bytes": [P(epbr_request), P(sz)],
+    "epbr_serve_submit": [vp, P(epbr_request), P(C.c_uint64)],
+    "epbr_serve_poll": [vp, C.c_uint64, P(i32), P(epbr_result)],
+    "epbr_serve_wait": [vp, C.c_uint64, i32, P(epbr_result)],
+    "epbr_serve_get_stats": [vp, P(epbr_serve_stats)],
+    "epbr_serve_destroy": [vp],
 }
 OTHER = {"epbr_last_error": ([], C.c_char_p), "epbr_version": ([], C.c_char_p)}
 

@@ -410,8 +410,7 @@ static epbr_status build_tiles(epbr_batch* b) {
 
 static epbr_status add_kernel(epbr_batch* b, cudaGraphNode_t* node, const cudaGraphNode_t* dep, void* func,
                               dim3 grid, dim3 block, void** args) {
-  cudaKernelNodeParams kp;
-  memset(&kp, 0, sizeof(kp));
+  cudaKernelNodeParams kp = {};
   kp.func = func;
   kp.gridDim = grid;
   kp.blockDim = block;
@@ -444,8 +443,7 @@ static epbr_status build_graph(epbr_batch* b) {
     a[3] = &b->ntiles;
     a[4] = &b->d_counter;
     a[5] = &b->bp;
-    cudaMemsetParams mp;
-    memset(&mp, 0, sizeof(mp));
+    cudaMemsetParams mp = {};
     mp.dst = b->d_counter;
     mp.elementSize = 4;
     mp.width = 1;
