@@ -12,9 +12,12 @@
 
 namespace epbr {
 
-constexpr int kShadeBX = 32, kShadeBY = 8;
+#ifndef EPBR_SHADE_BY
+#define EPBR_SHADE_BY 4  // block rows (block = 32 x EPBR_SHADE_BY threads, one pixel each)
+#endif
+constexpr int kShadeBX = 32, kShadeBY = EPBR_SHADE_BY;
 #ifndef EPBR_SHADE_MIN_BLOCKS
-#define EPBR_SHADE_MIN_BLOCKS 4  // resident 256-thread blocks per SM the register budget targets
+#define EPBR_SHADE_MIN_BLOCKS 8  // resident blocks per SM the register budget targets (64 registers)
 #endif
 
 // One thread per pixel of a 32x8 tile.  The G-buffer loads are issued before the lights are

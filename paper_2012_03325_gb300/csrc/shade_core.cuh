@@ -166,7 +166,8 @@ __device__ __forceinline__ Px px_setup(const GbufDev& g, const CamDev& cam, int 
   return px_decode<FMT>(px_load<FMT>(g, x, y), cam, x, y);
 }
 
-// Lights staged in shared memory as pairs (pos.xyz, -), (intensity * color.rgb, -).  Returns
+// Lights staged in shared memory as pairs (pos.xyz, Ic.r), (Ic.rgb, -) with Ic = intensity *
+// colour, so a monochrome light needs only the first float4.  Returns
 // whether every light this thread staged is monochrome (equal colour channels); callers combine
 // the flags with __syncthreads_and to pick the monochrome loop for the chunk.
 __device__ __forceinline__ bool stage_lights(float4* s_lights, const float4* __restrict__ lights, int first,
@@ -175,8 +176,8 @@ __device__ __forceinline__ bool stage_lights(float4* s_lights, const float4* __r
   for (int q = tid; q < cnt; q += nthreads) {
     float4 a = __ldg(lights + 2 * (first + q));
     float4 c = __ldg(lights + 2 * (first + q) + 1);
-    s_lights[2 * q] = make_float4(a.x, a.y, a.z, 0.0f);
     float4 ic = make_float4(a.w * c.x, a.w * c.y, a.w * c.z, 0.0f);
+    s_lights[2 * q] = make_float4(a.x, a.y, a.z, ic.x);  // .w: Ic of a monochrome light
     s_lights[2 * q + 1] = ic;
     mono = mono && ic.x == ic.y && ic.y == ic.z;
   }
@@ -221,16 +222,19 @@ __device__ __forceinline__ LightTerms light_terms(const Px& s, const Direct& d, 
   float3 L = xyz(lp) - s.P;
   float d2 = fmaf(L.x, L.x, fmaf(L.y, L.y, fmaf(L.z, L.z, 1e-30f)));
   float rs = rsqrt_ftz(d2);
-  float nl = dot3(s.n, L) * rs;
+  float3 l = L * rs;
+  float nl = dot3(s.n, l);
   float nlc = fmaxf(nl, 0.0f);
-  float lv = dot3(s.v, L) * rs;
-  float3 c = cross3(s.n, L) * rs + d.nxv;  // n x (l + v)
+  float lv = dot3(s.v, l);
+  // n x (l + v) = n x l + n x v, accumulated onto the per-pixel n x v
+  float3 c = f3(fmaf(s.n.y, l.z, fmaf(-s.n.z, l.y, d.nxv.x)), fmaf(s.n.z, l.x, fmaf(-s.n.x, l.z, d.nxv.y)),
+                fmaf(s.n.x, l.y, fmaf(-s.n.y, l.x, d.nxv.z)));
   float c2 = fmaf(c.x, c.x, fmaf(c.y, c.y, fmaf(c.z, c.z, 1e-18f)));
   float ns = nl + s.nv_raw;
   float hh = fmaf(2.0f, lv, 2.000001f);
   float den = fmaf(ns * ns, d.a2, c2);
   float xx = fmaf(-0.5f * hh, rsqrt_ftz(hh), 1.0f);  // 1 - v.h, v.h = |l + v| / 2
-  float x2 = xx * xx, fc = x2 * x2 * xx;
+  float fc = ex2_ftz(5.0f * lg2_ftz(fabsf(xx)));     // (1 - v.h)^5 (|xx|: v.h may round above 1)
   float w = rs * rs * nlc;  // (n.l) / d^2
   float spec = hh * hh * rcp_ftz(den * den * fmaf(nlc, d.omk, d.k));
   LightTerms t;
@@ -267,8 +271,9 @@ __device__ __forceinline__ void px_direct_mono(const Px& s, Direct& d, const flo
   float sa = 0.0f, sb = 0.0f, sbf = 0.0f;
 #pragma unroll 4
   for (int i = 0; i < cnt; ++i) {
-    float ic = s_lights[2 * i + 1].x;
-    LightTerms t = light_terms(s, d, s_lights[2 * i]);
+    float4 lp = s_lights[2 * i];
+    float ic = lp.w;
+    LightTerms t = light_terms(s, d, lp);
     sa = fmaf(ic, t.a, sa);
     sb = fmaf(ic, t.b, sb);
     sbf = fmaf(ic, t.bf, sbf);
