@@ -23,6 +23,10 @@ __constant__ float c_srgb8[256] = {
 };
 
 constexpr int kLightChunk = 256;
+#ifndef EPBR_LIGHT_UNROLL
+#define EPBR_LIGHT_UNROLL 8
+#endif
+constexpr int kLightUnroll = EPBR_LIGHT_UNROLL;  // light-loop unrolling of the monochrome loop
 
 struct IblDev {
   MapDev irr;
@@ -234,7 +238,11 @@ __device__ __forceinline__ LightTerms light_terms(const Px& s, const Direct& d, 
   float hh = fmaf(2.0f, lv, 2.000001f);
   float den = fmaf(ns * ns, d.a2, c2);
   float xx = fmaf(-0.5f * hh, rsqrt_ftz(hh), 1.0f);  // 1 - v.h, v.h = |l + v| / 2
-  float fc = ex2_ftz(5.0f * lg2_ftz(fabsf(xx)));     // (1 - v.h)^5 (|xx|: v.h may round above 1)
+#ifdef EPBR_FC_POW5
+  float x2 = xx * xx, fc = x2 * x2 * xx;
+#else
+  float fc = ex2_ftz(5.0f * lg2_ftz(fabsf(xx)));  // (1 - v.h)^5 (|xx|: v.h may round above 1)
+#endif
   float w = rs * rs * nlc;  // (n.l) / d^2
   float spec = hh * hh * rcp_ftz(den * den * fmaf(nlc, d.omk, d.k));
   LightTerms t;
@@ -269,7 +277,7 @@ __device__ __forceinline__ void px_direct(const Px& s, Direct& d, const float4* 
 // Adds `cnt` staged monochrome lights (Ic_r = Ic_g = Ic_b).
 __device__ __forceinline__ void px_direct_mono(const Px& s, Direct& d, const float4* s_lights, int cnt) {
   float sa = 0.0f, sb = 0.0f, sbf = 0.0f;
-#pragma unroll 4
+#pragma unroll(kLightUnroll)
   for (int i = 0; i < cnt; ++i) {
     float4 lp = s_lights[2 * i];
     float ic = lp.w;

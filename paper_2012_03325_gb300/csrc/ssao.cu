@@ -8,8 +8,12 @@
 
 namespace epbr {
 
+#ifndef EPBR_SSAO_MIN_BLOCKS
+#define EPBR_SSAO_MIN_BLOCKS 4  // resident 256-thread blocks per SM the register budget targets
+#endif
+
 template <int FMT>
-__global__ void __launch_bounds__(256, 4) k_ssao_raw(GbufDev g, CamDev cam, SsaoDev p, float* __restrict__ ao,
+__global__ void __launch_bounds__(256, EPBR_SSAO_MIN_BLOCKS) k_ssao_raw(GbufDev g, CamDev cam, SsaoDev p, float* __restrict__ ao,
                                                   long long ao_pitch, int Wa, int Ha) {
   __shared__ float4 s_kernel[kMaxSsaoSamples];
   int tid = threadIdx.y * blockDim.x + threadIdx.x;

@@ -7,6 +7,10 @@
 namespace epbr {
 
 constexpr int kMaxSsaoSamples = 256;
+#ifndef EPBR_SSAO_UNROLL
+#define EPBR_SSAO_UNROLL 8
+#endif
+constexpr int kSsaoUnroll = EPBR_SSAO_UNROLL;  // samples whose depth taps are in flight together
 
 struct SsaoDev {
   int K, scale, R;
@@ -43,46 +47,55 @@ __device__ __forceinline__ float2 ssao_texel(const GbufDev& g, const CamDev& cam
   }
   float ix_scale = 0.5f * cam.W / cam.sx, iy_scale = 0.5f * cam.H / cam.sy;
   float occ = 0.0f;
+  // Branch-free so that the depth taps of several samples are in flight together: an invalid
+  // sample (behind the camera or off-screen) reads pixel (0, 0) and is masked out.
+#pragma unroll(kSsaoUnroll)
   for (int k = 0; k < p.K; ++k) {
     float4 ks = s_kernel[k];
     float3 S = P + p.radius * (t * ks.x + b * ks.y + n * ks.z);
     float eS = -S.z;
-    if (!(eS > 0.0f)) continue;
     float inv = rcp_ftz(eS);
     float x = fmaf(S.x * inv, ix_scale, 0.5f * cam.W);
     float y = fmaf(-S.y * inv, iy_scale, 0.5f * cam.H);
-    if (!(x >= 0.0f && x < (float)cam.W && y >= 0.0f && y < (float)cam.H)) continue;
-    int ix = min((int)x, cam.W - 1), iy = min((int)y, cam.H - 1);
+    bool valid = eS > 0.0f && x >= 0.0f && x < (float)cam.W && y >= 0.0f && y < (float)cam.H;
+    int ix = valid ? min((int)x, cam.W - 1) : 0, iy = valid ? min((int)y, cam.H - 1) : 0;
     float eb = gb_depth(g, ix, iy);
-    if (!is_surface(eb)) continue;
-    if (eb <= eS - p.bias) occ += smoothstep01(p.radius * rcp_ftz(fabsf(e - eb)));
+    bool hit = valid && is_surface(eb) && eb <= eS - p.bias;
+    occ += hit ? smoothstep01(p.radius * rcp_ftz(fabsf(e - eb))) : 0.0f;
   }
   return make_float2(1.0f - occ / p.K, e);
 }
 
 // Depth-aware blur of one AO texel from shared-memory tiles: `ao` and `ed` point at the
 // centre texel inside row-major tiles of row pitch `tp` that hold R texels around it (taps
-// outside the image staged as background, e = +inf).  Weight
-//   w = exp(-(dx^2 + dy^2) / (2 sigma_s^2)) * exp(-|e_q - e_p| / (sigma_z e_p)),
-// evaluated as one exponential; background centre texels return 1.
-__device__ __forceinline__ float ssao_blur_texel(const SsaoDev& p, const float* ao, const float* ed, int tp) {
+// outside the image staged as background: AO 0, depth +inf).  Weight
+//   w = exp(-(dx^2 + dy^2) / (2 sigma_s^2)) * exp(-|e_q - e_p| / (sigma_z e_p))
+// as one base-2 exponential; a background tap has |e_q - e_p| = +inf and so weight exactly 0.
+// Background centre texels return 1.  RT > 0 fixes the radius at compile time (R = RT).
+template <int RT>
+__device__ __forceinline__ float ssao_blur_texel_r(const SsaoDev& p, const float* ao, const float* ed, int tp) {
   float ep = ed[0];
   if (!is_surface(ep)) return 1.0f;
+  const int R = RT > 0 ? RT : p.R;
   float ks = -1.4426950408889634f / (2.0f * p.sigma_s * p.sigma_s);
-  float kz = -1.4426950408889634f / (p.sigma_z * ep);
+  float kz = -1.4426950408889634f * rcp_ftz(p.sigma_z * ep);
   float num = 0.0f, den = 0.0f;
-  for (int dy = -p.R; dy <= p.R; ++dy) {
+#pragma unroll
+  for (int dy = -R; dy <= R; ++dy) {
     const float* ra = ao + dy * tp;
     const float* re = ed + dy * tp;
-    for (int dx = -p.R; dx <= p.R; ++dx) {
-      float eq = re[dx];
-      if (!is_surface(eq)) continue;
-      float w = exp2f(fmaf((float)(dx * dx + dy * dy), ks, fabsf(eq - ep) * kz));
+#pragma unroll
+    for (int dx = -R; dx <= R; ++dx) {
+      float w = ex2_ftz(fmaf(fabsf(re[dx] - ep), kz, (float)(dx * dx + dy * dy) * ks));
       num = fmaf(w, ra[dx], num);
       den += w;
     }
   }
   return num / den;
+}
+
+__device__ __forceinline__ float ssao_blur_texel(const SsaoDev& p, const float* ao, const float* ed, int tp) {
+  return p.R == 3 ? ssao_blur_texel_r<3>(p, ao, ed, tp) : ssao_blur_texel_r<0>(p, ao, ed, tp);
 }
 
 }  // namespace epbr
