@@ -3,7 +3,8 @@
 //   k_irradiance_part   exact-quadrature irradiance, per-block partial sums over a slice of
 //                       source texels staged in shared memory
 //   k_irradiance_final  sums the partials in a fixed order (deterministic) and normalises
-//   k_prefilter         GGX-prefiltered levels 1..M-1, one thread per output texel
+//   k_prefilter         GGX-prefiltered levels 1..M-1, one thread per output texel, the level's
+//                       sample set tabulated once per block in shared memory
 #include <algorithm>
 #include <mutex>
 
@@ -180,34 +181,81 @@ struct ChainDev {
   float4* dst[EPBR_MAX_LEVELS];
 };
 
+// One grid row per level (blockIdx.y = m - 1).  With n = v, a GGX half vector h with
+// tangent-space components (sin t cos p, sin t sin p, cos t) gives
+//   l = 2 (n.h) h - n = T (2 h_z h_x) + B (2 h_z h_y) + n (2 h_z^2 - 1),   n.l = 2 h_z^2 - 1,
+// both functions of the sample and the level only.  Each block therefore tabulates its level's
+// samples once, keeping those with n.l > 0 in sample order (a deterministic compaction), and the
+// per-texel loop is the rotation into the texel's frame plus the environment lookup.
+constexpr int kPrefilterMaxSamples = 2048;
+
+// Sample `sidx` of N for alpha^2 = a2 as (2 h_z h_x, 2 h_z h_y, n.l, -); kept iff n.l > 0.  Both
+// compaction passes call this, so they agree on every decision.
+__device__ __forceinline__ float4 prefilter_sample(int sidx, float a2, float invN) {
+  float xi2 = hammersley_xi2((unsigned)sidx);
+  float inv = 1.0f / fmaf(a2 - 1.0f, xi2, 1.0f);
+  float ct = sqrtf((1.0f - xi2) * inv), st = sqrtf(a2 * xi2 * inv);
+  float sp, cp;
+  sincospif(2.0f * (sidx * invN), &sp, &cp);
+  return make_float4(2.0f * ct * st * cp, 2.0f * ct * st * sp, fmaf(2.0f * ct, ct, -1.0f), 0.0f);
+}
+
 __global__ void __launch_bounds__(256) k_prefilter(MapDev src, ChainDev ch, int N) {
-  long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (gid >= ch.off[ch.nlev]) return;
-  int li = 0;
-  while (gid >= ch.off[li + 1]) ++li;
-  int m = li + 1;
-  long long t = gid - ch.off[li];
-  int W = ch.W[m], H = ch.H[m];
+  __shared__ float4 s_smp[kPrefilterMaxSamples];  // kept samples, in sample order
+  __shared__ int s_base[kPrefilterMaxSamples / 32 + 1];
+  const int m = blockIdx.y + 1;
+  const int W = ch.W[m], H = ch.H[m];
+  const long long ntex = (long long)W * H;
+  const long long t0 = (long long)blockIdx.x * blockDim.x;
+  if (t0 >= ntex) return;  // block-uniform
+  const float r = (float)m / (float)(ch.M - 1);
+  const float a2 = r * r * r * r;
+  const float invN = 1.0f / N;
+  const int groups = (N + 31) / 32;
+  const int lane = threadIdx.x & 31;
+  // pass 1: kept samples per group of 32
+  for (int gi = threadIdx.x / 32; gi < groups; gi += blockDim.x / 32) {
+    int sidx = gi * 32 + lane;
+    bool keep = sidx < N && prefilter_sample(sidx, a2, invN).z > 0.0f;
+    unsigned bal = __ballot_sync(0xffffffffu, keep);
+    if (lane == 0) s_base[gi] = __popc(bal);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {  // exclusive prefix over the groups, in sample order
+    int acc = 0;
+    for (int gi = 0; gi < groups; ++gi) {
+      int c = s_base[gi];
+      s_base[gi] = acc;
+      acc += c;
+    }
+    s_base[groups] = acc;
+  }
+  __syncthreads();
+  // pass 2: the kept samples at their compacted positions
+  for (int gi = threadIdx.x / 32; gi < groups; gi += blockDim.x / 32) {
+    int sidx = gi * 32 + lane;
+    float4 e = sidx < N ? prefilter_sample(sidx, a2, invN) : make_float4(0, 0, 0, 0);
+    bool keep = sidx < N && e.z > 0.0f;
+    unsigned bal = __ballot_sync(0xffffffffu, keep);
+    if (keep) s_smp[s_base[gi] + __popc(bal & ((1u << lane) - 1u))] = e;
+  }
+  __syncthreads();
+  const int ns = s_base[groups];
+  const long long t = t0 + threadIdx.x;
+  if (t >= ntex) return;
   int i = (int)(t % W), j = (int)(t / W);
   float3 n = texel_dir(i, j, W, H);
-  float r = (float)m / (float)(ch.M - 1);
-  float a2 = r * r * r * r;
   float3 tt, bb;
   onb(n, tt, bb);
   Kahan acc[4];
-  float invN = 1.0f / N;
-  for (int s = 0; s < N; ++s) {
-    float3 h = ggx_half(s * invN, hammersley_xi2((unsigned)s), a2, tt, bb, n);
-    float nh = dot3(n, h);
-    float nl = fmaf(2.0f * nh, nh, -1.0f);  // n.l with v = n, l = 2 (n.h) h - n
-    if (nl > 0.0f) {
-      float3 l = (2.0f * nh) * h - n;
-      float3 L = equirect_lookup(src, l);
-      acc[0].add(L.x * nl);
-      acc[1].add(L.y * nl);
-      acc[2].add(L.z * nl);
-      acc[3].add(nl);
-    }
+  for (int q = 0; q < ns; ++q) {
+    float4 e = s_smp[q];
+    float3 l = tt * e.x + bb * e.y + n * e.z;
+    float3 L = equirect_lookup(src, l);
+    acc[0].add(L.x * e.z);
+    acc[1].add(L.y * e.z);
+    acc[2].add(L.z * e.z);
+    acc[3].add(e.z);
   }
   float inv = 1.0f / (acc[3].s - acc[3].c);
   ch.dst[m][t] = make_float4((acc[0].s - acc[0].c) * inv, (acc[1].s - acc[1].c) * inv,
@@ -340,7 +388,8 @@ extern "C" epbr_status epbr_prefilter(const epbr_env* env, int32_t N, const epbr
   epbr_status st = validate_env(env);
   if (st) return st;
   if ((st = validate_ibl_for(ibl, env->width, env->height))) return st;
-  if (N < 1 || N > (1 << 24)) return fail(EPBR_ERR_INVALID_ARG, "prefilter: samples %d invalid", N);
+  if (N < 1 || N > kPrefilterMaxSamples)
+    return fail(EPBR_ERR_INVALID_ARG, "prefilter: samples %d outside [1, %d]", N, kPrefilterMaxSamples);
   cudaStream_t s = (cudaStream_t)stream;
   if (cudaMemcpyAsync(ibl->level[0], env->texels, (size_t)env->width * env->height * 16,
                       cudaMemcpyDeviceToDevice, s) != cudaSuccess)
@@ -357,8 +406,9 @@ extern "C" epbr_status epbr_prefilter(const epbr_env* env, int32_t N, const epbr
   }
   for (int li = 0; li < ch.nlev; ++li) ch.off[li + 1] = ch.off[li] + (long long)ch.W[li + 1] * ch.H[li + 1];
   MapDev src{(const float4*)env->texels, env->width, env->height};
-  long long total = ch.off[ch.nlev];
-  k_prefilter<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(src, ch, N);
+  long long most = (long long)ch.W[1] * ch.H[1];  // level 1 has the most texels
+  dim3 grid((unsigned)((most + 255) / 256), (unsigned)ch.nlev);
+  k_prefilter<<<grid, 256, 0, s>>>(src, ch, N);
   if ((st = check_launch("k_prefilter"))) return st;
   return ok();
 }
