@@ -51,6 +51,22 @@ def dist_env():
     return int(os.environ.get("RANK", 0)), int(os.environ.get("LOCAL_RANK", 0)), int(os.environ.get("WORLD_SIZE", 1))
 
 
+def max_over_ranks(local_ms: float, device=None) -> float:
+    """Length of the job's timed region: the slowest rank's (max over ranks; no-op alone)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return local_ms
+    t = torch.tensor([float(local_ms)], device=device if device is not None else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_mpx_per_s(px_per_step_per_rank: int, steps: int, world: int, job_ms: float) -> float:
+    """Whole-job throughput: pixels every rank shaded over the slowest rank's time."""
+    return px_per_step_per_rank * steps * world / (job_ms * 1e-3) / 1e6
+
+
 def workload_inputs(name: str):
     c = synth.CONFIGS[name]
     sc = synth.make_scene(c["seed"], c["width"], c["height"], c["spheres"], c["lights"])
@@ -378,10 +394,8 @@ def run_gpu(args):
     step_ms = [a.elapsed_time(b) for a, b in ev]
     total_ms = sum(step_ms)
     shade_ms = statistics.mean(a.elapsed_time(b) for a, b in ev_shade)
+    total_ms = max_over_ranks(total_ms, dev)
     if world > 1:
-        tt = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        total_ms = float(tt.item())
         dist.barrier()
 
     # end to end through the C ABI with host buffers: pinned G-buffer + lights in, RGBA8 out,
@@ -460,11 +474,7 @@ def run_gpu(args):
         s_dn.wait_stream(st_)
     e_end.record(s_dn)
     torch.cuda.synchronize()
-    e2e_total = e_start.elapsed_time(e_end)
-    if world > 1:
-        tt = torch.tensor([e2e_total], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        e2e_total = float(tt.item())
+    e2e_total = max_over_ranks(e_start.elapsed_time(e_end), dev)
     # the result of the last frame equals the device-only frame's (same inputs)
     assert torch.equal(ldr_h[(args.steps - 1) % 2], ldr.cpu()), "end-to-end frame differs from the device frame"
 
@@ -472,9 +482,8 @@ def run_gpu(args):
         if world > 1:
             dist.destroy_process_group()
         return
-    px = W * H * args.steps * world
-    value = px / (total_ms * 1e-3) / 1e6
-    e2e_value = px / (e2e_total * 1e-3) / 1e6
+    value = job_mpx_per_s(W * H, args.steps, world, total_ms)
+    e2e_value = job_mpx_per_s(W * H, args.steps, world, e2e_total)
     clocks = clk.summary()
     props = torch.cuda.get_device_properties(dev)
     sms = props.multi_processor_count
