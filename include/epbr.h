@@ -106,7 +106,7 @@ typedef struct epbr_gbuffer {
 } epbr_gbuffer;
 
 /* HDR environment map (Sec. 3.1: every texel acts as a light source).  DEVICE float4 texels
- * (r, g, b, ignored), dense rows of `width` texels.  Host struct. */
+ * (r, g, b, ignored), dense rows of `width` texels, at most 2^28 texels.  Host struct. */
 typedef struct epbr_env {
   const float* texels;
   int32_t width;

@@ -80,6 +80,8 @@ epbr_status validate_env(const epbr_env* e) {
   if (!e || !e->texels) return fail(EPBR_ERR_INVALID_ARG, "env or env->texels is NULL");
   if (e->width < 1 || e->height < 1 || e->width > (1 << 16) || e->height > (1 << 16))
     return fail(EPBR_ERR_INVALID_ARG, "env size %dx%d outside [1, 65536]", e->width, e->height);
+  if ((long long)e->width * e->height > (1LL << 28))
+    return fail(EPBR_ERR_INVALID_ARG, "env has %lld texels, more than 2^28", (long long)e->width * e->height);
   if (!aligned(e->texels, 16)) return fail(EPBR_ERR_INVALID_ARG, "env texels not 16-byte aligned");
   return EPBR_OK;
 }
@@ -101,8 +103,8 @@ extern "C" epbr_status epbr_ibl_layout(const epbr_ibl_params* p, int32_t W, int3
   if (p->lut_size < 1 || p->lut_size > 4096 || p->irr_width < 1 || p->irr_height < 1 ||
       p->irr_width > 4096 || p->irr_height > 4096 || p->prefilter_samples < 1 || p->lut_samples < 1)
     return fail(EPBR_ERR_INVALID_ARG, "ibl params out of range");
-  if (W < 1 || H < 1 || W > (1 << 16) || H > (1 << 16))
-    return fail(EPBR_ERR_INVALID_ARG, "env size %dx%d outside [1, 65536]", W, H);
+  if (W < 1 || H < 1 || W > (1 << 16) || H > (1 << 16) || (long long)W * H > (1LL << 28))
+    return fail(EPBR_ERR_INVALID_ARG, "env size %dx%d outside [1, 65536]^2 or above 2^28 texels", W, H);
   size_t off = 0;
   size_t irr_off = off;
   off = align256(off + (size_t)p->irr_width * p->irr_height * 16);

@@ -110,9 +110,9 @@ __device__ __forceinline__ float3 equirect_bilinear(const MapDev m, float u, flo
   int i0 = ix < 0 ? ix + m.W : (ix >= m.W ? ix - m.W : ix);
   int i1 = i0 + 1 == m.W ? 0 : i0 + 1;
   int j0 = min(max(iy, 0), m.H - 1), j1 = min(max(iy + 1, 0), m.H - 1);
-  const float4* r0 = m.texels + (size_t)j0 * m.W;
-  const float4* r1 = m.texels + (size_t)j1 * m.W;
-  float4 a = __ldg(r0 + i0), b = __ldg(r0 + i1), p = __ldg(r1 + i0), q = __ldg(r1 + i1);
+  int r0 = j0 * m.W, r1 = j1 * m.W;  // 32-bit: maps hold at most 2^28 texels
+  float4 a = __ldg(m.texels + (r0 + i0)), b = __ldg(m.texels + (r0 + i1));
+  float4 p = __ldg(m.texels + (r1 + i0)), q = __ldg(m.texels + (r1 + i1));
   float3 top = xyz(a) + fx * (xyz(b) - xyz(a));
   float3 bot = xyz(p) + fx * (xyz(q) - xyz(p));
   return top + fy * (bot - top);

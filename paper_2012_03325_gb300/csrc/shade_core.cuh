@@ -199,17 +199,18 @@ __device__ __forceinline__ bool stage_lights(float4* s_lights, const float4* __r
 struct Direct {
   float3 sa, sb, sbf;  // sums of Ic w (1 - fc), Ic w spec', Ic w spec' fc
   float3 nxv;          // n x v: n x (l + v) = (n x L) / |L| + n x v
-  float a2vv, a2, k, omk;
+  float a2vv, alpha, nva, k, omk;  // nva = alpha n.v: alpha (n.l + n.v) = fma(n.l, alpha, nva)
 };
 
 __device__ __forceinline__ Direct px_direct_begin(const Px& s) {
   Direct d;
   d.sa = d.sb = d.sbf = f3(0, 0, 0);
   float alpha = s.rough * s.rough;
-  d.a2 = alpha * alpha;
+  d.alpha = alpha;
+  d.nva = alpha * s.nv_raw;
   d.k = (s.rough + 1.0f) * (s.rough + 1.0f) * 0.125f;
   d.omk = 1.0f - d.k;
-  d.a2vv = d.a2 * rcp_ftz(4.0f * kPi * fmaf(s.nv, d.omk, d.k));  // alpha^2 G1(v) / (4 pi n.v)
+  d.a2vv = alpha * alpha * rcp_ftz(4.0f * kPi * fmaf(s.nv, d.omk, d.k));  // alpha^2 G1(v) / (4 pi n.v)
   d.nxv = cross3(s.n, s.v);
   return d;
 }
@@ -234,10 +235,10 @@ __device__ __forceinline__ LightTerms light_terms(const Px& s, const Direct& d, 
   float3 c = f3(fmaf(s.n.y, l.z, fmaf(-s.n.z, l.y, d.nxv.x)), fmaf(s.n.z, l.x, fmaf(-s.n.x, l.z, d.nxv.y)),
                 fmaf(s.n.x, l.y, fmaf(-s.n.y, l.x, d.nxv.z)));
   float c2 = fmaf(c.x, c.x, fmaf(c.y, c.y, fmaf(c.z, c.z, 1e-18f)));
-  float ns = nl + s.nv_raw;
-  float hh = fmaf(2.0f, lv, 2.000001f);
-  float den = fmaf(ns * ns, d.a2, c2);
-  float xx = fmaf(-0.5f * hh, rsqrt_ftz(hh), 1.0f);  // 1 - v.h, v.h = |l + v| / 2
+  float nsa = fmaf(nl, d.alpha, d.nva);  // alpha n.(l + v)
+  float hh = fmaf(2.0f, lv, 2.000001f);  // |l + v|^2
+  float den = fmaf(nsa, nsa, c2);
+  float xx = fmaf(-0.5f, sqrt_ftz(hh), 1.0f);  // 1 - v.h, v.h = |l + v| / 2
 #ifdef EPBR_FC_POW5
   float x2 = xx * xx, fc = x2 * x2 * xx;
 #else
