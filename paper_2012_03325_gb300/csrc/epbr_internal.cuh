@@ -37,7 +37,36 @@ __device__ __forceinline__ float dot3(float3 a, float3 b) { return fmaf(a.x, b.x
 __device__ __forceinline__ float3 cross3(float3 a, float3 b) {
   return f3(fmaf(a.y, b.z, -a.z * b.y), fmaf(a.z, b.x, -a.x * b.z), fmaf(a.x, b.y, -a.y * b.x));
 }
-__device__ __forceinline__ float3 normalize3(float3 a) { return a * rsqrtf(dot3(a, a)); }
+// Hardware approximations with denormal flushing (one MUFU instruction each, no fix-up code):
+// relative error ~2^-22, far inside the 1e-4 tolerance of the method.
+__device__ __forceinline__ float rsqrt_ftz(float x) {
+  float r;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+__device__ __forceinline__ float rcp_ftz(float x) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+__device__ __forceinline__ float ex2_ftz(float x) {
+  float r;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+__device__ __forceinline__ float lg2_ftz(float x) {
+  float r;
+  asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+
+__device__ __forceinline__ float sqrt_ftz(float x) {
+  float r;
+  asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+
+__device__ __forceinline__ float3 normalize3(float3 a) { return a * rsqrt_ftz(dot3(a, a)); }
 __device__ __forceinline__ float clamp01(float x) { return fminf(fmaxf(x, 0.0f), 1.0f); }
 __device__ __forceinline__ float3 xyz(float4 a) { return f3(a.x, a.y, a.z); }
 
@@ -90,15 +119,29 @@ struct MapDev {
   int W, H;
 };
 
-__device__ __forceinline__ float sqrt_ftz(float x) {
-  float r;
-  asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
-  return r;
+// atan2 by octant reduction and an odd polynomial fitted to atan on [0, 1] (coefficients from
+// gen_atan_poly.py, |error| ~1e-7 rad in FP32).  Signed zeros follow IEEE 754: the sign bit of
+// x picks the half plane, so atan2(+-0, -0) = +-pi and atan2(+-0, +0) = +-0.
+__device__ __forceinline__ float atan2_poly(float y, float x) {
+  constexpr float c[8] = {
+#include "atan_poly.inc"
+  };
+  float ax = fabsf(x), ay = fabsf(y);
+  float mx = fmaxf(ax, ay), mn = fminf(ax, ay);
+  float t = mn * rcp_ftz(fmaxf(mx, 1e-30f));
+  float s = t * t;
+  float p = c[7];
+#pragma unroll
+  for (int k = 6; k >= 0; --k) p = fmaf(p, s, c[k]);
+  float r = t * p;
+  r = ay > ax ? 1.57079632679489662f - r : r;
+  r = signbit(x) ? 3.14159265358979324f - r : r;
+  return copysignf(r, y);
 }
 
 __device__ __forceinline__ void dir_to_uv(float3 d, float& u, float& v) {
-  u = fmaf(atan2f(d.x, -d.z), kInv2Pi, 0.5f);
-  v = atan2f(sqrt_ftz(fmaf(d.x, d.x, d.z * d.z)), d.y) * kInvPi;
+  u = fmaf(atan2_poly(d.x, -d.z), kInv2Pi, 0.5f);
+  v = atan2_poly(sqrt_ftz(fmaf(d.x, d.x, d.z * d.z)), d.y) * kInvPi;
 }
 
 // Bilinear read at (u, v): wrap in u, clamp in v.
@@ -131,29 +174,6 @@ __device__ __forceinline__ void onb(float3 n, float3& t, float3& b) {
   float c = n.x * n.y * a;
   t = f3(fmaf(s * n.x * n.x, a, 1.0f), s * c, -s * n.x);
   b = f3(c, fmaf(n.y * n.y, a, s), -n.y);
-}
-
-// Hardware approximations with denormal flushing (one MUFU instruction each, no fix-up code):
-// relative error ~2^-22, far inside the 1e-4 tolerance of the method.
-__device__ __forceinline__ float rsqrt_ftz(float x) {
-  float r;
-  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
-  return r;
-}
-__device__ __forceinline__ float rcp_ftz(float x) {
-  float r;
-  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
-  return r;
-}
-__device__ __forceinline__ float ex2_ftz(float x) {
-  float r;
-  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
-  return r;
-}
-__device__ __forceinline__ float lg2_ftz(float x) {
-  float r;
-  asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
-  return r;
 }
 
 // Kahan-compensated accumulator.
