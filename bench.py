@@ -95,15 +95,18 @@ def config_dict(c, name, extra=None):
 # ------------------------------------------------------------------------------------------
 # algorithmic work of the compose kernel (per-unit figures)
 # ------------------------------------------------------------------------------------------
-FLOP_LIGHT_TEST = 20     # L = p - P, |L|^2, n.l test
+FLOP_LIGHT_TEST = 20     # L = p - P, |L|^2, normalisation, n.l test
 FLOP_LIGHT_LIT = 70      # the rest of Eq. 1 for a light with n.l > 0
-FLOP_IBL = 250           # split-sum ambient term with multiple scattering
-FLOP_BACKGROUND = 40     # environment lookup of a background pixel
+FLOP_IBL = 250           # split-sum ambient term with multiple scattering, times AO
+FLOP_DECODE = 60         # surface pixel: view ray, rotation, position, v and n normalised, F0, c_diff
+FLOP_BACKGROUND = 90     # background pixel: view ray, equirect mapping, bilinear read
+FLOP_TONEMAP = 36        # every pixel: exposure, ACES fit, clamp, sRGB transfer, rounding (x3)
 
 
 def compose_flops(sc, g, n_lights) -> tuple[float, dict]:
-    """Algorithmic FP32 FLOPs of one compose launch: per surface pixel, 20 per light for the
-    visibility test, 70 more per light with n.l > 0, 250 for IBL; 40 per background pixel."""
+    """Algorithmic FP32 FLOPs of one compose launch (with the fused tone map): per surface
+    pixel 60 for the decode, 20 per light for the visibility test, 70 more per light with
+    n.l > 0, 250 for IBL; 90 per background pixel; 36 per pixel for the tone map."""
     depth = g.depth
     surf = np.isfinite(depth)
     H, W = depth.shape
@@ -125,7 +128,8 @@ def compose_flops(sc, g, n_lights) -> tuple[float, dict]:
             lit += int(np.count_nonzero(np.einsum("ij,ij->i", L[:3] - P, n) > 0))
     ns = int(surf.sum())
     nb = int(surf.size - ns)
-    flops = ns * n_lights * FLOP_LIGHT_TEST + lit * FLOP_LIGHT_LIT + ns * FLOP_IBL + nb * FLOP_BACKGROUND
+    flops = (ns * (FLOP_DECODE + n_lights * FLOP_LIGHT_TEST + FLOP_IBL) + lit * FLOP_LIGHT_LIT + nb * FLOP_BACKGROUND
+             + (ns + nb) * FLOP_TONEMAP)
     return float(flops), {"surface_px": ns, "background_px": nb, "lit_pairs": lit}
 
 

@@ -13,11 +13,11 @@
 namespace epbr {
 
 #ifndef EPBR_SHADE_BY
-#define EPBR_SHADE_BY 4  // block rows (block = 32 x EPBR_SHADE_BY threads, one pixel each)
+#define EPBR_SHADE_BY 8  // block rows (block = 32 x EPBR_SHADE_BY threads, one pixel each)
 #endif
 constexpr int kShadeBX = 32, kShadeBY = EPBR_SHADE_BY;
 #ifndef EPBR_SHADE_MIN_BLOCKS
-#define EPBR_SHADE_MIN_BLOCKS 8  // resident blocks per SM the register budget targets (64 registers)
+#define EPBR_SHADE_MIN_BLOCKS 4  // resident blocks per SM the register budget targets (64 registers)
 #endif
 
 // One thread per pixel of a 32x8 tile.  The G-buffer loads are issued before the lights are
@@ -29,7 +29,11 @@ __global__ void __launch_bounds__(kShadeBX* kShadeBY, EPBR_SHADE_MIN_BLOCKS)
             long long hdr_pitch, uint8_t* ldr, long long ldr_pitch) {
   __shared__ float4 s_lights[2 * kLightChunk];
   int tid = threadIdx.y * kShadeBX + threadIdx.x;
-  int x = blockIdx.x * kShadeBX + threadIdx.x, y = blockIdx.y * kShadeBY + threadIdx.y;
+  // Rows are dispatched bottom-up: the costliest tiles (ground and objects) usually fill the
+  // bottom of a view and the cheap background the top, so the expensive work starts first and
+  // the tail of the launch is short.  Any order gives the same image.
+  int by = gridDim.y - 1 - blockIdx.y;
+  int x = blockIdx.x * kShadeBX + threadIdx.x, y = by * kShadeBY + threadIdx.y;
   bool inside = x < g.W && y < g.H;
   PxRaw raw;
   if (inside) raw = px_load<FMT>(g, x, y);
