@@ -170,10 +170,10 @@ def raycast_gbuffer(scene: Scene, width: int | None = None, height: int | None =
     mat = np.full((H, W), -1, np.int64)
     nrm = np.zeros((H, W, 3))
     # Ground square y = 0, |x|, |z| <= ground_half.
-    with np.errstate(divide="ignore", invalid="ignore"):
+    with np.errstate(divide="ignore", invalid="ignore"):  # rays parallel to or away from the plane
         tp = np.where(dy < 0.0, -eye[1] / dy, np.inf)
-    hx = eye[0] + tp * dx
-    hz = eye[2] + tp * dz
+        hx = eye[0] + tp * dx
+        hz = eye[2] + tp * dz
     gh = scene.ground_half
     hit = np.isfinite(tp) & (tp > 0) & (np.abs(hx) <= gh) & (np.abs(hz) <= gh)
     best = np.where(hit, tp, best)

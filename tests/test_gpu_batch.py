@@ -118,3 +118,22 @@ def test_render_batch_one_shot_and_validation():
     bad = ep.SsaoParams(sp.kernel, sp.noise, radius=0.5, scale=1, blur_radius=3)
     with pytest.raises(ep.EpbrError):
         ep.Batch(views, ibls, ep.batch_params(bad), keep=keep)
+
+
+def test_batch_colored_lights_equal_per_view():
+    ibls, views, keep, per, sp = _setup()
+    rng = np.random.default_rng(3)
+    for inp, d, *_ in per:  # recolour every view's lights in place (host and device)
+        if inp.lights.shape[0]:
+            inp.scene.lights[:, 4:7] = rng.uniform(0.1, 1.0, (inp.lights.shape[0], 3)).astype(np.float32)
+            d["lights"].copy_(torch.from_numpy(inp.scene.lights))
+    ref = _per_view(per, ibls, sp)
+    b = ep.Batch(views, ibls, ep.batch_params(sp), keep=keep)
+    for md in (ep.F.EPBR_BATCH_FUSED, ep.F.EPBR_BATCH_STAGED):
+        b.set_plan(md, 64, 32, 128)
+        b.launch()
+        torch.cuda.synchronize()
+        for (inp, _, ldr, hdr, _), (rh, rl, _) in zip(per, ref):
+            g, r = hdr.cpu().numpy()[..., :3], rh.cpu().numpy()[..., :3]
+            assert (np.abs(g - r) / np.maximum(np.abs(r), 1e-6)).max() <= 1e-6
+    b.close()

@@ -265,3 +265,59 @@ def test_invalid_arguments_raise():
         ep.epbr_brdf_lut(0, 16, torch.zeros(1, 1, 2, device="cuda"))
     with pytest.raises(ep.EpbrError):
         ep.epbr_tonemap(hdr, 7, ep.tonemap_params(), torch.zeros(16, 16, 4, dtype=torch.uint8, device="cuda"))
+
+
+def _color_lights(inp, seed, n_white=0):
+    rng = np.random.default_rng(seed)
+    L = inp.lights.copy()
+    L[:, 4:7] = rng.uniform(0.1, 1.0, (L.shape[0], 3)).astype(np.float32)
+    L[:n_white, 4:7] = 1.0
+    return L
+
+
+@pytest.mark.parametrize("NL,n_white", [(16, 0), (300, 290)])
+def test_shade_colored_lights(NL, n_white):
+    """Lights of arbitrary colour take the three-sums-per-channel loop; with 300 lights the
+    second 256-light chunk mixes colours into an otherwise monochrome list."""
+    inp = make_inputs("small", W=131, H=77, lights=NL)
+    inp.scene.lights = _color_lights(inp, 4, n_white)
+    d = gpu_inputs(inp)
+    ibl = gpu_ibl(inp, d["env"])
+    hdr = torch.zeros(inp.H, inp.W, 4, device="cuda")
+    ep.epbr_shade(d["gb"], d["cam"], d["lights"], ibl, ep.shade_params(ep.EPBR_SHADE_ALL), hdr)
+    gb = decoded(inp)
+    cam = oracle_camera(inp)
+    ref = oracle.shade(gb, cam, inp.lights, oracle_ibl(inp), ep.EPBR_SHADE_ALL)
+    check_hdr(np_(hdr)[..., :3], ref, REL_TOL_FP32, gb=gb, cam=cam, lights=inp.lights, ibl=oracle_ibl(inp),
+              flags=ep.EPBR_SHADE_ALL)
+
+
+def test_padded_row_pitches():
+    """Every image (G-buffer planes, AO, HDR, 8-bit) as a column slice of a wider allocation:
+    the kernels must follow the pitch, and results equal the dense-pitch run bit for bit."""
+    inp = make_inputs("small", W=150, H=70)
+    d = gpu_inputs(inp)
+    ibl = gpu_ibl(inp, d["env"])
+    pad = lambda t, extra: torch.zeros((t.shape[0], t.shape[1] + extra) + tuple(t.shape[2:]), dtype=t.dtype,
+                                       device="cuda")
+    rt = d["gb"].tensors
+    wide = [None if t is None else pad(t, 9) for t in rt]
+    for w, t in zip(wide, rt):
+        if w is not None:
+            w[:, :t.shape[1]] = t
+    gbp = ep.GBuffer.fp32(wide[0][:, :150], wide[1][:, :150], wide[3][:, :150])
+    sp = ep.SsaoParams(d["kernel"], d["noise"], radius=0.5)
+    Ha, Wa = sp.ao_shape(inp.W, inp.H)
+    outs = []
+    for gbx, padded in ((d["gb"], False), (gbp, True)):
+        ao = pad(torch.zeros(Ha, Wa, device="cuda"), 5)[:, :Wa] if padded else torch.zeros(Ha, Wa, device="cuda")
+        hdr = pad(torch.zeros(inp.H, inp.W, 4, device="cuda"), 3)[:, :inp.W] if padded else \
+            torch.zeros(inp.H, inp.W, 4, device="cuda")
+        ldr = pad(torch.zeros(inp.H, inp.W, 4, dtype=torch.uint8, device="cuda"), 7)[:, :inp.W] if padded else \
+            torch.zeros(inp.H, inp.W, 4, dtype=torch.uint8, device="cuda")
+        ep.epbr_ssao(gbx, d["cam"], sp, ao)
+        ep.epbr_shade_tonemap(gbx, d["cam"], d["lights"], ibl, ep.shade_params(ep.EPBR_SHADE_ALL, ao, 2), hdr,
+                              ep.EPBR_HDR_RGBA32F, ep.tonemap_params(), ldr)
+        outs.append((ao.cpu(), hdr.cpu(), ldr.cpu()))
+    for a, b in zip(*outs):
+        assert torch.equal(a, b)
