@@ -55,12 +55,13 @@ __global__ void __launch_bounds__(kBatchThreads, 2)
             int ntiles, int* __restrict__ counter, BatchDev bp) {
   constexpr int AW = TW / 2, AH = TH / 2;
   constexpr int RW = AW + 2 * kBatchMaxR, RH = AH + 2 * kBatchMaxR;
-  constexpr int PPT = TW * TH / kBatchThreads;  // pixels per thread
-  static_assert(TW * TH % kBatchThreads == 0, "tile must be a multiple of the block");
+  constexpr int PPT = TW * TH / kBatchThreads;  // pixels per thread, taken in pairs
+  static_assert(TW * TH % (2 * kBatchThreads) == 0, "tile must be a multiple of two blocks of pixels");
   __shared__ float s_raw[RH * RW];
   __shared__ float s_e[RH * RW];
   __shared__ float s_ao[AH * AW];
   __shared__ float4 s_lights[2 * kLightChunk];
+  __shared__ float4 s_dup[2 * kLightChunk];
   __shared__ float4 s_kernel[kBatchMaxK];
   __shared__ ViewDev s_view;
   __shared__ IblDev s_ibl;
@@ -88,7 +89,7 @@ __global__ void __launch_bounds__(kBatchThreads, 2)
       for (int q = tid; q < (int)(sizeof(IblDev) / 4); q += kBatchThreads) ((int*)&s_ibl)[q] = __ldg(isrc + q);
       int nl = s_view.NL;
       bool mono = true;
-      if (nl <= bp.light_chunk) mono = stage_lights(s_lights, s_view.lights, 0, nl, tid, kBatchThreads);
+      if (nl <= bp.light_chunk) mono = stage_lights(s_lights, s_view.lights, 0, nl, tid, kBatchThreads, s_dup);
       mono = __syncthreads_and(mono);
       if (tid == 0) s_mono = mono;
       cur_view = td.x;
@@ -116,64 +117,54 @@ __global__ void __launch_bounds__(kBatchThreads, 2)
       s_ao[q] = (x0 / 2 + tx < Wa && y0 / 2 + ty < Ha) ? ssao_blur_texel(bp.ssao, s_raw + c, s_e + c, RW) : 1.0f;
     }
     __syncthreads();
-    // 3. compose + tone map
+    // 3. compose + tone map, two pixels per thread at a time
     const int nl = v.NL;
     const bool staged = nl <= bp.light_chunk;
-    const bool mono = s_mono;
-    const bool diffuse_only = (bp.flags & EPBR_SHADE_DIFFUSE_ONLY) != 0;
-    for (int k = 0; k < PPT; ++k) {
-      int q = tid + k * kBatchThreads;
-      int py = q / TW, px = q - py * TW;
-      int x = x0 + px, y = y0 + py;
-      bool inside = x < W && y < H;
-      Px s;
-      if (inside) s = px_setup<FMT>(v.g, v.cam, x, y);
-      bool active = inside && s.surface;
-      Direct d;
-      if (active) d = px_direct_begin(s);
-      // one pass when the view's lights are staged already, else chunk by chunk (every thread
-      // takes part in the staging; nl and the chunk count are block-uniform)
-      for (int base = 0; base < nl; base += bp.light_chunk) {
-        int cnt = staged ? nl : min(bp.light_chunk, nl - base);
-        bool m = mono;
-        if (!staged) {
-          __syncthreads();
-          m = __syncthreads_and(stage_lights(s_lights, v.lights, base, cnt, tid, kBatchThreads));
-        }
-        if (active) {
-          if (diffuse_only)
-            px_direct_diffuse(s, d, s_lights, cnt);
-          else if (m)
-            px_direct_mono(s, d, s_lights, cnt);
+    for (int k = 0; k < PPT; k += 2) {
+      int xs[2], ys[2], pxs[2], pys[2];
+      bool in[2], act[2];
+      Px s[2];
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        int q = tid + (k + h) * kBatchThreads;
+        pys[h] = q / TW;
+        pxs[h] = q - pys[h] * TW;
+        xs[h] = x0 + pxs[h];
+        ys[h] = y0 + pys[h];
+        in[h] = xs[h] < W && ys[h] < H;
+        if (in[h]) s[h] = px_setup<FMT>(v.g, v.cam, xs[h], ys[h]);
+        act[h] = in[h] && s[h].surface;
+      }
+      shade_lights(s, act, nl, bp.flags, v.lights, s_lights, s_dup, bp.light_chunk, staged, s_mono != 0, tid,
+                   kBatchThreads);
+      float3 c[2];
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        float ao = act[h] ? s_ao[(pys[h] >> 1) * AW + (pxs[h] >> 1)] : 1.0f;
+        if (in[h]) c[h] = px_finish(s[h], s_ibl, bp.flags, ao);
+      }
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        if (!in[h]) continue;
+        if (v.hdr) {
+          if (bp.hdr_format == EPBR_HDR_RGBA32F)
+            store_hdr<EPBR_HDR_RGBA32F>(v.hdr, v.hdr_pitch, xs[h], ys[h], c[h]);
           else
-            px_direct(s, d, s_lights, cnt);
+            store_hdr<EPBR_HDR_RGBA16F>(v.hdr, v.hdr_pitch, xs[h], ys[h], c[h]);
         }
+        ((unsigned*)(v.ldr + (size_t)ys[h] * v.ldr_pitch))[xs[h]] = pack_rgba8(c[h], bp.exposure, bp.op);
       }
-      if (!inside) continue;
-      if (active && nl > 0) {
-        if (diffuse_only)
-          px_direct_diffuse_end(s, d);
-        else
-          px_direct_end(s, d);
-      }
-      float ao = s.surface ? s_ao[(py >> 1) * AW + (px >> 1)] : 1.0f;
-      float3 c = px_finish(s, s_ibl, bp.flags, ao);
-      if (v.hdr) {
-        if (bp.hdr_format == EPBR_HDR_RGBA32F)
-          store_hdr<EPBR_HDR_RGBA32F>(v.hdr, v.hdr_pitch, x, y, c);
-        else
-          store_hdr<EPBR_HDR_RGBA16F>(v.hdr, v.hdr_pitch, x, y, c);
-      }
-      ((unsigned*)(v.ldr + (size_t)y * v.ldr_pitch))[x] = pack_rgba8(c, bp.exposure, bp.op);
     }
   }
 }
 
 // ------------------------------------------------------------------------------------------
 // Staged mode: the three stages of the per-view pipeline, each one launch over a tile list that
-// spans every view (one 32x8 tile per block, tiles of the costliest views first).
+// spans every view (one tile per block: 32x8 AO texels, 32x16 pixels for the compose; tiles of
+// the costliest views first).
 // ------------------------------------------------------------------------------------------
 constexpr int kMvBX = 32, kMvBY = 8;
+constexpr int kMvTileH = 2 * kMvBY;  // compose tiles: 32 x 16 pixels, two per thread
 
 // Copies view td.x (and, when `with_ibl`, its lighting set) into shared memory.
 __device__ __forceinline__ void mv_stage_view(const ViewDev* views, const IblDev* ibls, int vi, ViewDev& s_view,
@@ -238,61 +229,54 @@ __global__ void __launch_bounds__(kMvBX* kMvBY) k_mv_ssao_blur(const ViewDev* __
 }
 
 template <int FMT>
-__global__ void __launch_bounds__(kMvBX* kMvBY, 4)
+__global__ void __launch_bounds__(kMvBX* kMvBY, 2)
     k_mv_shade(const ViewDev* __restrict__ views, const IblDev* __restrict__ ibls, const int4* __restrict__ tiles,
                BatchDev bp) {
   __shared__ float4 s_lights[2 * kLightChunk];
+  __shared__ float4 s_dup[2 * kLightChunk];
   __shared__ ViewDev s_view;
   __shared__ IblDev s_ibl;
+  constexpr int kThreads = kMvBX * kMvBY;
   int tid = threadIdx.y * kMvBX + threadIdx.x;
   int4 td = __ldg(tiles + blockIdx.x);
-  mv_stage_view(views, ibls, td.x, s_view, &s_ibl, tid, kMvBX * kMvBY);
+  mv_stage_view(views, ibls, td.x, s_view, &s_ibl, tid, kThreads);
   __syncthreads();
   const ViewDev& v = s_view;
-  int x = td.y * kMvBX + threadIdx.x, y = td.z * kMvBY + threadIdx.y;
-  bool inside = x < v.g.W && y < v.g.H;
-  PxRaw raw;
-  if (inside) raw = px_load<FMT>(v.g, x, y);
+  int x = td.y * kMvBX + threadIdx.x;
+  int yy[2] = {td.z * kMvTileH + 2 * (int)threadIdx.y, td.z * kMvTileH + 2 * (int)threadIdx.y + 1};
+  bool in[2] = {x < v.g.W && yy[0] < v.g.H, x < v.g.W && yy[1] < v.g.H};
+  PxRaw raw[2];
+#pragma unroll
+  for (int h = 0; h < 2; ++h)
+    if (in[h]) raw[h] = px_load<FMT>(v.g, x, yy[h]);
   int nl = v.NL;
   bool mono = false;
-  if (nl <= kLightChunk) mono = __syncthreads_and(stage_lights(s_lights, v.lights, 0, nl, tid, kMvBX * kMvBY));
-  Px s;
-  if (inside) s = px_decode<FMT>(raw, v.cam, x, y);
-  bool active = inside && s.surface;
-  bool diffuse_only = (bp.flags & EPBR_SHADE_DIFFUSE_ONLY) != 0;
-  Direct d;
-  if (active) d = px_direct_begin(s);
-  for (int base = 0; base < nl; base += kLightChunk) {
-    int cnt = min(kLightChunk, nl - base);
-    if (nl > kLightChunk) {
-      __syncthreads();
-      mono = __syncthreads_and(stage_lights(s_lights, v.lights, base, cnt, tid, kMvBX * kMvBY));
-    }
-    if (active) {
-      if (diffuse_only)
-        px_direct_diffuse(s, d, s_lights, cnt);
-      else if (mono)
-        px_direct_mono(s, d, s_lights, cnt);
+  if (nl <= kLightChunk) mono = __syncthreads_and(stage_lights(s_lights, v.lights, 0, nl, tid, kThreads, s_dup));
+  Px s[2];
+  bool act[2];
+  float ao[2];
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    if (in[h]) s[h] = px_decode<FMT>(raw[h], v.cam, x, yy[h]);
+    act[h] = in[h] && s[h].surface;
+    ao[h] = act[h] ? __ldg(v.ao + (size_t)(yy[h] >> 1) * v.ao_w + (x >> 1)) : 1.0f;
+  }
+  shade_lights(s, act, nl, bp.flags, v.lights, s_lights, s_dup, kLightChunk, nl <= kLightChunk, mono, tid, kThreads);
+  float3 c[2];
+#pragma unroll
+  for (int h = 0; h < 2; ++h)
+    if (in[h]) c[h] = px_finish(s[h], s_ibl, bp.flags, ao[h]);
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    if (!in[h]) continue;
+    if (v.hdr) {
+      if (bp.hdr_format == EPBR_HDR_RGBA32F)
+        store_hdr<EPBR_HDR_RGBA32F>(v.hdr, v.hdr_pitch, x, yy[h], c[h]);
       else
-        px_direct(s, d, s_lights, cnt);
+        store_hdr<EPBR_HDR_RGBA16F>(v.hdr, v.hdr_pitch, x, yy[h], c[h]);
     }
+    ((unsigned*)(v.ldr + (size_t)yy[h] * v.ldr_pitch))[x] = pack_rgba8(c[h], bp.exposure, bp.op);
   }
-  if (!inside) return;
-  if (active && nl > 0) {
-    if (diffuse_only)
-      px_direct_diffuse_end(s, d);
-    else
-      px_direct_end(s, d);
-  }
-  float ao = s.surface ? __ldg(v.ao + (size_t)(y >> 1) * v.ao_w + (x >> 1)) : 1.0f;
-  float3 c = px_finish(s, s_ibl, bp.flags, ao);
-  if (v.hdr) {
-    if (bp.hdr_format == EPBR_HDR_RGBA32F)
-      store_hdr<EPBR_HDR_RGBA32F>(v.hdr, v.hdr_pitch, x, y, c);
-    else
-      store_hdr<EPBR_HDR_RGBA16F>(v.hdr, v.hdr_pitch, x, y, c);
-  }
-  ((unsigned*)(v.ldr + (size_t)y * v.ldr_pitch))[x] = pack_rgba8(c, bp.exposure, bp.op);
 }
 
 // ------------------------------------------------------------------------------------------
@@ -396,7 +380,7 @@ static epbr_status build_tiles(epbr_batch* b) {
         off += n;
       }
     }
-    std::vector<int4> t = make_tiles(b, kMvBX, kMvBY, false), ta = make_tiles(b, kMvBX, kMvBY, true);
+    std::vector<int4> t = make_tiles(b, kMvBX, kMvTileH, false), ta = make_tiles(b, kMvBX, kMvBY, true);
     if ((st = upload_tiles(t, &b->d_tiles, &b->tiles_cap))) return st;
     if ((st = upload_tiles(ta, &b->d_ao_tiles, &b->ao_tiles_cap))) return st;
     b->ntiles = (int)t.size();
@@ -489,7 +473,7 @@ static epbr_status set_plan(epbr_batch* b, int mode, int tw, int th, int chunk) 
     return fail(EPBR_ERR_INVALID_ARG, "batch: plan mode %d tile %dx%d chunk %d not available", mode, tw, th, chunk);
   b->mode = mode;
   b->tile_w = mode == kModeFused ? tw : kMvBX;
-  b->tile_h = mode == kModeFused ? th : kMvBY;
+  b->tile_h = mode == kModeFused ? th : kMvTileH;
   b->chunk = mode == kModeFused ? chunk : kLightChunk;
   epbr_status st = build_tiles(b);
   if (st) return st;

@@ -1,6 +1,7 @@
 // Deferred compose and tone mapping of one view.
-//   k_shade    one thread per pixel in 32x8 blocks: G-buffer decode, Cook-Torrance over the
-//              point lights (staged in shared memory in chunks of 256), split-sum IBL times AO,
+//   k_shade    two pixels per thread in 32x8 blocks (32x16 pixel tiles): G-buffer decode,
+//              Cook-Torrance over the point lights (staged in shared memory in chunks of 256;
+//              monochrome chunks in packed FP32x2 arithmetic), split-sum IBL times AO,
 //              background from the environment; optional fused tone-map epilogue (Sec. 5.4).
 //              The per-pixel arithmetic lives in shade_core.cuh.
 //   k_tonemap  ACES / Reinhard + sRGB transfer, 8-bit output
@@ -13,66 +14,61 @@
 namespace epbr {
 
 #ifndef EPBR_SHADE_BY
-#define EPBR_SHADE_BY 8  // block rows (block = 32 x EPBR_SHADE_BY threads, one pixel each)
+#define EPBR_SHADE_BY 8  // block rows of threads (block = 32 x EPBR_SHADE_BY threads, two pixels each)
 #endif
 constexpr int kShadeBX = 32, kShadeBY = EPBR_SHADE_BY;
+constexpr int kShadeTileH = 2 * kShadeBY;  // pixel rows per block
 #ifndef EPBR_SHADE_MIN_BLOCKS
-#define EPBR_SHADE_MIN_BLOCKS 4  // resident blocks per SM the register budget targets (64 registers)
+#define EPBR_SHADE_MIN_BLOCKS 2  // resident blocks per SM the register budget targets
 #endif
 
-// One thread per pixel of a 32x8 tile.  The G-buffer loads are issued before the lights are
-// staged so that they are in flight during the staging barrier.  Lights are staged in chunks of
-// 256; a chunk whose lights are all monochrome takes the one-sum-per-term loop.
+// Two vertically adjacent pixels per thread, a 32 x 2*EPBR_SHADE_BY tile per block.  The G-buffer
+// loads are issued before the lights are staged so that they are in flight during the staging
+// barrier.  Lights are staged in chunks of 256; a chunk whose lights are all monochrome takes the
+// packed two-pixel loop (px_direct_mono2), any other chunk the per-pixel colour loop.
 template <int FMT, int HDR, bool LDR>
 __global__ void __launch_bounds__(kShadeBX* kShadeBY, EPBR_SHADE_MIN_BLOCKS)
     k_shade(GbufDev g, CamDev cam, const float4* __restrict__ lights, int NL, IblDev ibl, ShadeDev p, void* hdr,
             long long hdr_pitch, uint8_t* ldr, long long ldr_pitch) {
   __shared__ float4 s_lights[2 * kLightChunk];
+  __shared__ float4 s_dup[2 * kLightChunk];
+  constexpr int kThreads = kShadeBX * kShadeBY;
   int tid = threadIdx.y * kShadeBX + threadIdx.x;
   // Rows are dispatched bottom-up: the costliest tiles (ground and objects) usually fill the
   // bottom of a view and the cheap background the top, so the expensive work starts first and
   // the tail of the launch is short.  Any order gives the same image.
   int by = gridDim.y - 1 - blockIdx.y;
-  int x = blockIdx.x * kShadeBX + threadIdx.x, y = by * kShadeBY + threadIdx.y;
-  bool inside = x < g.W && y < g.H;
-  PxRaw raw;
-  if (inside) raw = px_load<FMT>(g, x, y);
+  int x = blockIdx.x * kShadeBX + threadIdx.x;
+  int yy[2] = {by * kShadeTileH + 2 * (int)threadIdx.y, by * kShadeTileH + 2 * (int)threadIdx.y + 1};
+  bool in[2] = {x < g.W && yy[0] < g.H, x < g.W && yy[1] < g.H};
+  PxRaw raw[2];
+#pragma unroll
+  for (int h = 0; h < 2; ++h)
+    if (in[h]) raw[h] = px_load<FMT>(g, x, yy[h]);
   bool mono = false;
-  if (NL <= kLightChunk) mono = __syncthreads_and(stage_lights(s_lights, lights, 0, NL, tid, kShadeBX * kShadeBY));
-  Px s;
-  if (inside) s = px_decode<FMT>(raw, cam, x, y);
-  bool active = inside && s.surface;
-  bool diffuse_only = (p.flags & EPBR_SHADE_DIFFUSE_ONLY) != 0;
-  Direct d;
-  if (active) d = px_direct_begin(s);
-  for (int base = 0; base < NL; base += kLightChunk) {
-    int cnt = min(kLightChunk, NL - base);
-    if (NL > kLightChunk) {
-      __syncthreads();
-      mono = __syncthreads_and(stage_lights(s_lights, lights, base, cnt, tid, kShadeBX * kShadeBY));
-    }
-    if (active) {
-      if (diffuse_only)
-        px_direct_diffuse(s, d, s_lights, cnt);
-      else if (mono)
-        px_direct_mono(s, d, s_lights, cnt);
-      else
-        px_direct(s, d, s_lights, cnt);
-    }
+  if (NL <= kLightChunk) mono = __syncthreads_and(stage_lights(s_lights, lights, 0, NL, tid, kThreads, s_dup));
+  Px s[2];
+  bool act[2];
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    if (in[h]) s[h] = px_decode<FMT>(raw[h], cam, x, yy[h]);
+    act[h] = in[h] && s[h].surface;
   }
-  if (!inside) return;
-  if (active && NL > 0) {
-    if (diffuse_only)
-      px_direct_diffuse_end(s, d);
-    else
-      px_direct_end(s, d);
+  float ao[2];  // loaded before the light loop, which hides their latency
+#pragma unroll
+  for (int h = 0; h < 2; ++h) ao[h] = act[h] ? ao_at(p, x, yy[h]) : 1.0f;
+  shade_lights(s, act, NL, p.flags, lights, s_lights, s_dup, kLightChunk, NL <= kLightChunk, mono, tid, kThreads);
+  // Both pixels' lookups are issued before either is stored.
+  float3 c[2];
+#pragma unroll
+  for (int h = 0; h < 2; ++h)
+    if (in[h]) c[h] = px_finish(s[h], ibl, p.flags, ao[h]);
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    if (!in[h]) continue;
+    if (hdr) store_hdr<HDR>(hdr, hdr_pitch, x, yy[h], c[h]);
+    if (LDR) ((unsigned*)(ldr + (size_t)yy[h] * ldr_pitch))[x] = pack_rgba8(c[h], p.exposure, p.op);
   }
-  float ao = 1.0f;
-  if (p.ao && s.surface)
-    ao = __ldg((const float*)((const char*)p.ao + (size_t)(y / p.ao_scale) * p.ao_pitch) + x / p.ao_scale);
-  float3 c = px_finish(s, ibl, p.flags, ao);
-  if (hdr) store_hdr<HDR>(hdr, hdr_pitch, x, y, c);
-  if (LDR) ((unsigned*)(ldr + (size_t)y * ldr_pitch))[x] = pack_rgba8(c, p.exposure, p.op);
 }
 
 template <int HDR>
@@ -143,6 +139,7 @@ static epbr_status shade_common(const epbr_gbuffer* g, const epbr_camera* cam, c
   p.ao = sp->ao;
   p.ao_pitch = sp->ao_pitch;
   p.ao_scale = sp->ao_scale < 1 ? 1 : sp->ao_scale;
+  p.ao_inv = 1.0f / (float)p.ao_scale;
   p.exposure = tp ? tp->exposure : 1.0f;
   p.op = tp ? tp->op : 0;
   if (sp->ao) {
@@ -161,7 +158,7 @@ static epbr_status shade_common(const epbr_gbuffer* g, const epbr_camera* cam, c
   }
   GbufDev gd = make_gbuf(*g);
   CamDev cd = make_cam(*cam);
-  dim3 blk(kShadeBX, kShadeBY), grd((g->width + kShadeBX - 1) / kShadeBX, (g->height + kShadeBY - 1) / kShadeBY);
+  dim3 blk(kShadeBX, kShadeBY), grd((g->width + kShadeBX - 1) / kShadeBX, (g->height + kShadeTileH - 1) / kShadeTileH);
   cudaStream_t s = (cudaStream_t)stream;
   const float4* L = (const float4*)lights;
   int nl = (sp->flags & EPBR_SHADE_DIRECT) ? NL : 0;

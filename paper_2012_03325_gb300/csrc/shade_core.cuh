@@ -38,11 +38,21 @@ struct IblDev {
 struct ShadeDev {
   unsigned flags;
   int ao_scale;
+  float ao_inv;  // 1 / ao_scale
   const float* ao;
   long long ao_pitch;
   float exposure;
   int op;
 };
+
+// AO texel of pixel (x, y): texel (floor(x / scale), floor(y / scale)), the quotients taken as
+// floor((x + 1/2) / scale) in FP32, exact for x < 2^15 and scale <= 8 (the fraction stays at
+// least 1/16 away from an integer while the rounding error is below 2^-8).
+__device__ __forceinline__ float ao_at(const ShadeDev& p, int x, int y) {
+  if (!p.ao) return 1.0f;
+  int ax = __float2int_rd(((float)x + 0.5f) * p.ao_inv), ay = __float2int_rd(((float)y + 0.5f) * p.ao_inv);
+  return __ldg((const float*)((const char*)p.ao + (size_t)ay * p.ao_pitch) + ax);
+}
 
 // Tone map one channel: clamp exposure * x to [0, 1e6], ACES fit (Narkowicz 2015) or Reinhard,
 // clamp to [0, 1], sRGB transfer (IEC 61966-2-1), round half up to 8 bits.
@@ -173,9 +183,11 @@ __device__ __forceinline__ Px px_setup(const GbufDev& g, const CamDev& cam, int 
 // Lights staged in shared memory as pairs (pos.xyz, Ic.r), (Ic.rgb, -) with Ic = intensity *
 // colour, so a monochrome light needs only the first float4.  Returns
 // whether every light this thread staged is monochrome (equal colour channels); callers combine
-// the flags with __syncthreads_and to pick the monochrome loop for the chunk.
+// the flags with __syncthreads_and to pick the monochrome loop for the chunk.  With s_dup, each
+// light is also written as (x, x, y, y), (z, z, Ic, Ic): the operands of the two-pixel packed
+// loop (px_direct_mono2), each coordinate already duplicated into both halves of a pair.
 __device__ __forceinline__ bool stage_lights(float4* s_lights, const float4* __restrict__ lights, int first,
-                                             int cnt, int tid, int nthreads) {
+                                             int cnt, int tid, int nthreads, float4* s_dup = nullptr) {
   bool mono = true;
   for (int q = tid; q < cnt; q += nthreads) {
     float4 a = __ldg(lights + 2 * (first + q));
@@ -183,6 +195,10 @@ __device__ __forceinline__ bool stage_lights(float4* s_lights, const float4* __r
     float4 ic = make_float4(a.w * c.x, a.w * c.y, a.w * c.z, 0.0f);
     s_lights[2 * q] = make_float4(a.x, a.y, a.z, ic.x);  // .w: Ic of a monochrome light
     s_lights[2 * q + 1] = ic;
+    if (s_dup) {
+      s_dup[2 * q] = make_float4(a.x, a.x, a.y, a.y);
+      s_dup[2 * q + 1] = make_float4(a.z, a.z, ic.x, ic.x);
+    }
     mono = mono && ic.x == ic.y && ic.y == ic.z;
   }
   return mono;
@@ -292,16 +308,27 @@ __device__ __forceinline__ void px_direct_mono(const Px& s, Direct& d, const flo
   d.sbf = d.sbf + f3(sbf, sbf, sbf);
 }
 
-__device__ __forceinline__ void px_direct_end(Px& s, const Direct& d) {
+// alpha^2 G1(v) / (4 pi n.v): the per-pixel factor of the specular sums.
+__device__ __forceinline__ float spec_factor(const Px& s) {
+  float alpha = s.rough * s.rough, k = (s.rough + 1.0f) * (s.rough + 1.0f) * 0.125f;
+  return alpha * alpha * rcp_ftz(4.0f * kPi * fmaf(s.nv, 1.0f - k, k));
+}
+
+// Adds K sa + F0 sb a2vv + (1 - F0) sbf a2vv to s.acc (the per-channel material factors of the
+// three light sums).
+__device__ __forceinline__ void px_direct_fold(Px& s, float3 sa, float3 sb, float3 sbf, float a2vv) {
   float3 F0 = f3(fmaf(s.metal, s.albedo.x - 0.04f, 0.04f), fmaf(s.metal, s.albedo.y - 0.04f, 0.04f),
                  fmaf(s.metal, s.albedo.z - 0.04f, 0.04f));
   float3 omF0 = f3(1.0f - F0.x, 1.0f - F0.y, 1.0f - F0.z);
   float3 K = mul3(s.albedo * ((1.0f - s.metal) * kInvPi), omF0);
-  float3 sb = d.sb * d.a2vv, sbf = d.sbf * d.a2vv;
-  s.acc.x += fmaf(K.x, d.sa.x, fmaf(F0.x, sb.x, omF0.x * sbf.x));
-  s.acc.y += fmaf(K.y, d.sa.y, fmaf(F0.y, sb.y, omF0.y * sbf.y));
-  s.acc.z += fmaf(K.z, d.sa.z, fmaf(F0.z, sb.z, omF0.z * sbf.z));
+  sb = sb * a2vv;
+  sbf = sbf * a2vv;
+  s.acc.x += fmaf(K.x, sa.x, fmaf(F0.x, sb.x, omF0.x * sbf.x));
+  s.acc.y += fmaf(K.y, sa.y, fmaf(F0.y, sb.y, omF0.y * sbf.y));
+  s.acc.z += fmaf(K.z, sa.z, fmaf(F0.z, sb.z, omF0.z * sbf.z));
 }
+
+__device__ __forceinline__ void px_direct_end(Px& s, const Direct& d) { px_direct_fold(s, d.sa, d.sb, d.sbf, d.a2vv); }
 
 // Diffuse-only variant: sum of Ic (n.l)/d^2, times albedo/pi at the end.
 __device__ __forceinline__ void px_direct_diffuse(const Px& s, Direct& d, const float4* s_lights, int cnt) {
@@ -321,6 +348,158 @@ __device__ __forceinline__ void px_direct_diffuse(const Px& s, Direct& d, const 
 
 __device__ __forceinline__ void px_direct_diffuse_end(Px& s, const Direct& d) {
   s.acc = s.acc + mul3(s.albedo * kInvPi, d.sa);
+}
+
+// ---- Two pixels per thread: the monochrome light loop in packed FP32x2 instructions ----------
+//
+// Each thread shades two pixels; every per-pixel quantity of the light loop is a float2 whose
+// halves belong to the two pixels, and each arithmetic step is one fma/mul/add.f32x2 for both.
+// The loop runs in a per-pixel tangent frame (t, b, n) (Duff et al. ONB around n), where with
+// L = R (p_light - P) = R p_light + q (q = -R P) and v = (v_t, v_b, n.v):
+//   n.L = L_z,  s = L / |L| + v,  |n x s|^2 = s_x^2 + s_y^2,  n.s = s_z,  |s|^2 = |n x s|^2 + s_z^2,
+// i.e. the quantities of the direct-light terms above without any cross or dot product per light.
+// The loop keeps four sums per pixel: Ic w, Ic w fc, Ic w spec', Ic w spec' fc, so
+// sa = (Ic w) - (Ic w fc), sb = Ic w spec', sbf = Ic w spec' fc of the scalar loop.
+
+__device__ __forceinline__ float2 dup2(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float2 pfma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 pmul(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 padd(float2 a, float2 b) { return __fadd2_rn(a, b); }
+
+// Per-pixel constants of the packed loop for two pixels.
+struct Frame2 {
+  float2 tx, ty, tz, bx, by, bz, nx, ny, nz;  // rows of R = (t; b; n)
+  float2 qx, qy, qz;                          // q = -R P
+  float2 vx, vy, vz;                          // R v
+  float2 al, k, omk;                          // alpha, Smith-Schlick k, 1 - k
+};
+
+struct Sums2 {
+  float2 w, wf, b, bf;  // sums of Ic w, Ic w fc, Ic w spec', Ic w spec' fc
+};
+
+struct FrameHalf {
+  float t[3], b[3], n[3], q[3], v[3], al, k, omk;
+};
+
+__device__ __forceinline__ FrameHalf frame_half(const Px& s, bool active) {
+  FrameHalf h;
+  if (!active) {  // an inactive half computes finite values that are never used
+#pragma unroll
+    for (int i = 0; i < 3; ++i) h.t[i] = h.b[i] = h.n[i] = h.q[i] = h.v[i] = 0.0f;
+    h.al = h.k = h.omk = 1.0f;
+    return h;
+  }
+  float3 t, b;
+  onb(s.n, t, b);
+  h.t[0] = t.x, h.t[1] = t.y, h.t[2] = t.z;
+  h.b[0] = b.x, h.b[1] = b.y, h.b[2] = b.z;
+  h.n[0] = s.n.x, h.n[1] = s.n.y, h.n[2] = s.n.z;
+  h.q[0] = -dot3(t, s.P), h.q[1] = -dot3(b, s.P), h.q[2] = -dot3(s.n, s.P);
+  h.v[0] = dot3(t, s.v), h.v[1] = dot3(b, s.v), h.v[2] = s.nv_raw;
+  h.al = s.rough * s.rough;
+  h.k = (s.rough + 1.0f) * (s.rough + 1.0f) * 0.125f;
+  h.omk = 1.0f - h.k;
+  return h;
+}
+
+__device__ __forceinline__ Frame2 make_frame2(const Px& s0, bool a0, const Px& s1, bool a1) {
+  FrameHalf h0 = frame_half(s0, a0), h1 = frame_half(s1, a1);
+  Frame2 f;
+  f.tx = make_float2(h0.t[0], h1.t[0]), f.ty = make_float2(h0.t[1], h1.t[1]), f.tz = make_float2(h0.t[2], h1.t[2]);
+  f.bx = make_float2(h0.b[0], h1.b[0]), f.by = make_float2(h0.b[1], h1.b[1]), f.bz = make_float2(h0.b[2], h1.b[2]);
+  f.nx = make_float2(h0.n[0], h1.n[0]), f.ny = make_float2(h0.n[1], h1.n[1]), f.nz = make_float2(h0.n[2], h1.n[2]);
+  f.qx = make_float2(h0.q[0], h1.q[0]), f.qy = make_float2(h0.q[1], h1.q[1]), f.qz = make_float2(h0.q[2], h1.q[2]);
+  f.vx = make_float2(h0.v[0], h1.v[0]), f.vy = make_float2(h0.v[1], h1.v[1]), f.vz = make_float2(h0.v[2], h1.v[2]);
+  f.al = make_float2(h0.al, h1.al), f.k = make_float2(h0.k, h1.k), f.omk = make_float2(h0.omk, h1.omk);
+  return f;
+}
+
+// Adds `cnt` monochrome lights staged as (x, x, y, y), (z, z, Ic, Ic) to the sums of both pixels.
+// Guards as in light_terms: |L|^2 + 1e-30, |n x s|^2 + 1e-18.
+__device__ __forceinline__ void px_direct_mono2(const Frame2& f, Sums2& S, const float4* s_dup, int cnt) {
+  float2 sw = S.w, swf = S.wf, sb = S.b, sbf = S.bf;
+  const float2 e30 = dup2(1e-30f), e18 = dup2(1e-18f), mhalf = dup2(-0.5f), one = dup2(1.0f);
+#pragma unroll(kLightUnroll)
+  for (int i = 0; i < cnt; ++i) {
+    float4 u = s_dup[2 * i], z = s_dup[2 * i + 1];
+    float2 X = make_float2(u.x, u.y), Y = make_float2(u.z, u.w), Z = make_float2(z.x, z.y), IC = make_float2(z.z, z.w);
+    float2 Lx = pfma(f.tx, X, pfma(f.ty, Y, pfma(f.tz, Z, f.qx)));
+    float2 Ly = pfma(f.bx, X, pfma(f.by, Y, pfma(f.bz, Z, f.qy)));
+    float2 Lz = pfma(f.nx, X, pfma(f.ny, Y, pfma(f.nz, Z, f.qz)));
+    float2 d2 = pfma(Lx, Lx, pfma(Ly, Ly, pfma(Lz, Lz, e30)));
+    float2 rs = make_float2(rsqrt_ftz(d2.x), rsqrt_ftz(d2.y));
+    float2 sx = pfma(Lx, rs, f.vx), sy = pfma(Ly, rs, f.vy), sz = pfma(Lz, rs, f.vz);
+    float2 c2 = pfma(sx, sx, pfma(sy, sy, e18));  // |n x s|^2
+    float2 hh = pfma(sz, sz, c2);                 // |s|^2
+    float2 nsa = pmul(sz, f.al);                  // alpha n.s
+    float2 den = pfma(nsa, nsa, c2);
+    float2 nlc = pmul(make_float2(fmaxf(Lz.x, 0.0f), fmaxf(Lz.y, 0.0f)), rs);  // max(n.l, 0)
+    float2 xx = pfma(mhalf, make_float2(sqrt_ftz(hh.x), sqrt_ftz(hh.y)), one);  // 1 - v.h
+    float2 x2 = pmul(xx, xx);
+    float2 fc = pmul(pmul(x2, x2), xx);  // (1 - v.h)^5 in the FMA pipe (the MUFU pipe is the busier one here)
+    float2 icw = pmul(pmul(IC, pmul(rs, rs)), nlc);        // Ic (n.l) / d^2
+    float2 q = pmul(pmul(den, den), pfma(nlc, f.omk, f.k));
+    float2 icb = pmul(icw, pmul(pmul(hh, hh), make_float2(rcp_ftz(q.x), rcp_ftz(q.y))));
+    sw = padd(sw, icw);
+    swf = pfma(icw, fc, swf);
+    sb = padd(sb, icb);
+    sbf = pfma(icb, fc, sbf);
+  }
+  S.w = sw, S.wf = swf, S.b = sb, S.bf = sbf;
+}
+
+// Folds half `h` (0 or 1) of the packed sums into pixel s.
+__device__ __forceinline__ void px_direct_fold2(Px& s, const Sums2& S, int h) {
+  float w = h ? S.w.y : S.w.x, wf = h ? S.wf.y : S.wf.x, b = h ? S.b.y : S.b.x, bf = h ? S.bf.y : S.bf.x;
+  float sa = w - wf;
+  px_direct_fold(s, f3(sa, sa, sa), f3(b, b, b), f3(bf, bf, bf), spec_factor(s));
+}
+
+// Direct light of a pixel pair summed over all NL lights, in chunks of `chunk` lights staged in
+// shared memory (s_lights, and s_dup for the packed loop).  With `prestaged` the block has staged
+// all lights already (NL <= chunk) and `mono` is their block vote; otherwise every chunk is staged
+// here, so every thread of the block must call this with the same NL, chunk and prestaged.
+// Monochrome chunks take the packed loop; other chunks, and the diffuse-only mode, the per-pixel
+// loops, whose sums are folded into s[h].acc chunk by chunk.
+__device__ __forceinline__ void shade_lights(Px (&s)[2], const bool (&act)[2], int NL, unsigned flags,
+                                             const float4* __restrict__ lights, float4* s_lights, float4* s_dup,
+                                             int chunk, bool prestaged, bool mono, int tid, int nthreads) {
+  const bool diffuse_only = (flags & EPBR_SHADE_DIFFUSE_ONLY) != 0;
+  Frame2 fr;
+  Sums2 sums;
+  sums.w = sums.wf = sums.b = sums.bf = make_float2(0.0f, 0.0f);
+  if (NL > 0 && !diffuse_only && (act[0] || act[1])) fr = make_frame2(s[0], act[0], s[1], act[1]);
+  for (int base = 0; base < NL; base += chunk) {
+    int cnt = prestaged ? NL : min(chunk, NL - base);
+    bool m = mono;
+    if (!prestaged) {
+      __syncthreads();  // the previous chunk has been read by every thread
+      m = __syncthreads_and(stage_lights(s_lights, lights, base, cnt, tid, nthreads, s_dup));
+    }
+    if (!(act[0] || act[1])) continue;
+    if (!diffuse_only && m) {
+      px_direct_mono2(fr, sums, s_dup, cnt);
+      continue;
+    }
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      if (!act[h]) continue;
+      Direct d = px_direct_begin(s[h]);
+      if (diffuse_only) {
+        px_direct_diffuse(s[h], d, s_lights, cnt);
+        px_direct_diffuse_end(s[h], d);
+      } else {
+        px_direct(s[h], d, s_lights, cnt);
+        px_direct_end(s[h], d);
+      }
+    }
+  }
+  if (NL > 0 && !diffuse_only) {
+#pragma unroll
+    for (int h = 0; h < 2; ++h)
+      if (act[h]) px_direct_fold2(s[h], sums, h);
+  }
 }
 
 // Adds the split-sum ambient term (times AO) to s.acc.
