@@ -568,8 +568,7 @@ extern "C" epbr_status epbr_batch_create(const epbr_view* views, int32_t n_views
   b->bp.hdr_format = p->hdr_format;
   b->bp.exposure = p->tonemap.exposure;
   b->bp.op = p->tonemap.op;
-  b->bp.ssao = SsaoDev{p->ssao.num_samples, 2, p->ssao.blur_radius, p->ssao.radius, p->ssao.bias,
-                       p->ssao.sigma_s, p->ssao.sigma_z, (const float4*)p->ssao.kernel, (const float2*)p->ssao.noise};
+  b->bp.ssao = make_ssao(p->ssao);  // scale 2, checked above
   bool ok_alloc = cudaMalloc(&b->d_views, sizeof(ViewDev) * n_views) == cudaSuccess &&
                   cudaMalloc(&b->d_ibls, sizeof(IblDev) * n_ibls) == cudaSuccess &&
                   cudaMalloc(&b->d_counter, sizeof(int)) == cudaSuccess;

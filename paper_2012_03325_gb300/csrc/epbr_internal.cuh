@@ -75,6 +75,8 @@ struct CamDev {
   float r[9];   // view_to_world rotation, r[3*i + j] = row i, column j
   float eye[3];
   float sx, sy;  // px = (2 (x + 0.5) / W - 1) * sx, py = (1 - 2 (y + 0.5) / H) * sy
+  float ax, bx, ay, by;  // the same as px = ax x + bx, py = ay y + by (coefficients in FP64)
+  float ix_scale, iy_scale;  // view -> pixel: x = 0.5 W (1 + px / sx), y = 0.5 H (1 - py / sy)
   int W, H;
 };
 
@@ -86,8 +88,15 @@ __host__ inline CamDev make_cam(const epbr_camera& c) {
   d.eye[1] = c.view_to_world[13];
   d.eye[2] = c.view_to_world[14];
   double t = tan(0.5 * (double)c.fov_y);
+  double sx = t * (double)c.width / (double)c.height;
   d.sy = (float)t;
-  d.sx = (float)(t * (double)c.width / (double)c.height);
+  d.sx = (float)sx;
+  d.ax = (float)(2.0 * sx / c.width);
+  d.bx = (float)(sx * (1.0 / c.width - 1.0));
+  d.ay = (float)(-2.0 * t / c.height);
+  d.by = (float)(t * (1.0 - 1.0 / c.height));
+  d.ix_scale = (float)(0.5 * c.width / sx);
+  d.iy_scale = (float)(0.5 * c.height / t);
   d.W = c.width;
   d.H = c.height;
   return d;
@@ -95,9 +104,7 @@ __host__ inline CamDev make_cam(const epbr_camera& c) {
 
 // View-space ray (px, py, -1) of the centre of pixel (x, y).
 __device__ __forceinline__ float3 view_ray(const CamDev& c, int x, int y) {
-  float px = fmaf(2.0f * (x + 0.5f), 1.0f / c.W, -1.0f) * c.sx;
-  float py = fmaf(-2.0f * (y + 0.5f), 1.0f / c.H, 1.0f) * c.sy;
-  return f3(px, py, -1.0f);
+  return f3(fmaf((float)x, c.ax, c.bx), fmaf((float)y, c.ay, c.by), -1.0f);
 }
 __device__ __forceinline__ float3 rot(const CamDev& c, float3 a) {
   return f3(fmaf(c.r[0], a.x, fmaf(c.r[1], a.y, c.r[2] * a.z)),
@@ -170,7 +177,7 @@ __device__ __forceinline__ float3 equirect_lookup(const MapDev m, float3 d) {
 // Branchless orthonormal basis (Duff et al., JCGT 2017) around unit n.
 __device__ __forceinline__ void onb(float3 n, float3& t, float3& b) {
   float s = copysignf(1.0f, n.z);
-  float a = -1.0f / (s + n.z);
+  float a = -rcp_ftz(s + n.z);  // |s + n.z| in [1, 2]
   float c = n.x * n.y * a;
   t = f3(fmaf(s * n.x * n.x, a, 1.0f), s * c, -s * n.x);
   b = f3(c, fmaf(n.y * n.y, a, s), -n.y);

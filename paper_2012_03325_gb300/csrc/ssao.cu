@@ -70,19 +70,6 @@ static epbr_status validate_ssao(const epbr_ssao_params* p) {
   return EPBR_OK;
 }
 
-static SsaoDev make_ssao(const epbr_ssao_params* p) {
-  SsaoDev d;
-  d.K = p->num_samples;
-  d.scale = p->scale;
-  d.R = p->blur_radius;
-  d.radius = p->radius;
-  d.bias = p->bias;
-  d.sigma_s = p->sigma_s;
-  d.sigma_z = p->sigma_z;
-  d.kernel = (const float4*)p->kernel;
-  d.noise = (const float2*)p->noise;
-  return d;
-}
 
 static void ao_dims(const epbr_gbuffer* g, const epbr_ssao_params* p, int* w, int* h) {
   *w = (g->width + p->scale - 1) / p->scale;
@@ -129,7 +116,7 @@ extern "C" epbr_status epbr_ssao_raw(const epbr_gbuffer* g, const epbr_camera* c
   dim3 blk(32, 8), grd((Wa + 31) / 32, (Ha + 7) / 8);
   GbufDev gd = make_gbuf(*g);
   CamDev cd = make_cam(*cam);
-  SsaoDev sd = make_ssao(p);
+  SsaoDev sd = make_ssao(*p);
   cudaStream_t s = (cudaStream_t)stream;
   if (g->format == EPBR_GBUFFER_FP32)
     k_ssao_raw<EPBR_GBUFFER_FP32><<<grd, blk, 0, s>>>(gd, cd, sd, ao, ao_pitch, Wa, Ha);
@@ -151,7 +138,7 @@ extern "C" epbr_status epbr_ssao_blur(const epbr_gbuffer* g, const epbr_ssao_par
   if (in == out) return fail(EPBR_ERR_INVALID_ARG, "ssao_blur: in and out must differ");
   dim3 blk(kBlurBX, kBlurBY), grd((Wa + kBlurBX - 1) / kBlurBX, (Ha + kBlurBY - 1) / kBlurBY);
   GbufDev gd = make_gbuf(*g);
-  SsaoDev sd = make_ssao(p);
+  SsaoDev sd = make_ssao(*p);
   cudaStream_t s = (cudaStream_t)stream;
   if (g->format == EPBR_GBUFFER_FP32)
     k_ssao_blur<EPBR_GBUFFER_FP32><<<grd, blk, 0, s>>>(gd, sd, in, in_pitch, out, out_pitch, Wa, Ha);

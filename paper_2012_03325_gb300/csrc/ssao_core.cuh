@@ -17,7 +17,25 @@ struct SsaoDev {
   float radius, bias, sigma_s, sigma_z;
   const float4* kernel;
   const float2* noise;
+  float inv_k;    // 1 / K
+  float blur_ks;  // -log2(e) / (2 sigma_s^2): the spatial exponent per squared texel distance
 };
+
+__host__ inline SsaoDev make_ssao(const epbr_ssao_params& p) {
+  SsaoDev d;
+  d.K = p.num_samples;
+  d.scale = p.scale;
+  d.R = p.blur_radius;
+  d.radius = p.radius;
+  d.bias = p.bias;
+  d.sigma_s = p.sigma_s;
+  d.sigma_z = p.sigma_z;
+  d.kernel = (const float4*)p.kernel;
+  d.noise = (const float2*)p.noise;
+  d.inv_k = (float)(1.0 / p.num_samples);
+  d.blur_ks = (float)(-1.4426950408889634 / (2.0 * (double)p.sigma_s * (double)p.sigma_s));
+  return d;
+}
 
 __device__ __forceinline__ float smoothstep01(float x) {
   x = clamp01(x);
@@ -38,14 +56,14 @@ __device__ __forceinline__ float2 ssao_texel(const GbufDev& g, const CamDev& cam
   float2 nz = __ldg(p.noise + ((j & 3) * 4 + (i & 3)));
   float3 rv = f3(nz.x, nz.y, 0.0f);
   float3 t = rv - n * dot3(rv, n), b;
-  float tl = sqrtf(dot3(t, t));
-  if (tl < 1e-4f) {
+  float tt = dot3(t, t);
+  if (tt < 1e-8f) {  // |t| < 1e-4
     onb(n, t, b);
   } else {
-    t = t * (1.0f / tl);
+    t = t * rsqrt_ftz(tt);
     b = cross3(n, t);
   }
-  float ix_scale = 0.5f * cam.W / cam.sx, iy_scale = 0.5f * cam.H / cam.sy;
+  const float ix_scale = cam.ix_scale, iy_scale = cam.iy_scale;
   float occ = 0.0f;
   // Branch-free so that the depth taps of several samples are in flight together: an invalid
   // sample (behind the camera or off-screen) reads pixel (0, 0) and is masked out.
@@ -63,7 +81,7 @@ __device__ __forceinline__ float2 ssao_texel(const GbufDev& g, const CamDev& cam
     bool hit = valid && is_surface(eb) && eb <= eS - p.bias;
     occ += hit ? smoothstep01(p.radius * rcp_ftz(fabsf(e - eb))) : 0.0f;
   }
-  return make_float2(1.0f - occ / p.K, e);
+  return make_float2(fmaf(-occ, p.inv_k, 1.0f), e);
 }
 
 // Depth-aware blur of one AO texel from shared-memory tiles: `ao` and `ed` point at the
@@ -77,7 +95,7 @@ __device__ __forceinline__ float ssao_blur_texel_r(const SsaoDev& p, const float
   float ep = ed[0];
   if (!is_surface(ep)) return 1.0f;
   const int R = RT > 0 ? RT : p.R;
-  float ks = -1.4426950408889634f / (2.0f * p.sigma_s * p.sigma_s);
+  const float ks = p.blur_ks;
   float kz = -1.4426950408889634f * rcp_ftz(p.sigma_z * ep);
   float num = 0.0f, den = 0.0f;
 #pragma unroll
@@ -91,7 +109,7 @@ __device__ __forceinline__ float ssao_blur_texel_r(const SsaoDev& p, const float
       den += w;
     }
   }
-  return num / den;
+  return num * rcp_ftz(den);  // den >= 1: the centre tap has weight 2^0
 }
 
 __device__ __forceinline__ float ssao_blur_texel(const SsaoDev& p, const float* ao, const float* ed, int tp) {
