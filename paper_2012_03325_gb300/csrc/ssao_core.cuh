@@ -63,22 +63,27 @@ __device__ __forceinline__ float2 ssao_texel(const GbufDev& g, const CamDev& cam
     t = t * rsqrt_ftz(tt);
     b = cross3(n, t);
   }
-  const float ix_scale = cam.ix_scale, iy_scale = cam.iy_scale;
+  const float ix_scale = cam.ix_scale, iy_scale = cam.iy_scale, hw = 0.5f * cam.W, hh = 0.5f * cam.H;
+  const float3 rt = t * p.radius, rb = b * p.radius, rn = n * p.radius;
   float occ = 0.0f;
   // Branch-free so that the depth taps of several samples are in flight together: an invalid
-  // sample (behind the camera or off-screen) reads pixel (0, 0) and is masked out.
+  // sample (behind the camera or off-screen) reads pixel (0, 0) and is masked out.  The pixel of
+  // a sample is (floor(x), floor(y)); 0 <= x < W is tested as 0 <= floor(x) < W, one unsigned
+  // compare (a negative or saturated conversion is out of range).
 #pragma unroll(kSsaoUnroll)
   for (int k = 0; k < p.K; ++k) {
     float4 ks = s_kernel[k];
-    float3 S = P + p.radius * (t * ks.x + b * ks.y + n * ks.z);
+    float3 S = f3(fmaf(rt.x, ks.x, fmaf(rb.x, ks.y, fmaf(rn.x, ks.z, P.x))),
+                  fmaf(rt.y, ks.x, fmaf(rb.y, ks.y, fmaf(rn.y, ks.z, P.y))),
+                  fmaf(rt.z, ks.x, fmaf(rb.z, ks.y, fmaf(rn.z, ks.z, P.z))));
     float eS = -S.z;
     float inv = rcp_ftz(eS);
-    float x = fmaf(S.x * inv, ix_scale, 0.5f * cam.W);
-    float y = fmaf(-S.y * inv, iy_scale, 0.5f * cam.H);
-    bool valid = eS > 0.0f && x >= 0.0f && x < (float)cam.W && y >= 0.0f && y < (float)cam.H;
-    int ix = valid ? min((int)x, cam.W - 1) : 0, iy = valid ? min((int)y, cam.H - 1) : 0;
-    float eb = gb_depth(g, ix, iy);
-    bool hit = valid && is_surface(eb) && eb <= eS - p.bias;
+    int ix = __float2int_rd(fmaf(S.x * inv, ix_scale, hw));
+    int iy = __float2int_rd(fmaf(-S.y * inv, iy_scale, hh));
+    bool valid = eS > 0.0f && (unsigned)ix < (unsigned)cam.W && (unsigned)iy < (unsigned)cam.H;
+    float eb = gb_depth(g, valid ? ix : 0, valid ? iy : 0);
+    // eb <= eS - bias (finite) already excludes a background tap at +inf
+    bool hit = valid && eb > 0.0f && eb <= eS - p.bias;
     occ += hit ? smoothstep01(p.radius * rcp_ftz(fabsf(e - eb))) : 0.0f;
   }
   return make_float2(fmaf(-occ, p.inv_k, 1.0f), e);
