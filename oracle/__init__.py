@@ -45,6 +45,11 @@ class SsaoParams(C.Structure):
                 ("noise", C.POINTER(C.c_double))]
 
 
+class BloomParams(C.Structure):
+    _fields_ = [("threshold", C.c_double), ("strength", C.c_double), ("sigma", C.c_double),
+                ("radius", C.c_int), ("levels", C.c_int)]
+
+
 class Ibl(C.Structure):
     _fields_ = [("irr", C.POINTER(C.c_double)), ("Wi", C.c_int), ("Hi", C.c_int), ("M", C.c_int),
                 ("level", C.POINTER(C.c_double) * MAX_LEVELS), ("Wl", C.c_int * MAX_LEVELS),
@@ -84,6 +89,7 @@ def lib():
             L.or_equirect_lookup.argtypes = [dp, C.c_int, C.c_int, dp, dp]
             L.or_equirect_lookup.restype = None
             L.or_num_threads.argtypes = [C.c_int]
+            L.or_bloom.argtypes = [dp, C.c_int, C.c_int, C.POINTER(BloomParams), dp, dp, dp]
             _lib = L
     return _lib
 
@@ -267,6 +273,35 @@ def tonemap(hdr, exposure: float = 1.0, op: int = 0):
     sc = np.zeros((h.shape[0], 3))
     lib().or_tonemap(_dp(h), h.shape[0], exposure, op, out.ctypes.data, _dp(sc))
     return out, sc
+
+
+def bloom_level_sizes(W: int, H: int, levels: int):
+    """(W_k, H_k) of pyramid levels 1 .. levels-1: each ceil-halves the previous."""
+    out, w, h = [], W, H
+    for _ in range(1, levels):
+        w, h = (w + 1) // 2, (h + 1) // 2
+        out.append((w, h))
+    return out
+
+
+def bloom(hdr, threshold: float = 1.0, strength: float = 1.0, sigma: float = 2.0, radius: int = 4,
+          levels: int = 6, return_levels: bool = False):
+    """Bloom of an (H, W, >=3) HDR image (Sec. 5.3; readings in epbr_oracle.c); returns (H, W, 3),
+    and with return_levels also the lists of levels 1 .. levels-1 before and after the blur.
+    The input must hold FP32-representable values (the bright-map decision is made in FP32)."""
+    x = _f64(np.asarray(hdr)[..., :3])
+    H, W = x.shape[:2]
+    y = np.zeros((H, W, 3))
+    bp = BloomParams(threshold, strength, sigma, radius, levels)
+    sizes = bloom_level_sizes(W, H, levels)
+    n = sum(w * h * 3 for w, h in sizes)
+    pyr, blr = np.zeros(n), np.zeros(n)
+    assert lib().or_bloom(_dp(x), W, H, C.byref(bp), _dp(y), _dp(pyr), _dp(blr)) == 0
+    if not return_levels:
+        return y
+    split = lambda a: [a[o:o + w * h * 3].reshape(h, w, 3) for (w, h), o in
+                       zip(sizes, np.cumsum([0] + [w * h * 3 for w, h in sizes])[:-1])]
+    return y, split(pyr), split(blr)
 
 
 def brdf(n, l, v, albedo, metal: float, rough: float) -> np.ndarray:

@@ -16,7 +16,9 @@
  *   - normal-oriented hemisphere SSAO at half resolution with a bilateral blur (Sec. 5.2;
  *     Bavoil & Sainz 2008);
  *   - ACES filmic tone mapping (Narkowicz 2015 fit) or Reinhard, then the sRGB transfer
- *     function of IEC 61966-2-1 (Sec. 5.4).
+ *     function of IEC 61966-2-1 (Sec. 5.4);
+ *   - bloom (Sec. 5.3): bright map, an image pyramid of up to six levels, a Gaussian blur of
+ *     every level from the second one up, the blurred levels added onto the image.
  * Conventions the paper leaves open (equirect mapping, sample sets, SSAO constants, rounding)
  * are stated beside the code that uses them.
  *
@@ -800,4 +802,134 @@ void or_ggx_half_vector(double xi1, double xi2, double alpha, const double* n, d
 }
 void or_equirect_lookup(const double* map, int W, int H, const double* d, double* out) {
   equirect_lookup(map, W, H, d, out);
+}
+
+/* ------------------------------------------------------------------------------------------ */
+/* Bloom (Sec. 5.3)                                                                            */
+/* ------------------------------------------------------------------------------------------ */
+/* Readings of the paper's description (it names the steps, not their constants):
+ *   bright map   B(x) = X(x) where the luminance of X(x) exceeds the threshold, else 0; the
+ *                luminance is the Rec. 709 weighting 0.2126 R + 0.7152 G + 0.0722 B.  The
+ *                comparison decides a discrete outcome, so it is made in FP32 in one fixed
+ *                order, ((0.2126 R + 0.7152 G) + 0.0722 B) with every product and sum rounded
+ *                to FP32 (the CUDA path evaluates the same expression), on FP32 inputs;
+ *   pyramid      level 0 = B at full resolution; level k = 2x2 box average of level k-1, size
+ *                ceil(W_{k-1} / 2) x ceil(H_{k-1} / 2), the odd last row / column averaging its
+ *                edge texel with itself (clamp to edge); L levels in total, 2 <= L <= 6;
+ *   blur         levels 1 .. L-1 ("from the second one upwards"): separable Gaussian of radius
+ *                R texels, weights exp(-d^2 / (2 sigma^2)) normalised to sum 1 over |d| <= R,
+ *                clamp to edge, rows then columns;
+ *   compositing  Y(x) = X(x) + s * sum_{k=1}^{L-1} U_k(x), U_k = level k after the blur sampled
+ *                bilinearly (clamp to edge) at the centre of pixel x, which lies at texel
+ *                coordinate (x + 1/2) / 2^k - 1/2 of level k.  Level 0 (the bright map itself)
+ *                is not added: it is the pyramid's source, and adding it would brighten the
+ *                bright pixels in place instead of spreading them. */
+typedef struct {
+  double threshold, strength, sigma;
+  int radius, levels;
+} or_bloom_params;
+
+static int bright_f32(double r, double g, double b, double threshold) {
+  float lr = 0.2126f * (float)r;
+  float lg = 0.7152f * (float)g;
+  float lb = 0.0722f * (float)b;
+  float lum = (lr + lg) + lb;
+  return lum > (float)threshold;
+}
+
+/* x: W*H*3 (FP32-representable values); y: W*H*3 output; levels_out (NULL allowed): levels
+ * 1 .. L-1 before (pyr) and after (blurred) the blur, each level row-major RGB, concatenated in
+ * level order, sum_k W_k H_k 3 doubles each.  Returns 0, or -1 on bad arguments. */
+int or_bloom(const double* x, int W, int H, const or_bloom_params* bp, double* y, double* pyr, double* blurred) {
+  if (W < 1 || H < 1 || bp->levels < 2 || bp->levels > 6 || bp->radius < 0 || bp->radius > 8 ||
+      !(bp->sigma > 0.0))
+    return -1;
+  int L = bp->levels, R = bp->radius;
+  double* lev[6] = {0};
+  int Wl[6], Hl[6];
+  Wl[0] = W;
+  Hl[0] = H;
+  lev[0] = (double*)malloc(sizeof(double) * 3 * (size_t)W * H);
+  for (long p = 0; p < (long)W * H; ++p) {
+    int on = bright_f32(x[3 * p], x[3 * p + 1], x[3 * p + 2], bp->threshold);
+    for (int c = 0; c < 3; ++c) lev[0][3 * p + c] = on ? x[3 * p + c] : 0.0;
+  }
+  for (int k = 1; k < L; ++k) {
+    Wl[k] = (Wl[k - 1] + 1) / 2;
+    Hl[k] = (Hl[k - 1] + 1) / 2;
+    lev[k] = (double*)malloc(sizeof(double) * 3 * (size_t)Wl[k] * Hl[k]);
+    const double* src = lev[k - 1];
+    int Ws = Wl[k - 1], Hs = Hl[k - 1];
+    for (int j = 0; j < Hl[k]; ++j)
+      for (int i = 0; i < Wl[k]; ++i)
+        for (int c = 0; c < 3; ++c) {
+          double sum = 0.0;
+          for (int b = 0; b < 2; ++b)
+            for (int a = 0; a < 2; ++a) {
+              int si = 2 * i + a < Ws ? 2 * i + a : Ws - 1;
+              int sj = 2 * j + b < Hs ? 2 * j + b : Hs - 1;
+              sum += src[3 * ((long)sj * Ws + si) + c];
+            }
+          lev[k][3 * ((long)j * Wl[k] + i) + c] = 0.25 * sum;
+        }
+  }
+  /* Gaussian weights, normalised */
+  double w[17], wsum = 0.0;
+  for (int d = -R; d <= R; ++d) {
+    w[d + R] = exp(-(double)(d * d) / (2.0 * bp->sigma * bp->sigma));
+    wsum += w[d + R];
+  }
+  for (int d = 0; d <= 2 * R; ++d) w[d] /= wsum;
+  long off = 0;
+  for (int k = 1; k < L; ++k) {
+    int Wk = Wl[k], Hk = Hl[k];
+    if (pyr) memcpy(pyr + off, lev[k], sizeof(double) * 3 * (size_t)Wk * Hk);
+    double* t = (double*)malloc(sizeof(double) * 3 * (size_t)Wk * Hk);
+    for (int j = 0; j < Hk; ++j) /* rows */
+      for (int i = 0; i < Wk; ++i)
+        for (int c = 0; c < 3; ++c) {
+          double sum = 0.0;
+          for (int d = -R; d <= R; ++d) {
+            int q = i + d < 0 ? 0 : (i + d >= Wk ? Wk - 1 : i + d);
+            sum += w[d + R] * lev[k][3 * ((long)j * Wk + q) + c];
+          }
+          t[3 * ((long)j * Wk + i) + c] = sum;
+        }
+    for (int j = 0; j < Hk; ++j) /* columns */
+      for (int i = 0; i < Wk; ++i)
+        for (int c = 0; c < 3; ++c) {
+          double sum = 0.0;
+          for (int d = -R; d <= R; ++d) {
+            int q = j + d < 0 ? 0 : (j + d >= Hk ? Hk - 1 : j + d);
+            sum += w[d + R] * t[3 * ((long)q * Wk + i) + c];
+          }
+          lev[k][3 * ((long)j * Wk + i) + c] = sum;
+        }
+    free(t);
+    if (blurred) memcpy(blurred + off, lev[k], sizeof(double) * 3 * (size_t)Wk * Hk);
+    off += 3L * Wk * Hk;
+  }
+  for (int py = 0; py < H; ++py)
+    for (int px = 0; px < W; ++px) {
+      double add[3] = {0.0, 0.0, 0.0};
+      for (int k = 1; k < L; ++k) {
+        int Wk = Wl[k], Hk = Hl[k];
+        double scale = (double)(1 << k);
+        double u = (px + 0.5) / scale - 0.5, v = (py + 0.5) / scale - 0.5;
+        double x0 = floor(u), y0 = floor(v), fx = u - x0, fy = v - y0;
+        int i0 = (int)clampd(x0, 0, Wk - 1), i1 = (int)clampd(x0 + 1, 0, Wk - 1);
+        int j0 = (int)clampd(y0, 0, Hk - 1), j1 = (int)clampd(y0 + 1, 0, Hk - 1);
+        for (int c = 0; c < 3; ++c) {
+          double a = lev[k][3 * ((long)j0 * Wk + i0) + c], b = lev[k][3 * ((long)j0 * Wk + i1) + c];
+          double p = lev[k][3 * ((long)j1 * Wk + i0) + c], q = lev[k][3 * ((long)j1 * Wk + i1) + c];
+          add[c] += (1 - fy) * ((1 - fx) * a + fx * b) + fy * ((1 - fx) * p + fx * q);
+        }
+      }
+      for (int c = 0; c < 3; ++c) {
+        long o = 3 * ((long)py * W + px) + c;
+        y[o] = x[o] + bp->strength * add[c];
+      }
+    }
+  for (int k = 0; k < L; ++k) free(lev[k]);
+  return 0;
 }
