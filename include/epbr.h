@@ -319,6 +319,42 @@ epbr_status epbr_shade_tonemap(const epbr_gbuffer* gbuffer, const epbr_camera* c
                                uint8_t* ldr, int64_t ldr_pitch, void* stream);
 
 /* ---------------------------------------------------------------------------------------- */
+/* Bloom (Sec. 5.3: bright map, image pyramid of up to six levels blurred from the second one */
+/* upwards, added onto the image)                                                            */
+/* ---------------------------------------------------------------------------------------- */
+typedef struct epbr_bloom_params {
+  float threshold;  /* a pixel enters the bright map when its luminance exceeds this */
+  float strength;   /* s: factor of the added levels, >= 0 */
+  float sigma;      /* Gaussian sigma in texels of each level, > 0 */
+  int32_t radius;   /* R: blur taps on each side, 0..8 */
+  int32_t levels;   /* L: pyramid levels including the full-resolution bright map, 2..6 */
+} epbr_bloom_params;
+
+/* Device workspace epbr_bloom needs for a width x height image: levels 1 .. L-1 before and
+ * after the blur, RGBA32F, each 256-byte aligned. */
+epbr_status epbr_bloom_workspace_size(int32_t width, int32_t height, const epbr_bloom_params* params,
+                                      size_t* bytes);
+
+/* Y = X + s * sum_{k=1}^{L-1} U_k, per pixel, where
+ *   bright map B = X where lum(X) > threshold, else 0; lum = (0.2126 R + 0.7152 G) + 0.0722 B
+ *     evaluated in FP32 with every product and sum rounded (no contraction);
+ *   level 0 = B; level k = 2x2 box average of level k-1, ceil(W_{k-1}/2) x ceil(H_{k-1}/2),
+ *     clamped to the edge;
+ *   levels 1 .. L-1 are blurred with a separable Gaussian of radius R, weights
+ *     exp(-d^2 / (2 sigma^2)) normalised over |d| <= R, clamped to the edge;
+ *   U_k = blurred level k sampled bilinearly (clamp to edge) at texel coordinate
+ *     (x + 1/2) / 2^k - 1/2 for pixel x (likewise y).
+ * `hdr` DEVICE RGBA32F/RGBA16F input (alpha ignored); `workspace` DEVICE, at least
+ * epbr_bloom_workspace_size bytes, 16-byte aligned.  Outputs (at least one): `out_hdr` DEVICE
+ * RGBA32F/RGBA16F (alpha 1; may equal `hdr` when the format and pitch are the same: every pixel
+ * is read before it is written, by the same thread), and `ldr` DEVICE uchar4, the tone map of
+ * Y with `tonemap` (required with `ldr`).  Stream-ordered; no allocation. */
+epbr_status epbr_bloom(const void* hdr, int32_t hdr_format, int64_t hdr_pitch, int32_t width, int32_t height,
+                       const epbr_bloom_params* params, void* workspace, size_t workspace_bytes,
+                       void* out_hdr, int32_t out_format, int64_t out_pitch,
+                       const epbr_tonemap_params* tonemap, uint8_t* ldr, int64_t ldr_pitch, void* stream);
+
+/* ---------------------------------------------------------------------------------------- */
 /* Batching: many views of uneven size in one persistent launch (a system form layered on the */
 /* pass; the paper renders one view per frame, Sec. 4)                                       */
 /* ---------------------------------------------------------------------------------------- */

@@ -284,6 +284,35 @@ def epbr_tonemap(hdr: torch.Tensor, hdr_format: int, tp: F.epbr_tonemap_params, 
 
 
 # ------------------------------------------------------------------------------------------
+# bloom (Sec. 5.3)
+# ------------------------------------------------------------------------------------------
+def bloom_params(threshold: float = 1.0, strength: float = 1.0, sigma: float = 2.0, radius: int = 4,
+                 levels: int = 6) -> F.epbr_bloom_params:
+    return F.epbr_bloom_params(threshold, strength, sigma, radius, levels)
+
+
+def epbr_bloom_workspace_size(W: int, H: int, bp: F.epbr_bloom_params) -> int:
+    n = C.c_size_t()
+    _check(lib().epbr_bloom_workspace_size(W, H, C.byref(bp), C.byref(n)))
+    return n.value
+
+
+def epbr_bloom(hdr: torch.Tensor, hdr_format: int, bp: F.epbr_bloom_params, out_hdr: torch.Tensor | None = None,
+               out_format: int = EPBR_HDR_RGBA32F, tp: F.epbr_tonemap_params | None = None,
+               ldr: torch.Tensor | None = None, workspace: torch.Tensor | None = None, stream=None):
+    _dev(hdr, name="hdr")
+    H, W = hdr.shape[0], hdr.shape[1]
+    need = epbr_bloom_workspace_size(W, H, bp)
+    ws = workspace if workspace is not None else _workspace(need, hdr.device)
+    op = _dev(out_hdr, name="out_hdr") if out_hdr is not None else None
+    lp = _dev(ldr, torch.uint8, "ldr") if ldr is not None else None
+    _check(lib().epbr_bloom(hdr.data_ptr(), hdr_format, _pitch(hdr, 1), W, H, C.byref(bp), _aligned(ws),
+                            ws.numel() - (_aligned(ws) - ws.data_ptr()), op, out_format,
+                            _pitch(out_hdr, 1) if out_hdr is not None else 0, C.byref(tp) if tp is not None else None,
+                            lp, _pitch(ldr, 1) if ldr is not None else 0, _stream(stream)))
+
+
+# ------------------------------------------------------------------------------------------
 # batching: many views, one persistent launch replayed from a CUDA graph
 # ------------------------------------------------------------------------------------------
 def view(g: GBuffer, cam: F.epbr_camera, lights: torch.Tensor | None, ibl_index: int, ldr: torch.Tensor,

@@ -83,6 +83,11 @@ class epbr_tonemap_params(C.Structure):
     _fields_ = [("exposure", C.c_float), ("op", C.c_int32)]
 
 
+class epbr_bloom_params(C.Structure):
+    _fields_ = [("threshold", C.c_float), ("strength", C.c_float), ("sigma", C.c_float), ("radius", C.c_int32),
+                ("levels", C.c_int32)]
+
+
 class epbr_view(C.Structure):
     _fields_ = [("gbuffer", epbr_gbuffer), ("camera", epbr_camera), ("lights", C.c_void_p),
                 ("num_lights", C.c_int32), ("ibl_index", C.c_int32), ("hdr", C.c_void_p), ("hdr_pitch", C.c_int64),
@@ -141,6 +146,9 @@ PROTOTYPES = {
     "epbr_shade_tonemap": [P(epbr_gbuffer), P(epbr_camera), vp, i32, P(epbr_ibl), P(epbr_shade_params), vp,
                            i32, i64, P(epbr_tonemap_params), vp, i64, vp],
     "epbr_tonemap": [vp, i32, i32, i32, i64, P(epbr_tonemap_params), vp, i64, vp],
+    "epbr_bloom_workspace_size": [i32, i32, P(epbr_bloom_params), P(sz)],
+    "epbr_bloom": [vp, i32, i64, i32, i32, P(epbr_bloom_params), vp, sz, vp, i32, i64, P(epbr_tonemap_params), vp,
+                   i64, vp],
     "epbr_batch_create": [P(epbr_view), i32, P(epbr_ibl), i32, P(epbr_batch_params), P(vp)],
     "epbr_batch_launch": [vp, vp],
     "epbr_batch_autotune": [vp, C.c_char_p, vp],

@@ -361,6 +361,25 @@ def make_hdr_field(seed: int, width: int, height: int) -> np.ndarray:
     return x.astype(np.float32)
 
 
+def make_bloom_field(seed: int, width: int, height: int, n_spots: int = 12) -> np.ndarray:
+    """Synthetic HDR RGBA32F frame for the bloom tests: a smooth gradient in [0, 0.8] (below a
+    threshold of 1) with `n_spots` bright discs (radius 1..24 px, values 2..60) and a few isolated
+    bright pixels, so that the bright map is sparse and has both blobs and single texels."""
+    g = np.random.Generator(np.random.PCG64(seed))
+    yy, xx = np.mgrid[0:height, 0:width].astype(np.float64)
+    base = 0.8 * (0.5 * (xx / max(width - 1, 1)) + 0.3 * (yy / max(height - 1, 1)) + 0.2 * g.uniform(size=(height, width)))
+    img = np.repeat(base[..., None], 4, axis=2) * np.array([1.0, 0.9, 0.8, 0.0])
+    for _ in range(n_spots):
+        cx, cy, r = g.uniform(0, width), g.uniform(0, height), g.uniform(1, 24)
+        val = g.uniform(2, 60, 3)
+        m = (xx - cx) ** 2 + (yy - cy) ** 2 <= r * r
+        img[m, :3] = val
+    for _ in range(max(1, width * height // 4096)):
+        img[int(g.uniform(0, height)), int(g.uniform(0, width)), :3] = g.uniform(2, 100, 3)
+    img[..., 3] = 1.0
+    return img.astype(np.float32)
+
+
 BATCH_RESOLUTIONS = [(512, 512), (1280, 720), (1920, 1080), (3840, 2160)]
 
 
