@@ -44,6 +44,8 @@ def parse():
     ap.add_argument("--serve-seconds", type=float, default=3.0, help="arrival window per rate (serve workload)")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="CPU-baseline time budget")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--bloom", action="store_true",
+                    help="add the bloom pass (Sec. 5.3) to the frame: shade to HDR, then bloom + tone map")
     return ap.parse_args()
 
 
@@ -75,6 +77,22 @@ def workload_inputs(name: str):
     k = synth.make_ssao_kernel(c["seed"], c["ssao_k"])
     nz = synth.make_ssao_noise(c["seed"])
     return c, sc, g, env, k, nz
+
+
+BLOOM = {"threshold": 1.0, "strength": 0.5, "sigma": 2.0, "radius": 4, "levels": 6}
+
+
+def _hbm_peak_gbs() -> float:
+    """Measured copy bandwidth of this machine's GPUs (MEASURED_PEAKS.json), else 6800 GB/s."""
+    try:
+        with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"])
+    except (OSError, KeyError, ValueError):
+        return 6800.0
+
+
+HBM_PEAK_GBS = _hbm_peak_gbs()
+BLOOM_LAUNCHES = 3  # pyramid, blur of every level, composite with the tone map
 
 
 def config_dict(c, name, extra=None):
@@ -237,9 +255,11 @@ def sources_sha(files=SHADE_SOURCES):
 # ------------------------------------------------------------------------------------------
 # CPU oracle baseline
 # ------------------------------------------------------------------------------------------
-def oracle_frame_rate(c, sc, g, env, k, nz, seconds: float, oracle_ibl=None, threads: int = 0):
+def oracle_frame_rate(c, sc, g, env, k, nz, seconds: float, oracle_ibl=None, threads: int = 0, bloom=False):
     """The FP64 oracle's per-frame path (blurred SSAO, compose, tone map) on horizontal bands of
-    the frame until `seconds` elapse; returns (Mpixels/s, cores, sample description)."""
+    the frame until `seconds` elapse; returns (Mpixels/s, cores, sample description).  With
+    `bloom`, the oracle's bloom of one whole frame (it needs the whole image) is timed as well and
+    its time per pixel added."""
     import oracle
     W, H = c["width"], c["height"]
     if oracle_ibl is None:
@@ -271,6 +291,14 @@ def oracle_frame_rate(c, sc, g, env, k, nz, seconds: float, oracle_ibl=None, thr
         px_done += pixels.size
         y0 = (y0 + band) % H
     dt = time.perf_counter() - t0
+    if bloom:
+        frame = synth.make_bloom_field(1, W, H)
+        tb = time.perf_counter()
+        oracle.bloom(frame, **BLOOM)
+        tb = time.perf_counter() - tb
+        rate = 1.0 / (dt / px_done + tb / (W * H)) / 1e6
+        return rate, cores, (f"{px_done} px in {px_done // W} full-width rows ({dt:.1f} s wall) + the bloom of one "
+                             f"{W}x{H} frame ({tb:.2f} s, one thread)")
     return px_done / dt / 1e6, cores, f"{px_done} px in {px_done // W} full-width rows ({dt:.1f} s wall)"
 
 
@@ -359,20 +387,38 @@ def run_gpu(args):
     tp = ep.tonemap_params(1.0, ep.EPBR_TONEMAP_ACES)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
 
-    ev_shade = []
+    ev_shade, ev_bloom = [], []
+    bp = ep.bloom_params(**BLOOM) if args.bloom else None
+    ws_bloom = torch.empty(ep.epbr_bloom_workspace_size(W, H, bp) + 256, dtype=torch.uint8, device=dev) \
+        if args.bloom else None
+
+    def compose(g_, shp_, hdr_, ldr_, lights_, record=False):
+        """Compose (+ bloom): with bloom the compose writes HDR only and the bloom pass tone-maps."""
+        if record:
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+        if args.bloom:
+            ep.epbr_shade(g_, cam, lights_, ibl, shp_, hdr_, hdr_fmt, stream=stream)
+        else:
+            ep.epbr_shade_tonemap(g_, cam, lights_, ibl, shp_, hdr_, hdr_fmt, tp, ldr_, stream=stream)
+        if record:
+            b.record(stream)
+            ev_shade.append((a, b))
+        if args.bloom:
+            if record:
+                a2, b2 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a2.record(stream)
+            ep.epbr_bloom(hdr_, hdr_fmt, bp, None, 0, tp, ldr_, workspace=ws_bloom, stream=stream)
+            if record:
+                b2.record(stream)
+                ev_bloom.append((a2, b2))
 
     def step(record=False):
         ep.epbr_ssao_raw(gb, cam, sp, ao_raw, stream=stream)
         ep.epbr_ssao_blur(gb, sp, ao_raw, ao, stream=stream)
-        if record:
-            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            a.record(stream)
-        ep.epbr_shade_tonemap(gb, cam, lights, ibl, shp, hdr, hdr_fmt, tp, ldr, stream=stream)
-        if record:
-            b.record(stream)
-            ev_shade.append((a, b))
+        compose(gb, shp, hdr, ldr, lights, record)
 
-    launches_per_step = 3
+    launches_per_step = 3 + (BLOOM_LAUNCHES if args.bloom else 0)
     with torch.cuda.stream(stream):
         for _ in range(max(3, args.warmup)):
             step()
@@ -453,8 +499,7 @@ def run_gpu(args):
             flush.zero_()  # L2 flush inside the timed window
             ep.epbr_ssao_raw(b["gb"], cam, sp, b["ao_raw"], stream=stream)
             ep.epbr_ssao_blur(b["gb"], sp, b["ao_raw"], b["ao"], stream=stream)
-            ep.epbr_shade_tonemap(b["gb"], cam, b["lights"], ibl, b["shp"], b["hdr"], hdr_fmt, tp, b["ldr"],
-                                  stream=stream)
+            compose(b["gb"], b["shp"], b["hdr"], b["ldr"], b["lights"])
             c = ev()
             c.record(stream)
         done_comp[i % 2] = c
@@ -506,7 +551,10 @@ def run_gpu(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": config_dict(c, name, {"precompute_ms": precompute_ms,
                                             "median_step_ms": statistics.median(step_ms),
-                                            "wall_s": wall}),
+                                            "wall_s": wall,
+                                            **({"step": "ssao_raw + ssao_blur + shade (HDR) + bloom with the tone map "
+                                                        "fused per frame; lighting set precomputed once",
+                                                "bloom": BLOOM} if args.bloom else {})}),
             "roofline": roofline,
             "e2e": {"value": e2e_value, "unit": "Mpixels/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                     "how": "pinned host G-buffer + lights uploaded and RGBA8 downloaded every step; frames "
@@ -514,8 +562,19 @@ def run_gpu(args):
                            "streams with 2 buffer sets; L2 flush inside the window"},
             "gpu_launches": launches_per_step * args.steps,
             "clocks": clocks}
+    if args.bloom:
+        bloom_ms = statistics.mean(a.elapsed_time(b) for a, b in ev_bloom)
+        hdr_bytes = 8 if compact else 16
+        # compulsory traffic of the pass: the HDR image read twice (bright pass, composite), level 1
+        # written once (a quarter of the pixels, 16 B) and the RGBA8 image written
+        bloom_bytes = W * H * (2 * hdr_bytes + 4 + 4)
+        line["bloom"] = {"ms": bloom_ms, "launches": BLOOM_LAUNCHES, "bound": "hbm",
+                         "algorithmic_bytes": bloom_bytes, "achieved": bloom_bytes / (bloom_ms * 1e-3) / 1e9,
+                         "peak": HBM_PEAK_GBS, "unit": "GB/s",
+                         "frac": bloom_bytes / (bloom_ms * 1e-3) / 1e9 / HBM_PEAK_GBS}
     if not args.no_cpu_baseline and world == 1:
-        rate, cores, sample = oracle_frame_rate(dict(c, name=name), sc, g, env, k, nz, args.cpu_seconds)
+        rate, cores, sample = oracle_frame_rate(dict(c, name=name), sc, g, env, k, nz, args.cpu_seconds,
+                                                bloom=args.bloom)
         line["cpu_baseline"] = {"value": rate, "unit": "Mpixels/s", "cores": cores, "kind": "oracle",
                                 "sample": sample}
     print(json.dumps(line), flush=True)

@@ -1,13 +1,17 @@
 // Bloom (Sec. 5.3): bright map, image pyramid, blur of every level from the second one upwards,
 // the blurred levels added onto the image (then, optionally, the tone map of Sec. 5.4).
-//   k_bloom_bright_down  level 1 straight from the HDR image: each thread applies the bright test
-//                        to its 2x2 pixels and averages them (the full-resolution bright map,
-//                        level 0, is never stored)
-//   k_bloom_down         level k from level k-1, 2x2 box average, clamped to the edge
-//   k_bloom_blur         every level 1 .. L-1 in one launch: a 32x8 texel tile plus an R-texel halo
-//                        in shared memory, rows then columns of the separable Gaussian
-//   k_bloom_composite    per pixel: X + s * sum_k bilinear(level k at the pixel centre), HDR store
-//                        and / or the fused tone map
+//   k_bloom_pyramid    levels 1 .. L-1 in one launch: a block reads a 64x64-pixel footprint,
+//                      applies the bright test and averages 2x2 pixels into its 32x32 level-1
+//                      tile, then halves the tile in shared memory level by level.  A level's
+//                      clamp to the edge never reaches outside the block, because tiles are
+//                      aligned to powers of two.  The full-resolution bright map is never stored.
+//   k_bloom_blur       every level in one launch: a 32x16 texel tile plus an R-texel halo in shared
+//                      memory, rows then columns of the separable Gaussian
+//   k_bloom_composite  one 2x2 pixel quad per thread: X + s * sum_k bilinear(level k at the pixel
+//                      centre), HDR store and / or the fused tone map.  On level 1 the quad's four
+//                      bilinear footprints lie in a 3x3 texel block; on level k >= 2 both pixels of
+//                      a row (or column) pair fall in the same texel cell, so the quad loads 2x2
+//                      texels per level.  Each pixel's arithmetic is the per-pixel bilinear.
 #include <string.h>
 
 #include <cmath>
@@ -17,7 +21,8 @@
 namespace epbr {
 
 constexpr int kBloomMaxLevels = 6, kBloomMaxR = 8;
-constexpr int kBloomTX = 32, kBloomTY = 8;
+constexpr int kBloomTX = 32, kBloomTY = 8;       // threads per block: 32 x 8
+constexpr int kBlurTW = 32, kBlurTH = 16;         // blur output tile
 
 struct BloomLevel {
   float4* pyr;  // before the blur
@@ -41,37 +46,65 @@ __device__ __forceinline__ bool bloom_bright(float3 c, float threshold) {
 
 template <int HF>
 __global__ void __launch_bounds__(kBloomTX* kBloomTY)
-    k_bloom_bright_down(const void* __restrict__ hdr, long long pitch, int W, int H, float threshold,
-                        float4* __restrict__ p1, int W1, int H1) {
-  int i = blockIdx.x * kBloomTX + threadIdx.x, j = blockIdx.y * kBloomTY + threadIdx.y;
-  if (i >= W1 || j >= H1) return;
-  float3 sum = f3(0, 0, 0);
+    k_bloom_pyramid(const void* __restrict__ hdr, long long pitch, int W, int H, float threshold, BloomDev d) {
+  __shared__ float4 s_a[32 * 32];  // levels 1, 3, 5 of the block's tile
+  __shared__ float4 s_b[16 * 16];  // levels 2, 4
+  const int tid = threadIdx.y * kBloomTX + threadIdx.x;
+  {
+    const BloomLevel& l1 = d.lev[1];
 #pragma unroll
-  for (int b = 0; b < 2; ++b)
+    for (int r = 0; r < 4; ++r) {
+      int li = threadIdx.x, lj = threadIdx.y + 8 * r;
+      int i = blockIdx.x * 32 + li, j = blockIdx.y * 32 + lj;
+      float3 sum = f3(0, 0, 0);
+      if (i < l1.W && j < l1.H) {
 #pragma unroll
-    for (int a = 0; a < 2; ++a) {
-      float3 c = load_hdr<HF>(hdr, pitch, min(2 * i + a, W - 1), min(2 * j + b, H - 1));
-      if (bloom_bright(c, threshold)) sum = sum + c;
+        for (int b = 0; b < 2; ++b)
+#pragma unroll
+          for (int a = 0; a < 2; ++a) {
+            float3 c = load_hdr<HF>(hdr, pitch, min(2 * i + a, W - 1), min(2 * j + b, H - 1));
+            if (bloom_bright(c, threshold)) sum = sum + c;
+          }
+        sum = 0.25f * sum;
+        l1.pyr[(size_t)j * l1.W + i] = make_float4(sum.x, sum.y, sum.z, 0.0f);
+      }
+      s_a[lj * 32 + li] = make_float4(sum.x, sum.y, sum.z, 0.0f);
     }
-  p1[(size_t)j * W1 + i] = make_float4(0.25f * sum.x, 0.25f * sum.y, 0.25f * sum.z, 0.0f);
-}
-
-__global__ void __launch_bounds__(kBloomTX* kBloomTY)
-    k_bloom_down(const float4* __restrict__ src, int Ws, int Hs, float4* __restrict__ dst, int Wd, int Hd) {
-  int i = blockIdx.x * kBloomTX + threadIdx.x, j = blockIdx.y * kBloomTY + threadIdx.y;
-  if (i >= Wd || j >= Hd) return;
-  float3 sum = f3(0, 0, 0);
+  }
 #pragma unroll
-  for (int b = 0; b < 2; ++b)
+  for (int k = 2; k < kBloomMaxLevels; ++k) {
+    if (k >= d.L) break;
+    __syncthreads();  // level k-1 of the tile is in shared memory
+    const float4* src = (k & 1) ? s_b : s_a;
+    float4* dst = (k & 1) ? s_a : s_b;
+    const int side = 32 >> (k - 1), sside = 2 * side;  // tile side of level k and of level k-1
+    const BloomLevel& ls = d.lev[k - 1];
+    const BloomLevel& lv = d.lev[k];
+    if (tid < side * side) {
+      int li = tid % side, lj = tid / side;
+      int i = blockIdx.x * side + li, j = blockIdx.y * side + lj;
+      float3 sum = f3(0, 0, 0);
+      if (i < lv.W && j < lv.H) {
+        // source texels clamped to level k-1's edge, as local indices of the block's tile
 #pragma unroll
-    for (int a = 0; a < 2; ++a) sum = sum + xyz(__ldg(src + (size_t)min(2 * j + b, Hs - 1) * Ws + min(2 * i + a, Ws - 1)));
-  dst[(size_t)j * Wd + i] = make_float4(0.25f * sum.x, 0.25f * sum.y, 0.25f * sum.z, 0.0f);
+        for (int b = 0; b < 2; ++b)
+#pragma unroll
+          for (int a = 0; a < 2; ++a) {
+            int si = min(2 * i + a, ls.W - 1) - blockIdx.x * sside, sj = min(2 * j + b, ls.H - 1) - blockIdx.y * sside;
+            sum = sum + xyz(src[sj * sside + si]);
+          }
+        sum = 0.25f * sum;
+        lv.pyr[(size_t)j * lv.W + i] = make_float4(sum.x, sum.y, sum.z, 0.0f);
+      }
+      dst[lj * side + li] = make_float4(sum.x, sum.y, sum.z, 0.0f);
+    }
+  }
 }
 
 __global__ void __launch_bounds__(kBloomTX* kBloomTY) k_bloom_blur(BloomDev d) {
-  constexpr int TW = kBloomTX + 2 * kBloomMaxR, TH = kBloomTY + 2 * kBloomMaxR;
+  constexpr int TW = kBlurTW + 2 * kBloomMaxR, TH = kBlurTH + 2 * kBloomMaxR;
   __shared__ float4 s_in[TH][TW];
-  __shared__ float4 s_row[TH][kBloomTX];
+  __shared__ float4 s_row[TH][kBlurTW];
   __shared__ float s_w[2 * kBloomMaxR + 1];
   const int tid = threadIdx.y * kBloomTX + threadIdx.x;
   const int R = d.R;
@@ -86,59 +119,129 @@ __global__ void __launch_bounds__(kBloomTX* kBloomTY) k_bloom_blur(BloomDev d) {
   for (int q = 2; q < kBloomMaxLevels; ++q)
     if (q == k) lv = d.lev[q], tiles_x = d.tiles_x[q];
   b -= d.tile_start[k];
-  const int x0 = (b % tiles_x) * kBloomTX, y0 = (b / tiles_x) * kBloomTY;
-  const int tw = kBloomTX + 2 * R, th = kBloomTY + 2 * R;
-  for (int q = tid; q < tw * th; q += kBloomTX * kBloomTY) {
-    int ty = q / tw, tx = q - ty * tw;
-    int x = min(max(x0 - R + tx, 0), lv.W - 1), y = min(max(y0 - R + ty, 0), lv.H - 1);
-    s_in[ty][tx] = __ldg(lv.pyr + (size_t)y * lv.W + x);
+  const int by = b / tiles_x;
+  const int x0 = (b - by * tiles_x) * kBlurTW, y0 = by * kBlurTH;
+  const int tw = kBlurTW + 2 * R, th = kBlurTH + 2 * R;
+  for (int ty = threadIdx.y; ty < th; ty += kBloomTY) {
+    const float4* row = lv.pyr + (size_t)min(max(y0 - R + ty, 0), lv.H - 1) * lv.W;
+    for (int tx = threadIdx.x; tx < tw; tx += kBloomTX) s_in[ty][tx] = __ldg(row + min(max(x0 - R + tx, 0), lv.W - 1));
   }
   __syncthreads();
-  for (int q = tid; q < th * kBloomTX; q += kBloomTX * kBloomTY) {
-    int ty = q / kBloomTX, tx = q - ty * kBloomTX;
+  for (int ty = threadIdx.y; ty < th; ty += kBloomTY) {
     float3 sum = f3(0, 0, 0);
-    for (int t = 0; t <= 2 * R; ++t) sum = sum + s_w[t] * xyz(s_in[ty][tx + t]);
-    s_row[ty][tx] = make_float4(sum.x, sum.y, sum.z, 0.0f);
+#pragma unroll
+    for (int t = 0; t <= 2 * kBloomMaxR; ++t) {
+      if (t > 2 * R) break;
+      sum = sum + s_w[t] * xyz(s_in[ty][threadIdx.x + t]);
+    }
+    s_row[ty][threadIdx.x] = make_float4(sum.x, sum.y, sum.z, 0.0f);
   }
   __syncthreads();
-  int x = x0 + threadIdx.x, y = y0 + threadIdx.y;
-  if (x >= lv.W || y >= lv.H) return;
-  float3 sum = f3(0, 0, 0);
-  for (int t = 0; t <= 2 * R; ++t) sum = sum + s_w[t] * xyz(s_row[threadIdx.y + t][threadIdx.x]);
-  lv.blr[(size_t)y * lv.W + x] = make_float4(sum.x, sum.y, sum.z, 0.0f);
+  const int x = x0 + threadIdx.x;
+#pragma unroll
+  for (int r = 0; r < kBlurTH / kBloomTY; ++r) {
+    const int ly = threadIdx.y + r * kBloomTY, y = y0 + ly;
+    if (x >= lv.W || y >= lv.H) continue;
+    float3 sum = f3(0, 0, 0);
+#pragma unroll
+    for (int t = 0; t <= 2 * kBloomMaxR; ++t) {
+      if (t > 2 * R) break;
+      sum = sum + s_w[t] * xyz(s_row[ly + t][threadIdx.x]);
+    }
+    lv.blr[(size_t)y * lv.W + x] = make_float4(sum.x, sum.y, sum.z, 0.0f);
+  }
 }
 
-// Level k sampled bilinearly at the centre of pixel (x, y): texel coordinate (x + 1/2) 2^-k - 1/2,
-// exact in FP32 for the admitted image sizes.
-__device__ __forceinline__ float3 bloom_sample(const BloomLevel& lv, int k, int x, int y) {
-  float s = __int_as_float((127 - k) << 23);  // 2^-k
-  float u = fmaf((float)x + 0.5f, s, -0.5f), v = fmaf((float)y + 0.5f, s, -0.5f);
-  float fu = floorf(u), fv = floorf(v);
-  float fx = u - fu, fy = v - fv;
-  int iu = (int)fu, iv = (int)fv;
-  int i0 = min(max(iu, 0), lv.W - 1), i1 = min(max(iu + 1, 0), lv.W - 1);
-  int j0 = min(max(iv, 0), lv.H - 1), j1 = min(max(iv + 1, 0), lv.H - 1);
-  const float4* r0 = lv.blr + (size_t)j0 * lv.W;
-  const float4* r1 = lv.blr + (size_t)j1 * lv.W;
-  float3 a = xyz(__ldg(r0 + i0)), b = xyz(__ldg(r0 + i1)), p = xyz(__ldg(r1 + i0)), q = xyz(__ldg(r1 + i1));
-  float3 top = a + fx * (b - a), bot = p + fx * (q - p);
-  return top + fy * (bot - top);
+__device__ __forceinline__ float3 lerp3(float3 a, float3 b, float t) { return a + t * (b - a); }
+
+// The bilinear value at fractions (fx, fy) of the texel cell with corners a (top left), b (top
+// right), p (bottom left), q (bottom right).
+__device__ __forceinline__ float3 bilerp(float3 a, float3 b, float3 p, float3 q, float fx, float fy) {
+  float3 top = lerp3(a, b, fx), bot = lerp3(p, q, fx);
+  return lerp3(top, bot, fy);
+}
+
+// Adds s * sum_k (level k sampled bilinearly at the pixel centre) to the quad's four pixels
+// c[b][a] = pixel (2 qi + a, 2 qj + b).  Pixel x lies at texel coordinate u = (x + 1/2) 2^-k - 1/2
+// of level k, exact in FP32 for the admitted sizes.
+__device__ __forceinline__ void bloom_add_quad(const BloomDev& d, float strength, int qi, int qj, float3 (&c)[2][2]) {
+  float3 add[2][2] = {{f3(0, 0, 0), f3(0, 0, 0)}, {f3(0, 0, 0), f3(0, 0, 0)}};
+  {
+    // level 1: pixel 2 qi sits at u = qi - 1/4 (cell qi-1, fraction 3/4), pixel 2 qi + 1 at
+    // qi + 1/4 (cell qi, fraction 1/4): the footprints span texels qi-1 .. qi+1
+    const BloomLevel& lv = d.lev[1];
+    int ci[3], cj[3];
+#pragma unroll
+    for (int t = 0; t < 3; ++t) {
+      ci[t] = min(max(qi - 1 + t, 0), lv.W - 1);
+      cj[t] = min(max(qj - 1 + t, 0), lv.H - 1);
+    }
+    float3 T[3][3];
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+      const float4* row = lv.blr + (size_t)cj[r] * lv.W;
+#pragma unroll
+      for (int t = 0; t < 3; ++t) T[r][t] = xyz(__ldg(row + ci[t]));
+    }
+#pragma unroll
+    for (int b = 0; b < 2; ++b)
+#pragma unroll
+      for (int a = 0; a < 2; ++a)
+        add[b][a] = add[b][a] + bilerp(T[b][a], T[b][a + 1], T[b + 1][a], T[b + 1][a + 1], a ? 0.25f : 0.75f,
+                                       b ? 0.25f : 0.75f);
+  }
+#pragma unroll
+  for (int k = 2; k < kBloomMaxLevels; ++k) {
+    if (k >= d.L) break;
+    // both pixels of a pair share floor(u) on this level (the pair's coordinates differ by
+    // 2^(1-k) <= 1/2 and no integer lies between them), so the quad reads one texel cell
+    const BloomLevel& lv = d.lev[k];
+    const float sc = __int_as_float((127 - k) << 23);  // 2^-k
+    float u[2], v[2];
+#pragma unroll
+    for (int a = 0; a < 2; ++a) {
+      u[a] = fmaf((float)(2 * qi + a) + 0.5f, sc, -0.5f);
+      v[a] = fmaf((float)(2 * qj + a) + 0.5f, sc, -0.5f);
+    }
+    const float fu = floorf(u[0]), fv = floorf(v[0]);
+    const int iu = (int)fu, iv = (int)fv;
+    const int i0 = min(max(iu, 0), lv.W - 1), i1 = min(max(iu + 1, 0), lv.W - 1);
+    const int j0 = min(max(iv, 0), lv.H - 1), j1 = min(max(iv + 1, 0), lv.H - 1);
+    const float4* r0 = lv.blr + (size_t)j0 * lv.W;
+    const float4* r1 = lv.blr + (size_t)j1 * lv.W;
+    float3 A = xyz(__ldg(r0 + i0)), B = xyz(__ldg(r0 + i1)), P = xyz(__ldg(r1 + i0)), Q = xyz(__ldg(r1 + i1));
+#pragma unroll
+    for (int b = 0; b < 2; ++b)
+#pragma unroll
+      for (int a = 0; a < 2; ++a) add[b][a] = add[b][a] + bilerp(A, B, P, Q, u[a] - fu, v[b] - fv);
+  }
+#pragma unroll
+  for (int b = 0; b < 2; ++b)
+#pragma unroll
+    for (int a = 0; a < 2; ++a) c[b][a] = c[b][a] + strength * add[b][a];
 }
 
 template <int HF, int OF, bool LDR>
 __global__ void __launch_bounds__(kBloomTX* kBloomTY)
     k_bloom_composite(const void* __restrict__ hdr, long long pitch, int W, int H, BloomDev d, float strength,
                       void* out, long long out_pitch, float exposure, int op, uint8_t* ldr, long long ldr_pitch) {
-  int x = blockIdx.x * kBloomTX + threadIdx.x, y = blockIdx.y * kBloomTY + threadIdx.y;
-  if (x >= W || y >= H) return;
-  float3 X = load_hdr<HF>(hdr, pitch, x, y);
-  float3 add = f3(0, 0, 0);
+  const int qi = blockIdx.x * kBloomTX + threadIdx.x, qj = blockIdx.y * kBloomTY + threadIdx.y;
+  if (2 * qi >= W || 2 * qj >= H) return;
+  float3 c[2][2];
 #pragma unroll
-  for (int k = 1; k < kBloomMaxLevels; ++k)
-    if (k < d.L) add = add + bloom_sample(d.lev[k], k, x, y);
-  float3 Y = X + strength * add;
-  if (out) store_hdr<OF>(out, out_pitch, x, y, Y);
-  if (LDR) ((unsigned*)(ldr + (size_t)y * ldr_pitch))[x] = pack_rgba8(Y, exposure, op);
+  for (int b = 0; b < 2; ++b)
+#pragma unroll
+    for (int a = 0; a < 2; ++a) c[b][a] = load_hdr<HF>(hdr, pitch, min(2 * qi + a, W - 1), min(2 * qj + b, H - 1));
+  bloom_add_quad(d, strength, qi, qj, c);
+#pragma unroll
+  for (int b = 0; b < 2; ++b)
+#pragma unroll
+    for (int a = 0; a < 2; ++a) {
+      int x = 2 * qi + a, y = 2 * qj + b;
+      if (x >= W || y >= H) continue;
+      if (out) store_hdr<OF>(out, out_pitch, x, y, c[b][a]);
+      if (LDR) ((unsigned*)(ldr + (size_t)y * ldr_pitch))[x] = pack_rgba8(c[b][a], exposure, op);
+    }
 }
 
 static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
@@ -232,27 +335,23 @@ extern "C" epbr_status epbr_bloom(const void* hdr, int32_t hdr_format, int64_t h
   int tiles = 0;
   for (int k = 1; k < L; ++k) {
     d.tile_start[k] = tiles;
-    d.tiles_x[k] = (d.lev[k].W + kBloomTX - 1) / kBloomTX;
-    tiles += d.tiles_x[k] * ((d.lev[k].H + kBloomTY - 1) / kBloomTY);
+    d.tiles_x[k] = (d.lev[k].W + kBlurTW - 1) / kBlurTW;
+    tiles += d.tiles_x[k] * ((d.lev[k].H + kBlurTH - 1) / kBlurTH);
   }
   d.tile_start[L] = tiles;
   cudaStream_t s = (cudaStream_t)stream;
   dim3 blk(kBloomTX, kBloomTY);
   auto grid_of = [](int w, int h) { return dim3((w + kBloomTX - 1) / kBloomTX, (h + kBloomTY - 1) / kBloomTY); };
-  const BloomLevel& l1 = d.lev[1];
+  // pyramid blocks: one per 32x32 tile of level 1 (64x64 pixels)
+  dim3 gp((d.lev[1].W + 31) / 32, (d.lev[1].H + 31) / 32);
   if (hdr_format == EPBR_HDR_RGBA32F)
-    k_bloom_bright_down<EPBR_HDR_RGBA32F><<<grid_of(l1.W, l1.H), blk, 0, s>>>(hdr, hdr_pitch, width, height,
-                                                                              params->threshold, l1.pyr, l1.W, l1.H);
+    k_bloom_pyramid<EPBR_HDR_RGBA32F><<<gp, blk, 0, s>>>(hdr, hdr_pitch, width, height, params->threshold, d);
   else
-    k_bloom_bright_down<EPBR_HDR_RGBA16F><<<grid_of(l1.W, l1.H), blk, 0, s>>>(hdr, hdr_pitch, width, height,
-                                                                              params->threshold, l1.pyr, l1.W, l1.H);
-  for (int k = 2; k < L; ++k)
-    k_bloom_down<<<grid_of(d.lev[k].W, d.lev[k].H), blk, 0, s>>>(d.lev[k - 1].pyr, d.lev[k - 1].W, d.lev[k - 1].H,
-                                                                 d.lev[k].pyr, d.lev[k].W, d.lev[k].H);
+    k_bloom_pyramid<EPBR_HDR_RGBA16F><<<gp, blk, 0, s>>>(hdr, hdr_pitch, width, height, params->threshold, d);
   k_bloom_blur<<<tiles, blk, 0, s>>>(d);
   float exposure = tonemap ? tonemap->exposure : 1.0f;
   int op = tonemap ? tonemap->op : 0;
-  dim3 g = grid_of(width, height);
+  dim3 g = grid_of((width + 1) / 2, (height + 1) / 2);  // one thread per 2x2 pixel quad
   bool in32 = hdr_format == EPBR_HDR_RGBA32F, out32 = !out_hdr || out_format == EPBR_HDR_RGBA32F;
   if (in32 && out32)
     launch_composite<EPBR_HDR_RGBA32F, EPBR_HDR_RGBA32F>(g, blk, s, hdr, hdr_pitch, width, height, d, params->strength,
