@@ -50,6 +50,11 @@ class BloomParams(C.Structure):
                 ("radius", C.c_int), ("levels", C.c_int)]
 
 
+class Shadows(C.Structure):
+    _fields_ = [("maps", C.POINTER(C.c_double)), ("cams", C.POINTER(C.c_double)), ("S", C.c_int),
+                ("b0", C.c_double), ("b1", C.c_double)]
+
+
 class Ibl(C.Structure):
     _fields_ = [("irr", C.POINTER(C.c_double)), ("Wi", C.c_int), ("Hi", C.c_int), ("M", C.c_int),
                 ("level", C.POINTER(C.c_double) * MAX_LEVELS), ("Wl", C.c_int * MAX_LEVELS),
@@ -89,6 +94,10 @@ def lib():
             L.or_equirect_lookup.argtypes = [dp, C.c_int, C.c_int, dp, dp]
             L.or_equirect_lookup.restype = None
             L.or_num_threads.argtypes = [C.c_int]
+            L.or_shade_shadows.argtypes = [dp, C.POINTER(Camera), dp, C.c_int, C.POINTER(Ibl), dp, C.c_int,
+                                           C.c_int, C.POINTER(Shadows), lp, C.c_long, dp, dp, dp, C.c_int]
+            L.or_shadow_vis.argtypes = [C.POINTER(Shadows), C.c_int, dp, dp]
+            L.or_shadow_vis.restype = None
             L.or_bloom.argtypes = [dp, C.c_int, C.c_int, C.POINTER(BloomParams), dp, dp, dp]
             _lib = L
     return _lib
@@ -264,6 +273,43 @@ def shade(gb, cam: Camera, lights, ibl: IblSet | None, flags: int, ao=None, ao_s
     assert lib().or_shade(_dp(gb), C.byref(cam), lp, len(lights), ib, aop, ao_scale, flags, pp,
                           n if px is not None else 0, _dp(out), threads) == 0
     return out if px is not None else out.reshape(cam.H, cam.W, 3)
+
+
+def shade_shadows(gb, cam: Camera, lights, ibl: IblSet | None, flags: int, maps, cams, b0: float, b1: float,
+                  ao=None, ao_scale: int = 1, pixels=None, threads: int = 0):
+    """shade() with shadow maps and 3x3 PCF (Sec. 5.1; readings in epbr_oracle.c).  maps: (NL, S, S)
+    eye depths; cams: (NL, 16) world->light-view rows and f.  Returns (out, lo, hi), lo / hi the
+    radiance with every tied shadow decision taken the darker / brighter way."""
+    keep = _Keep()
+    gb = _f64(gb)
+    lights = np.asarray(lights, np.float64).reshape(-1, 8)[:, :7] if len(lights) else np.zeros((0, 7))
+    lp = keep.ptr(lights) if len(lights) else None
+    ib = C.byref(ibl.struct(keep)) if ibl is not None else None
+    aop = keep.ptr(ao) if ao is not None else None
+    m = _f64(maps)
+    cm = _f64(cams)
+    assert m.ndim == 3 and m.shape[0] == len(lights) and m.shape[1] == m.shape[2] and cm.shape == (len(lights), 16)
+    sh = Shadows(_dp(m), _dp(cm), m.shape[1], b0, b1)
+    if pixels is not None:
+        px = np.ascontiguousarray(pixels, dtype=np.int64)
+        n = px.size
+        pp = px.ctypes.data_as(C.POINTER(C.c_long))
+    else:
+        px, n, pp = None, cam.W * cam.H, None
+    out, lo, hi = np.zeros((n, 3)), np.zeros((n, 3)), np.zeros((n, 3))
+    assert lib().or_shade_shadows(_dp(gb), C.byref(cam), lp, len(lights), ib, aop, ao_scale, flags, C.byref(sh), pp,
+                                  n if px is not None else 0, _dp(out), _dp(lo), _dp(hi), threads) == 0
+    shp = (lambda a: a) if px is not None else (lambda a: a.reshape(cam.H, cam.W, 3))
+    return shp(out), shp(lo), shp(hi)
+
+
+def shadow_vis(maps, cams, b0: float, b1: float, light: int, P) -> np.ndarray:
+    """(vis, vis_lo, vis_hi) of world point P for one light (Sec. 5.1 readings in epbr_oracle.c)."""
+    m, cm = _f64(maps), _f64(cams)
+    sh = Shadows(_dp(m), _dp(cm), m.shape[1], b0, b1)
+    out = np.zeros(3)
+    lib().or_shadow_vis(C.byref(sh), light, _dp(_f64(P)), _dp(out))
+    return out
 
 
 def tonemap(hdr, exposure: float = 1.0, op: int = 0):

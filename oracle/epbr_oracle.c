@@ -17,6 +17,8 @@
  *     Bavoil & Sainz 2008);
  *   - ACES filmic tone mapping (Narkowicz 2015 fit) or Reinhard, then the sRGB transfer
  *     function of IEC 61966-2-1 (Sec. 5.4);
+ *   - shadow maps with 3x3 percentage-closer filtering for the point lights (Sec. 5.1;
+ *     Williams 1978, Reeves et al. 1987);
  *   - bloom (Sec. 5.3): bright map, an image pyramid of up to six levels, a Gaussian blur of
  *     every level from the second one up, the blurred levels added onto the image.
  * Conventions the paper leaves open (equirect mapping, sample sets, SSAO constants, rounding)
@@ -635,9 +637,84 @@ typedef struct {
   int flags;
   const long* pixels;
   double* out;
+  const struct or_shadows_s* sh; /* NULL: unshadowed */
+  double *out_lo, *out_hi;       /* with sh: bounds over tied shadow decisions (NULL allowed) */
 } shade_ctx;
 
-static void shade_pixel(const shade_ctx* c, long pix, double* out) {
+/* ------------------------------------------------------------------------------------------ */
+/* Shadow maps with 3x3 percentage-closer filtering (Sec. 5.1; Williams 1978, Reeves 1987)     */
+/* ------------------------------------------------------------------------------------------ */
+/* Readings: each light renders one perspective depth map "as if it were a normal camera": cams
+ * holds per light the world->light-view matrix (3 rows of 4; the light camera looks along -z)
+ * and f = 1/tan(fov/2), square maps of S x S eye depths (+inf = nothing).  A fragment at light
+ * depth z = -q.z > 0 projects to texel coordinates s = (q.x f / z + 1) S/2, t = (1 - q.y f / z) S/2
+ * (row 0 at the top, as the main camera) and texel (floor s, floor t).  A tap lights it when
+ * z <= d + b0 + b1 z; taps outside the map and fragments behind the light (z <= 0) are lit.
+ * Visibility = lit taps of the 3x3 block around the texel / 9; it multiplies the light's whole
+ * direct term.  Ties: a tap whose d is within OR_TIE_DEPTH * max(z, 1) of the threshold may go
+ * either way, and so may the block when s or t lies within OR_TIE_PX of a texel edge; vis_lo /
+ * vis_hi bound the visibility over those choices. */
+typedef struct or_shadows_s {
+  const double* maps; /* NL*S*S */
+  const double* cams; /* NL*16: rows 0..2 of the world->view matrix (12), f, 3 unused */
+  int S;
+  double b0, b1;
+} or_shadows;
+
+static int shadow_block_lit(const or_shadows* sh, const double* map, int bi, int bj, double z, int mode) {
+  /* mode 0: exact decisions; -1: ties count as shadowed; +1: ties count as lit */
+  double thr = z - sh->b0 - sh->b1 * z, tie = OR_TIE_DEPTH * (z > 1.0 ? z : 1.0);
+  int lit = 0;
+  for (int dy = -1; dy <= 1; ++dy)
+    for (int dx = -1; dx <= 1; ++dx) {
+      long i = bi + dx, j = bj + dy;
+      if (i < 0 || j < 0 || i >= sh->S || j >= sh->S) {
+        ++lit;
+        continue;
+      }
+      double d = map[j * sh->S + i];
+      if (mode == 0) lit += d >= thr;
+      else if (mode < 0) lit += d >= thr + tie;
+      else lit += d >= thr - tie;
+    }
+  return lit;
+}
+
+static void shadow_vis(const or_shadows* sh, int light, const double* P, double* vis, double* vlo, double* vhi) {
+  const double* V = sh->cams + 16 * (long)light;
+  double q[3];
+  for (int r = 0; r < 3; ++r) q[r] = V[4 * r] * P[0] + V[4 * r + 1] * P[1] + V[4 * r + 2] * P[2] + V[4 * r + 3];
+  double z = -q[2];
+  if (!(z > 0.0)) {
+    *vis = *vlo = *vhi = 1.0;
+    return;
+  }
+  double f = V[12], S = sh->S;
+  double sx = (q[0] * f / z + 1.0) * 0.5 * S, sy = (1.0 - q[1] * f / z) * 0.5 * S;
+  if (!(fabs(sx) < 1e9 && fabs(sy) < 1e9)) { /* far outside the frustum */
+    *vis = *vlo = *vhi = 1.0;
+    return;
+  }
+  double fx = floor(sx), fy = floor(sy);
+  const double* map = sh->maps + (long)light * sh->S * sh->S;
+  *vis = shadow_block_lit(sh, map, (int)fx, (int)fy, z, 0) / 9.0;
+  int cx[2] = {(int)fx, (int)fx}, cy[2] = {(int)fy, (int)fy};
+  if (sx - fx < OR_TIE_PX) cx[1] = (int)fx - 1;
+  if (sx - fx > 1.0 - OR_TIE_PX) cx[1] = (int)fx + 1;
+  if (sy - fy < OR_TIE_PX) cy[1] = (int)fy - 1;
+  if (sy - fy > 1.0 - OR_TIE_PX) cy[1] = (int)fy + 1;
+  int lo = 9, hi = 0;
+  for (int a = 0; a < 2; ++a)
+    for (int b = 0; b < 2; ++b) {
+      int l = shadow_block_lit(sh, map, cx[a], cy[b], z, -1), h = shadow_block_lit(sh, map, cx[a], cy[b], z, 1);
+      lo = l < lo ? l : lo;
+      hi = h > hi ? h : hi;
+    }
+  *vlo = lo / 9.0;
+  *vhi = hi / 9.0;
+}
+
+static void shade_pixel(const shade_ctx* c, long pix, double* out, double* lo, double* hi) {
   const or_camera* cam = c->cam;
   int x = (int)(pix % cam->W), y = (int)(pix / cam->W);
   const double* g = c->gb + pix * 9;
@@ -646,9 +723,11 @@ static void shade_pixel(const shade_ctx* c, long pix, double* out) {
   rot_apply(cam, r, dw);
   double e = g[8];
   out[0] = out[1] = out[2] = 0.0;
+  lo[0] = lo[1] = lo[2] = hi[0] = hi[1] = hi[2] = 0.0;
   if (!is_surface(e)) {
     /* A9: background shows the environment along the view ray. */
     if ((c->flags & OR_IBL) && c->ibl) equirect_lookup(c->ibl->level[0], c->ibl->Wl[0], c->ibl->Hl[0], dw, out);
+    for (int q = 0; q < 3; ++q) lo[q] = hi[q] = out[q];
     return;
   }
   double P[3], v[3], n[3] = {g[4], g[5], g[6]};
@@ -677,8 +756,15 @@ static void shade_pixel(const shade_ctx* c, long pix, double* out) {
       double nl = dot3(n, l);
       if (!(nl > 0.0)) continue;
       double rad[3] = {Lt[3] * Lt[4] / d2, Lt[3] * Lt[5] / d2, Lt[3] * Lt[6] / d2};
+      double vis = 1.0, vlo = 1.0, vhi = 1.0;
+      if (c->sh) shadow_vis(c->sh, i, P, &vis, &vlo, &vhi);
       if (diffuse_only) {
-        for (int q = 0; q < 3; ++q) out[q] += albedo[q] / OR_PI * rad[q] * nl;
+        for (int q = 0; q < 3; ++q) {
+          double t = albedo[q] / OR_PI * rad[q] * nl;
+          out[q] += vis * t;
+          lo[q] += vlo * t;
+          hi[q] += vhi * t;
+        }
         continue;
       }
       double h[3] = {l[0] + v[0], l[1] + v[1], l[2] + v[2]};
@@ -691,7 +777,10 @@ static void shade_pixel(const shade_ctx* c, long pix, double* out) {
         double F = F0[q] + (1.0 - F0[q]) * fc;
         double spec = D * G * F / (4.0 * nl * nv);
         double diff = (1.0 - F) * cdiff[q] / OR_PI;
-        out[q] += (diff + spec) * rad[q] * nl;
+        double t = (diff + spec) * rad[q] * nl;
+        out[q] += vis * t;
+        lo[q] += vlo * t;
+        hi[q] += vhi * t;
       }
     }
   }
@@ -706,7 +795,11 @@ static void shade_pixel(const shade_ctx* c, long pix, double* out) {
     double irr[3];
     equirect_lookup(ib->irr, ib->Wi, ib->Hi, n, irr);
     if (diffuse_only) {
-      for (int q = 0; q < 3; ++q) out[q] += albedo[q] * irr[q] * aoval;
+      for (int q = 0; q < 3; ++q) {
+        out[q] += albedo[q] * irr[q] * aoval;
+        lo[q] += albedo[q] * irr[q] * aoval;
+        hi[q] += albedo[q] * irr[q] * aoval;
+      }
       return;
     }
     double R[3];
@@ -739,6 +832,8 @@ static void shade_pixel(const shade_ctx* c, long pix, double* out) {
         La = (1.0 - kS) * cdiff[q] * irr[q] + (kS * A + B) * pref[q];
       }
       out[q] += La * aoval;
+      lo[q] += La * aoval;
+      hi[q] += La * aoval;
     }
   }
 }
@@ -747,7 +842,12 @@ static void shade_body(void* p, long i0, long i1) {
   shade_ctx* c = (shade_ctx*)p;
   for (long t = i0; t < i1; ++t) {
     long pix = c->pixels ? c->pixels[t] : t;
-    shade_pixel(c, pix, c->out + t * 3);
+    double lo[3], hi[3];
+    shade_pixel(c, pix, c->out + t * 3, lo, hi);
+    if (c->out_lo)
+      for (int q = 0; q < 3; ++q) c->out_lo[t * 3 + q] = lo[q];
+    if (c->out_hi)
+      for (int q = 0; q < 3; ++q) c->out_hi[t * 3 + q] = hi[q];
   }
 }
 
@@ -760,7 +860,23 @@ int or_shade(const double* gb, const or_camera* cam, const double* lights, int N
   if ((flags & OR_IBL) && !ibl) return 1;
   int s = ao_scale > 0 ? ao_scale : 1;
   shade_ctx c = {gb, cam, lights, NL, ibl, ao, (cam->W + s - 1) / s, (cam->H + s - 1) / s, s,
-                 flags, pixels, out};
+                 flags, pixels, out, NULL, NULL, NULL};
+  long cnt = pixels ? n : (long)cam->W * cam->H;
+  or_parallel_for(cnt, threads, shade_body, &c);
+  return 0;
+}
+
+/* or_shade with shadow maps (Sec. 5.1): each light's direct term times its PCF visibility;
+ * out_lo / out_hi (NULL allowed) receive the radiance with every tied shadow decision taken
+ * the darker / the brighter way. */
+int or_shade_shadows(const double* gb, const or_camera* cam, const double* lights, int NL,
+                     const or_ibl* ibl, const double* ao, int ao_scale, int flags, const or_shadows* sh,
+                     const long* pixels, long n, double* out, double* out_lo, double* out_hi, int threads) {
+  if (!gb || !cam || !out || !sh || (NL > 0 && !lights) || sh->S < 1 || !sh->maps || !sh->cams) return 1;
+  if ((flags & OR_IBL) && !ibl) return 1;
+  int s = ao_scale > 0 ? ao_scale : 1;
+  shade_ctx c = {gb, cam, lights, NL, ibl, ao, (cam->W + s - 1) / s, (cam->H + s - 1) / s, s,
+                 flags, pixels, out, sh, out_lo, out_hi};
   long cnt = pixels ? n : (long)cam->W * cam->H;
   or_parallel_for(cnt, threads, shade_body, &c);
   return 0;
@@ -932,4 +1048,9 @@ int or_bloom(const double* x, int W, int H, const or_bloom_params* bp, double* y
     }
   for (int k = 0; k < L; ++k) free(lev[k]);
   return 0;
+}
+
+/* Helper exposed for tests: visibility of world point P for one light -> (vis, vis_lo, vis_hi). */
+void or_shadow_vis(const or_shadows* sh, int light, const double* P, double* out) {
+  shadow_vis(sh, light, P, &out[0], &out[1], &out[2]);
 }

@@ -19,7 +19,7 @@ camera at (0, 0.6 F, 1.6 F) looking at the origin with a 60 degree vertical fiel
 from __future__ import annotations
 
 import math
-from dataclasses import dataclass, field
+from dataclasses import dataclass, field, replace
 
 import numpy as np
 
@@ -238,6 +238,33 @@ def raycast_gbuffer(scene: Scene, width: int | None = None, height: int | None =
     depth = best.astype(np.float32)
     depth[~lit] = np.inf
     return GBuffer(rt0, rt1, depth)
+
+
+def light_camera(light_pos, target=(0.0, 0.0, 0.0)) -> np.ndarray:
+    """view_to_world (4x4, float64) of a light's shadow camera at light_pos looking at target."""
+    fwd = np.asarray(target, np.float64) - np.asarray(light_pos, np.float64)
+    fwd /= np.linalg.norm(fwd)
+    up = (0.0, 0.0, -1.0) if abs(fwd[2]) < 0.9 else (1.0, 0.0, 0.0)
+    return camera_matrix(light_pos, target, up)
+
+
+def make_shadow_maps(scene: "Scene", size: int, fov_deg: float = 90.0, target=(0.0, 0.0, 0.0)):
+    """Per-light shadow maps of the analytic scene: each light's camera (light_camera) renders a
+    size x size map of eye depths (+inf = nothing) by the same float64 ray cast as the G-buffer.
+    Returns (maps (NL, size, size) float32, cams (NL, 16) float32): cams[i, :12] are the rows of the
+    world->light-view matrix, cams[i, 12] = 1 / tan(fov / 2)."""
+    nl = len(scene.lights)
+    maps = np.zeros((nl, size, size), np.float32)
+    cams = np.zeros((nl, 16), np.float32)
+    f = 1.0 / math.tan(math.radians(fov_deg) / 2)
+    for i in range(nl):
+        v2w = light_camera(scene.lights[i, :3].astype(np.float64), target)
+        sc = replace(scene, width=size, height=size, view_to_world=v2w, fov_y=math.radians(fov_deg))
+        maps[i] = raycast_gbuffer(sc).depth
+        w2v = np.linalg.inv(v2w)
+        cams[i, :12] = w2v[:3, :4].reshape(-1)
+        cams[i, 12] = f
+    return maps, cams
 
 
 def _srgb_encode8(x: np.ndarray) -> np.ndarray:
