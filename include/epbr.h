@@ -319,6 +319,34 @@ epbr_status epbr_shade_tonemap(const epbr_gbuffer* gbuffer, const epbr_camera* c
                                uint8_t* ldr, int64_t ldr_pitch, void* stream);
 
 /* ---------------------------------------------------------------------------------------- */
+/* Shadow maps with 3x3 percentage-closer filtering for the point lights (Sec. 5.1; Williams */
+/* 1978, Reeves et al. 1987)                                                                 */
+/* ---------------------------------------------------------------------------------------- */
+typedef struct epbr_shadows {
+  const float* maps;     /* DEVICE: one size x size map per light, map i at maps + i*size*size,
+                            row-major eye depths along the light camera's view axis, +inf where
+                            the map holds no surface; 4-byte aligned */
+  const float* cameras;  /* DEVICE float[num_lights * 16], 16-byte aligned: per light the rows of
+                            the world -> light-view matrix (12 floats; the light camera looks along
+                            -z, x right, y up), then f = 1 / tan(fov / 2), then 3 unused */
+  int32_t size;          /* S: map width and height, 1..8192 */
+  float bias_const;      /* b0 >= 0 */
+  float bias_slope;      /* b1 >= 0: a tap lights the fragment when z <= d + b0 + b1 z */
+} epbr_shadows;
+
+/* epbr_shade_tonemap with each light's direct term multiplied by its visibility: the fragment
+ * P maps to light-view q, depth z = -q.z, texel coordinates s = (q.x f / z + 1) S/2,
+ * t = (1 - q.y f / z) S/2, texel (floor s, floor t); visibility = lit taps of the 3x3 block
+ * around that texel / 9, a tap outside the map and a fragment behind the light (z <= 0) being
+ * lit.  The ambient term and background are unshadowed.  Outputs: `hdr` (NULL allowed) and
+ * `ldr` (NULL allowed, needs `tonemap`), at least one.  The maps are the caller's (render them
+ * once and reuse them while the scene and lights stay still, as Sec. 5.1 does). */
+epbr_status epbr_shade_shadows(const epbr_gbuffer* gbuffer, const epbr_camera* camera, const epbr_light* lights,
+                               int32_t num_lights, const epbr_ibl* ibl, const epbr_shade_params* params,
+                               const epbr_shadows* shadows, void* hdr, int32_t hdr_format, int64_t hdr_pitch,
+                               const epbr_tonemap_params* tonemap, uint8_t* ldr, int64_t ldr_pitch, void* stream);
+
+/* ---------------------------------------------------------------------------------------- */
 /* Bloom (Sec. 5.3: bright map, image pyramid of up to six levels blurred from the second one */
 /* upwards, added onto the image)                                                            */
 /* ---------------------------------------------------------------------------------------- */

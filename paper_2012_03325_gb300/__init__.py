@@ -284,6 +284,37 @@ def epbr_tonemap(hdr: torch.Tensor, hdr_format: int, tp: F.epbr_tonemap_params, 
 
 
 # ------------------------------------------------------------------------------------------
+# shadow maps with 3x3 PCF (Sec. 5.1)
+# ------------------------------------------------------------------------------------------
+class Shadows:
+    """Owns the shadow-map tensors and their epbr_shadows struct.  maps: (NL, S, S) float32 eye
+    depths; cameras: (NL, 16) float32 (world -> light-view rows, then f)."""
+
+    def __init__(self, maps: torch.Tensor, cameras: torch.Tensor, bias_const: float = 0.02,
+                 bias_slope: float = 0.01):
+        _dev(maps, torch.float32, "maps")
+        _dev(cameras, torch.float32, "cameras")
+        if maps.dim() != 3 or maps.shape[1] != maps.shape[2] or not maps.is_contiguous():
+            raise ValueError("maps must be a contiguous (NL, S, S) tensor")
+        if cameras.shape != (maps.shape[0], 16) or not cameras.is_contiguous():
+            raise ValueError("cameras must be a contiguous (NL, 16) tensor")
+        self.tensors = (maps, cameras)
+        self.struct = F.epbr_shadows(maps.data_ptr(), cameras.data_ptr(), maps.shape[1], bias_const, bias_slope)
+
+
+def epbr_shade_shadows(g: GBuffer, cam: F.epbr_camera, lights, ibl: Ibl | None, params: F.epbr_shade_params,
+                       shadows: Shadows, hdr: torch.Tensor | None, hdr_format: int,
+                       tp: F.epbr_tonemap_params | None = None, ldr: torch.Tensor | None = None, stream=None):
+    lp, nl = _lights(lights)
+    hp = _dev(hdr, name="hdr") if hdr is not None else None
+    dp = _dev(ldr, torch.uint8, "ldr") if ldr is not None else None
+    _check(lib().epbr_shade_shadows(C.byref(g.struct), C.byref(cam), lp, nl, C.byref(ibl.struct) if ibl else None,
+                                    C.byref(params), C.byref(shadows.struct), hp, hdr_format,
+                                    _pitch(hdr, 1) if hdr is not None else 0, C.byref(tp) if tp is not None else None,
+                                    dp, _pitch(ldr, 1) if ldr is not None else 0, _stream(stream)))
+
+
+# ------------------------------------------------------------------------------------------
 # bloom (Sec. 5.3)
 # ------------------------------------------------------------------------------------------
 def bloom_params(threshold: float = 1.0, strength: float = 1.0, sigma: float = 2.0, radius: int = 4,

@@ -114,7 +114,8 @@ static void launch_shade(dim3 grd, dim3 blk, cudaStream_t s, const GbufDev& g, c
 static epbr_status shade_common(const epbr_gbuffer* g, const epbr_camera* cam, const epbr_light* lights,
                                 int32_t NL, const epbr_ibl* ibl, const epbr_shade_params* sp, void* hdr,
                                 int32_t hdr_format, int64_t hdr_pitch, const epbr_tonemap_params* tp,
-                                uint8_t* ldr, int64_t ldr_pitch, void* stream) {
+                                uint8_t* ldr, int64_t ldr_pitch, void* stream, bool shadowed = false,
+                                const epbr_shadows* shadows = nullptr) {
   epbr_status st = validate_gbuffer(g, true);
   if (st) return st;
   if ((st = validate_camera(cam, g))) return st;
@@ -162,6 +163,12 @@ static epbr_status shade_common(const epbr_gbuffer* g, const epbr_camera* cam, c
   cudaStream_t s = (cudaStream_t)stream;
   const float4* L = (const float4*)lights;
   int nl = (sp->flags & EPBR_SHADE_DIRECT) ? NL : 0;
+  if (shadowed) {
+    if ((st = launch_shade_shadows(gd, cd, g->format, L, nl, ib, p, shadows, hdr, hdr_format, hdr_pitch, ldr, ldr_pitch,
+                                   s)))
+      return st;
+    return ok();
+  }
   if (g->format == EPBR_GBUFFER_FP32) {
     if (hdr_format == EPBR_HDR_RGBA32F)
       launch_shade<EPBR_GBUFFER_FP32, EPBR_HDR_RGBA32F>(grd, blk, s, gd, cd, L, nl, ib, p, hdr, hdr_pitch, ldr, ldr_pitch);
@@ -217,4 +224,13 @@ extern "C" epbr_status epbr_tonemap(const void* hdr, int32_t hdr_format, int32_t
     k_tonemap<EPBR_HDR_RGBA16F><<<grd, blk, 0, s>>>(hdr, hdr_pitch, W, H, tp->exposure, tp->op, out, out_pitch);
   epbr_status st = check_launch("k_tonemap");
   return st ? st : ok();
+}
+
+extern "C" epbr_status epbr_shade_shadows(const epbr_gbuffer* g, const epbr_camera* cam, const epbr_light* lights,
+                                          int32_t NL, const epbr_ibl* ibl, const epbr_shade_params* sp,
+                                          const epbr_shadows* shadows, void* hdr, int32_t hdr_format,
+                                          int64_t hdr_pitch, const epbr_tonemap_params* tp, uint8_t* ldr,
+                                          int64_t ldr_pitch, void* stream) {
+  return shade_common(g, cam, lights, NL, ibl, sp, hdr, hdr_format, hdr_pitch, tp, ldr, ldr_pitch, stream, true,
+                      shadows);
 }

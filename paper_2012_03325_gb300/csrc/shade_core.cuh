@@ -553,4 +553,10 @@ __device__ __forceinline__ float3 px_finish(Px& s, const IblDev& ibl, unsigned f
   return s.acc;
 }
 
+// Host: launches the shadowed compose (shadow.cu) after shade.cu has validated the common
+// arguments; validates `shadows`.
+epbr_status launch_shade_shadows(const GbufDev& g, const CamDev& c, int fmt, const float4* L, int NL,
+                                 const IblDev& ibl, const ShadeDev& p, const epbr_shadows* shadows, void* hdr,
+                                 int hdr_format, long long hp, uint8_t* ldr, long long lp, cudaStream_t st);
+
 }  // namespace epbr
