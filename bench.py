@@ -44,6 +44,8 @@ def parse():
     ap.add_argument("--serve-seconds", type=float, default=3.0, help="arrival window per rate (serve workload)")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="CPU-baseline time budget")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--shadows", action="store_true",
+                    help="shade with per-light shadow maps and 3x3 PCF (Sec. 5.1); maps stay resident")
     ap.add_argument("--bloom", action="store_true",
                     help="add the bloom pass (Sec. 5.3) to the frame: shade to HDR, then bloom + tone map")
     return ap.parse_args()
@@ -119,6 +121,9 @@ FLOP_IBL = 250           # split-sum ambient term with multiple scattering, time
 FLOP_DECODE = 60         # surface pixel: view ray, rotation, position, v and n normalised, F0, c_diff
 FLOP_BACKGROUND = 90     # background pixel: view ray, equirect mapping, bilinear read
 FLOP_TONEMAP = 36        # every pixel: exposure, ACES fit, clamp, sRGB transfer, rounding (x3)
+FLOP_SHADOW = 40         # lit pair with shadows: light-view transform (18), 1/z, texel coordinates (6),
+                         # threshold (2), nine depth compares, the visibility scale (3)
+SHADOW = {"size": 512, "fov_deg": 90.0, "bias_const": 0.02, "bias_slope": 0.01}
 
 
 def compose_flops(sc, g, n_lights) -> tuple[float, dict]:
@@ -255,7 +260,8 @@ def sources_sha(files=SHADE_SOURCES):
 # ------------------------------------------------------------------------------------------
 # CPU oracle baseline
 # ------------------------------------------------------------------------------------------
-def oracle_frame_rate(c, sc, g, env, k, nz, seconds: float, oracle_ibl=None, threads: int = 0, bloom=False):
+def oracle_frame_rate(c, sc, g, env, k, nz, seconds: float, oracle_ibl=None, threads: int = 0, bloom=False,
+                      shadow_maps=None):
     """The FP64 oracle's per-frame path (blurred SSAO, compose, tone map) on horizontal bands of
     the frame until `seconds` elapse; returns (Mpixels/s, cores, sample description).  With
     `bloom`, the oracle's bloom of one whole frame (it needs the whole image) is timed as well and
@@ -286,7 +292,13 @@ def oracle_frame_rate(c, sc, g, env, k, nz, seconds: float, oracle_ibl=None, thr
         ao_img = np.ones(((H + 1) // 2, (W + 1) // 2))
         ao_img.reshape(-1)[texels] = ao
         pixels = (ys[:, None] * W + np.arange(W)[None, :]).reshape(-1)
-        hdr = oracle.shade(gb, cam, sc.lights, oracle_ibl, 7, ao=ao_img, ao_scale=2, pixels=pixels, threads=threads)
+        if shadow_maps is not None:
+            hdr, _, _ = oracle.shade_shadows(gb, cam, sc.lights, oracle_ibl, 7, shadow_maps[0], shadow_maps[1],
+                                             SHADOW["bias_const"], SHADOW["bias_slope"], ao=ao_img, ao_scale=2,
+                                             pixels=pixels, threads=threads)
+        else:
+            hdr = oracle.shade(gb, cam, sc.lights, oracle_ibl, 7, ao=ao_img, ao_scale=2, pixels=pixels,
+                               threads=threads)
         oracle.tonemap(hdr)
         px_done += pixels.size
         y0 = (y0 + band) % H
@@ -392,12 +404,20 @@ def run_gpu(args):
     ws_bloom = torch.empty(ep.epbr_bloom_workspace_size(W, H, bp) + 256, dtype=torch.uint8, device=dev) \
         if args.bloom else None
 
+    shadows = None
+    if args.shadows:
+        maps, cams = synth.make_shadow_maps(sc, SHADOW["size"], SHADOW["fov_deg"])
+        shadows = ep.Shadows(t(maps), t(cams), SHADOW["bias_const"], SHADOW["bias_slope"])
+
     def compose(g_, shp_, hdr_, ldr_, lights_, record=False):
         """Compose (+ bloom): with bloom the compose writes HDR only and the bloom pass tone-maps."""
         if record:
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             a.record(stream)
-        if args.bloom:
+        if args.shadows:
+            ep.epbr_shade_shadows(g_, cam, lights_, ibl, shp_, shadows, hdr_, hdr_fmt, None if args.bloom else tp,
+                                  None if args.bloom else ldr_, stream=stream)
+        elif args.bloom:
             ep.epbr_shade(g_, cam, lights_, ibl, shp_, hdr_, hdr_fmt, stream=stream)
         else:
             ep.epbr_shade_tonemap(g_, cam, lights_, ibl, shp_, hdr_, hdr_fmt, tp, ldr_, stream=stream)
@@ -537,11 +557,15 @@ def run_gpu(args):
     props = torch.cuda.get_device_properties(dev)
     sms = props.multi_processor_count
     flops, counts = compose_flops(sc, g, c["lights"])
+    if args.shadows:
+        flops += counts["lit_pairs"] * FLOP_SHADOW
     clock_mhz = clocks["sm_mhz"] if clocks else 2070.0
     peak_tflops = sms * 128 * 2 * clock_mhz * 1e6 / 1e12
     achieved = flops / (shade_ms * 1e-3) / 1e12
-    traffic = kernel_traffic("k_shade", SHADE_SOURCES) if not compact else None
-    roofline = {"bound": "alu", "kernel": "k_shade (compose + fused tone map)", "achieved": achieved,
+    traffic = kernel_traffic("k_shade", SHADE_SOURCES) if not compact and not args.shadows else None
+    kname = "k_shade_shadow (compose with shadow maps + fused tone map)" if args.shadows else \
+        "k_shade (compose + fused tone map)"
+    roofline = {"bound": "alu", "kernel": kname, "achieved": achieved,
                 "peak": peak_tflops, "unit": "TFLOP/s", "frac": achieved / peak_tflops, "traffic": traffic,
                 "peak_basis": f"{sms} SMs x 128 FP32 lanes x 2 FLOP x {clock_mhz:.0f} MHz "
                               f"({'median SM clock sampled during the timed region' if clocks else 'max clock, no samples'})",
@@ -554,7 +578,10 @@ def run_gpu(args):
                                             "wall_s": wall,
                                             **({"step": "ssao_raw + ssao_blur + shade (HDR) + bloom with the tone map "
                                                         "fused per frame; lighting set precomputed once",
-                                                "bloom": BLOOM} if args.bloom else {})}),
+                                                "bloom": BLOOM} if args.bloom else {}),
+                                            **({"shadows": dict(SHADOW, maps="one per light, resident (static "
+                                                                "scene), generated by the ray caster")}
+                                               if args.shadows else {})}),
             "roofline": roofline,
             "e2e": {"value": e2e_value, "unit": "Mpixels/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                     "how": "pinned host G-buffer + lights uploaded and RGBA8 downloaded every step; frames "
@@ -574,7 +601,8 @@ def run_gpu(args):
                          "frac": bloom_bytes / (bloom_ms * 1e-3) / 1e9 / HBM_PEAK_GBS}
     if not args.no_cpu_baseline and world == 1:
         rate, cores, sample = oracle_frame_rate(dict(c, name=name), sc, g, env, k, nz, args.cpu_seconds,
-                                                bloom=args.bloom)
+                                                bloom=args.bloom,
+                                                shadow_maps=(maps, cams) if args.shadows else None)
         line["cpu_baseline"] = {"value": rate, "unit": "Mpixels/s", "cores": cores, "kind": "oracle",
                                 "sample": sample}
     print(json.dumps(line), flush=True)
