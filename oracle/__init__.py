@@ -55,6 +55,10 @@ class Shadows(C.Structure):
                 ("b0", C.c_double), ("b1", C.c_double)]
 
 
+class EdlParams(C.Structure):
+    _fields_ = [("strength", C.c_double), ("radius", C.c_int), ("directions", C.c_int)]
+
+
 class Ibl(C.Structure):
     _fields_ = [("irr", C.POINTER(C.c_double)), ("Wi", C.c_int), ("Hi", C.c_int), ("M", C.c_int),
                 ("level", C.POINTER(C.c_double) * MAX_LEVELS), ("Wl", C.c_int * MAX_LEVELS),
@@ -98,6 +102,7 @@ def lib():
                                            C.c_int, C.POINTER(Shadows), lp, C.c_long, dp, dp, dp, C.c_int]
             L.or_shadow_vis.argtypes = [C.POINTER(Shadows), C.c_int, dp, dp]
             L.or_shadow_vis.restype = None
+            L.or_edl.argtypes = [dp, C.c_int, C.c_int, C.POINTER(EdlParams), dp, C.c_int, dp]
             L.or_bloom.argtypes = [dp, C.c_int, C.c_int, C.POINTER(BloomParams), dp, dp, dp]
             _lib = L
     return _lib
@@ -309,6 +314,17 @@ def shadow_vis(maps, cams, b0: float, b1: float, light: int, P) -> np.ndarray:
     sh = Shadows(_dp(m), _dp(cm), m.shape[1], b0, b1)
     out = np.zeros(3)
     lib().or_shadow_vis(C.byref(sh), light, _dp(_f64(P)), _dp(out))
+    return out
+
+
+def edl(gb, strength: float = 8.0, radius: int = 1, directions: int = 8, ao=None, ao_scale: int = 1) -> np.ndarray:
+    """Eye-dome lighting of a decoded (H, W, 9) G-buffer (Sec. 4.2; readings in epbr_oracle.c) -> (H, W, 3)."""
+    g = _f64(gb)
+    H, W = g.shape[:2]
+    out = np.zeros((H, W, 3))
+    keep = _Keep()
+    aop = keep.ptr(ao) if ao is not None else None
+    assert lib().or_edl(_dp(g), W, H, C.byref(EdlParams(strength, radius, directions)), aop, ao_scale, _dp(out)) == 0
     return out
 
 

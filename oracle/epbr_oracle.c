@@ -19,6 +19,7 @@
  *     function of IEC 61966-2-1 (Sec. 5.4);
  *   - shadow maps with 3x3 percentage-closer filtering for the point lights (Sec. 5.1;
  *     Williams 1978, Reeves et al. 1987);
+ *   - eye-dome lighting for point clouds (Sec. 4.2; Boucheny 2009);
  *   - bloom (Sec. 5.3): bright map, an image pyramid of up to six levels, a Gaussian blur of
  *     every level from the second one up, the blurred levels added onto the image.
  * Conventions the paper leaves open (equirect mapping, sample sets, SSAO constants, rounding)
@@ -1053,4 +1054,57 @@ int or_bloom(const double* x, int W, int H, const or_bloom_params* bp, double* y
 /* Helper exposed for tests: visibility of world point P for one light -> (vis, vis_lo, vis_hi). */
 void or_shadow_vis(const or_shadows* sh, int light, const double* P, double* out) {
   shadow_vis(sh, light, P, &out[0], &out[1], &out[2]);
+}
+
+/* ------------------------------------------------------------------------------------------ */
+/* Eye-dome lighting for point clouds (Sec. 4.2; Boucheny 2009)                                */
+/* ------------------------------------------------------------------------------------------ */
+/* Readings: the paper darkens a pixel the more its depth exceeds its screen neighbours'.
+ *   obscurance  w(p) = (1/N) sum_k max(0, log2 e_p - log2 e_{q_k}), q_k = p + (round(r cos t_k),
+ *               round(r sin t_k)), t_k = 2 pi k / N (round half away from zero, in FP64);
+ *               a neighbour outside the image or without a surface counts as infinitely far
+ *               (contributes 0)
+ *   shade       s(p) = exp(-A w(p)) (A: strength); output = G-buffer colour * s * AO (AO
+ *               optional, nearest at (x / ao_scale, y / ao_scale)); background pixels 0. */
+typedef struct {
+  double strength;
+  int radius, directions;
+} or_edl_params;
+
+static double edl_log_depth(const double* gb, int W, int H, int x, int y) {
+  if (x < 0 || y < 0 || x >= W || y >= H) return INFINITY;
+  double e = gb[((long)y * W + x) * 9 + 8];
+  return is_surface(e) ? log2(e) : INFINITY;
+}
+
+/* gb: W*H*9 decoded G-buffer (albedo 0..2, depth 8); out: W*H*3. */
+int or_edl(const double* gb, int W, int H, const or_edl_params* ep, const double* ao, int ao_scale, double* out) {
+  if (W < 1 || H < 1 || ep->radius < 1 || ep->directions < 1 || ep->directions > 64) return -1;
+  int N = ep->directions, dx[64], dy[64];
+  for (int k = 0; k < N; ++k) {
+    double t = 2.0 * OR_PI * k / N;
+    dx[k] = (int)round(ep->radius * cos(t));
+    dy[k] = (int)round(ep->radius * sin(t));
+  }
+  int s = ao_scale > 0 ? ao_scale : 1, Wa = (W + s - 1) / s;
+  for (int y = 0; y < H; ++y)
+    for (int x = 0; x < W; ++x) {
+      long p = (long)y * W + x;
+      double lp = edl_log_depth(gb, W, H, x, y);
+      if (isinf(lp)) {
+        out[3 * p] = out[3 * p + 1] = out[3 * p + 2] = 0.0;
+        continue;
+      }
+      double w = 0.0;
+      for (int k = 0; k < N; ++k) {
+        double lq = edl_log_depth(gb, W, H, x + dx[k], y + dy[k]);
+        double d = lp - lq;
+        w += d > 0.0 ? d : 0.0;
+      }
+      w /= N;
+      double sh = exp(-ep->strength * w);
+      if (ao) sh *= ao[(long)(y / s) * Wa + x / s];
+      for (int c = 0; c < 3; ++c) out[3 * p + c] = gb[p * 9 + c] * sh;
+    }
+  return 0;
 }
