@@ -319,6 +319,26 @@ epbr_status epbr_shade_tonemap(const epbr_gbuffer* gbuffer, const epbr_camera* c
                                uint8_t* ldr, int64_t ldr_pitch, void* stream);
 
 /* ---------------------------------------------------------------------------------------- */
+/* Eye-dome lighting for point clouds (Sec. 4.2; Boucheny 2009): shading from depth alone    */
+/* ---------------------------------------------------------------------------------------- */
+typedef struct epbr_edl_params {
+  float strength;      /* A >= 0 */
+  int32_t radius;      /* r: neighbour distance in pixels, 1..8 */
+  int32_t directions;  /* N: neighbours at angles 2 pi k / N, 1..16 */
+} epbr_edl_params;
+
+/* Per pixel p with a surface: w = (1/N) sum_k max(0, log2 e_p - log2 e_{q_k}), q_k = p +
+ * (round(r cos(2 pi k/N)), round(r sin(2 pi k/N))) (round half away from zero), a neighbour
+ * outside the image or without a surface counting as infinitely far; output = G-buffer colour
+ * (rt[0]: FP32 rgb, or sRGB8 in the compact layout) * exp(-A w) * AO; background pixels 0,
+ * alpha 1.  The G-buffer needs rt[0] and the depth rt[3] only (a point cloud has no normals).
+ * `ao` DEVICE or NULL (read at (x/ao_scale, y/ao_scale), ao_scale 1..8).  Outputs `hdr` (NULL
+ * allowed) and `ldr` (NULL allowed, needs `tonemap`), at least one. */
+epbr_status epbr_edl(const epbr_gbuffer* gbuffer, const epbr_edl_params* params, const float* ao, int64_t ao_pitch,
+                     int32_t ao_scale, void* hdr, int32_t hdr_format, int64_t hdr_pitch,
+                     const epbr_tonemap_params* tonemap, uint8_t* ldr, int64_t ldr_pitch, void* stream);
+
+/* ---------------------------------------------------------------------------------------- */
 /* Shadow maps with 3x3 percentage-closer filtering for the point lights (Sec. 5.1; Williams */
 /* 1978, Reeves et al. 1987)                                                                 */
 /* ---------------------------------------------------------------------------------------- */

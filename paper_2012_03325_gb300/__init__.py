@@ -284,6 +284,25 @@ def epbr_tonemap(hdr: torch.Tensor, hdr_format: int, tp: F.epbr_tonemap_params, 
 
 
 # ------------------------------------------------------------------------------------------
+# eye-dome lighting for point clouds (Sec. 4.2)
+# ------------------------------------------------------------------------------------------
+def edl_params(strength: float = 8.0, radius: int = 1, directions: int = 8) -> F.epbr_edl_params:
+    return F.epbr_edl_params(strength, radius, directions)
+
+
+def epbr_edl(g: GBuffer, params: F.epbr_edl_params, hdr: torch.Tensor | None, hdr_format: int = EPBR_HDR_RGBA32F,
+             ao: torch.Tensor | None = None, ao_scale: int = 2, tp: F.epbr_tonemap_params | None = None,
+             ldr: torch.Tensor | None = None, stream=None):
+    ap = _dev(ao, torch.float32, "ao") if ao is not None else None
+    hp = _dev(hdr, name="hdr") if hdr is not None else None
+    dp = _dev(ldr, torch.uint8, "ldr") if ldr is not None else None
+    _check(lib().epbr_edl(C.byref(g.struct), C.byref(params), ap, _pitch(ao, 1) if ao is not None else 0, ao_scale,
+                          hp, hdr_format, _pitch(hdr, 1) if hdr is not None else 0,
+                          C.byref(tp) if tp is not None else None, dp, _pitch(ldr, 1) if ldr is not None else 0,
+                          _stream(stream)))
+
+
+# ------------------------------------------------------------------------------------------
 # shadow maps with 3x3 PCF (Sec. 5.1)
 # ------------------------------------------------------------------------------------------
 class Shadows:

@@ -83,6 +83,10 @@ class epbr_tonemap_params(C.Structure):
     _fields_ = [("exposure", C.c_float), ("op", C.c_int32)]
 
 
+class epbr_edl_params(C.Structure):
+    _fields_ = [("strength", C.c_float), ("radius", C.c_int32), ("directions", C.c_int32)]
+
+
 class epbr_shadows(C.Structure):
     _fields_ = [("maps", C.c_void_p), ("cameras", C.c_void_p), ("size", C.c_int32), ("bias_const", C.c_float),
                 ("bias_slope", C.c_float)]
@@ -151,6 +155,8 @@ PROTOTYPES = {
     "epbr_shade_tonemap": [P(epbr_gbuffer), P(epbr_camera), vp, i32, P(epbr_ibl), P(epbr_shade_params), vp,
                            i32, i64, P(epbr_tonemap_params), vp, i64, vp],
     "epbr_tonemap": [vp, i32, i32, i32, i64, P(epbr_tonemap_params), vp, i64, vp],
+    "epbr_edl": [P(epbr_gbuffer), P(epbr_edl_params), vp, i64, i32, vp, i32, i64, P(epbr_tonemap_params), vp, i64,
+                 vp],
     "epbr_shade_shadows": [P(epbr_gbuffer), P(epbr_camera), vp, i32, P(epbr_ibl), P(epbr_shade_params),
                            P(epbr_shadows), vp, i32, i64, P(epbr_tonemap_params), vp, i64, vp],
     "epbr_bloom_workspace_size": [i32, i32, P(epbr_bloom_params), P(sz)],

@@ -388,6 +388,26 @@ def make_hdr_field(seed: int, width: int, height: int) -> np.ndarray:
     return x.astype(np.float32)
 
 
+def make_point_cloud_gbuffer(seed: int, width: int, height: int, fill: float = 0.7) -> GBuffer:
+    """Synthetic point-cloud G-buffer for eye-dome lighting: colour and depth only (normals 0):
+    several depth layers (rough surfaces at depths 2..40 with per-pixel jitter) covering `fill` of
+    the image in splats, the rest background (+inf), so depth jumps between points and layers."""
+    g = np.random.Generator(np.random.PCG64(seed))
+    yy, xx = np.mgrid[0:height, 0:width].astype(np.float64)
+    depth = np.full((height, width), np.inf)
+    colour = np.zeros((height, width, 3))
+    for layer in range(4):
+        base = g.uniform(2, 40)
+        surf = base * (1 + 0.1 * np.sin(xx / g.uniform(5, 30)) * np.cos(yy / g.uniform(5, 30)))
+        surf *= 1 + 0.02 * g.uniform(-1, 1, (height, width))
+        keep = (g.uniform(size=(height, width)) < fill / 2) & (surf < depth)
+        depth[keep] = surf[keep]
+        colour[keep] = g.uniform(0.05, 1.0, 3) * g.uniform(0.7, 1.0, (int(keep.sum()), 1))
+    rt0 = np.concatenate([colour, np.zeros((height, width, 1))], axis=2).astype(np.float32)
+    rt1 = np.zeros((height, width, 4), np.float32)
+    return GBuffer(rt0, rt1, depth.astype(np.float32))
+
+
 def make_bloom_field(seed: int, width: int, height: int, n_spots: int = 12) -> np.ndarray:
     """Synthetic HDR RGBA32F frame for the bloom tests: a smooth gradient in [0, 0.8] (below a
     threshold of 1) with `n_spots` bright discs (radius 1..24 px, values 2..60) and a few isolated
