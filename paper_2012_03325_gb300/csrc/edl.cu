@@ -1,5 +1,5 @@
 // Eye-dome lighting for point clouds (Sec. 4.2; Boucheny 2009): shading from the depth map alone.
-//   k_edl  32x8 pixels per block; the block's log2 depths plus an r-pixel halo are staged in
+//   k_edl  32x16 pixels per block (two rows per thread); the block's log2 depths plus an r-pixel halo are staged in
 //          shared memory (one logarithm per texel; +inf for background and off-image texels, so
 //          their max(0, .) terms vanish), then each pixel sums its N neighbours' log-depth drops,
 //          shades its colour by exp(-A w), optionally times AO, and stores HDR and / or the
@@ -12,7 +12,7 @@
 
 namespace epbr {
 
-constexpr int kEdlBX = 32, kEdlBY = 8, kEdlMaxR = 8, kEdlMaxN = 16;
+constexpr int kEdlBX = 32, kEdlBY = 8, kEdlTileH = 2 * kEdlBY, kEdlMaxR = 8, kEdlMaxN = 16;
 
 struct EdlDev {
   float minus_a_log2e;  // -A / ln 2: exp(-A w) = 2^(minus_a_log2e w)
@@ -31,17 +31,18 @@ __device__ __forceinline__ float3 edl_colour(const GbufDev& g, int x, int y) {
   return f3(c_srgb8[a & 255u], c_srgb8[(a >> 8) & 255u], c_srgb8[(a >> 16) & 255u]);
 }
 
-template <int FMT, int HDR, bool LDR>
+template <int FMT, int HDR, bool LDR, int NT>
 __global__ void __launch_bounds__(kEdlBX* kEdlBY)
     k_edl(GbufDev g, EdlDev p, void* hdr, long long hdr_pitch, float exposure, int op, uint8_t* ldr,
           long long ldr_pitch) {
-  constexpr int TW = kEdlBX + 2 * kEdlMaxR, TH = kEdlBY + 2 * kEdlMaxR;
+  constexpr int TW = kEdlBX + 2 * kEdlMaxR, TH = kEdlTileH + 2 * kEdlMaxR;
   __shared__ float s_l[TH * TW];
   __shared__ int s_off[kEdlMaxN];  // neighbour k as an offset into the flat tile
-  const int R = p.R, tw = kEdlBX + 2 * R, th = kEdlBY + 2 * R;
+  const int R = p.R, tw = kEdlBX + 2 * R, th = kEdlTileH + 2 * R;
+  const int N = NT > 0 ? NT : p.N;  // NT > 0: the direction count fixed at compile time
   {
     const int tid = threadIdx.y * kEdlBX + threadIdx.x;
-    if (tid < p.N) {
+    if (tid < N) {
       int dx = 0, dy = 0;
 #pragma unroll
       for (int k = 0; k < kEdlMaxN; ++k)
@@ -49,7 +50,7 @@ __global__ void __launch_bounds__(kEdlBX* kEdlBY)
       s_off[tid] = dy * TW + dx;
     }
   }
-  const int x0 = blockIdx.x * kEdlBX, y0 = blockIdx.y * kEdlBY;
+  const int x0 = blockIdx.x * kEdlBX, y0 = blockIdx.y * kEdlTileH;
   const float inf = __int_as_float(0x7f800000);
   for (int ty = threadIdx.y; ty < th; ty += kEdlBY)
     for (int tx = threadIdx.x; tx < tw; tx += kEdlBX) {
@@ -62,31 +63,53 @@ __global__ void __launch_bounds__(kEdlBX* kEdlBY)
       s_l[ty * TW + tx] = l;
     }
   __syncthreads();
-  const int x = x0 + threadIdx.x, y = y0 + threadIdx.y;
-  if (x >= g.W || y >= g.H) return;
-  const int centre = (threadIdx.y + R) * TW + threadIdx.x + R;
-  const float lp = s_l[centre];
-  float3 c = f3(0, 0, 0);
-  if (lp != inf) {
-    float w = 0.0f;
-    for (int k = 0; k < p.N; ++k) w += fmaxf(lp - s_l[centre + s_off[k]], 0.0f);
-    float shade = ex2_ftz(p.minus_a_log2e * (w * p.inv_n));
-    if (p.ao)
-      shade *= __ldg((const float*)((const char*)p.ao + (size_t)__float2int_rd(((float)y + 0.5f) * p.ao_inv) * p.ao_pitch) +
-                     __float2int_rd(((float)x + 0.5f) * p.ao_inv));
-    c = edl_colour<FMT>(g, x, y) * shade;
+  int off[NT > 0 ? NT : 1];
+  if (NT > 0) {
+#pragma unroll
+    for (int k = 0; k < (NT > 0 ? NT : 1); ++k) off[k] = s_off[k];
   }
-  if (hdr) store_hdr<HDR>(hdr, hdr_pitch, x, y, c);
-  if (LDR) ((unsigned*)(ldr + (size_t)y * ldr_pitch))[x] = pack_rgba8(c, exposure, op);
+  const int x = x0 + threadIdx.x;
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const int ly = threadIdx.y + h * kEdlBY, y = y0 + ly;
+    if (x >= g.W || y >= g.H) continue;
+    const int centre = (ly + R) * TW + threadIdx.x + R;
+    const float lp = s_l[centre];
+    float3 c = f3(0, 0, 0);
+    if (lp != inf) {
+      float w = 0.0f;
+      if (NT > 0) {
+#pragma unroll
+        for (int k = 0; k < (NT > 0 ? NT : 1); ++k) w += fmaxf(lp - s_l[centre + off[k]], 0.0f);
+      } else {
+        for (int k = 0; k < N; ++k) w += fmaxf(lp - s_l[centre + s_off[k]], 0.0f);
+      }
+      float shade = ex2_ftz(p.minus_a_log2e * (w * p.inv_n));
+      if (p.ao)
+        shade *= __ldg((const float*)((const char*)p.ao + (size_t)__float2int_rd(((float)y + 0.5f) * p.ao_inv) *
+                                                              p.ao_pitch) +
+                       __float2int_rd(((float)x + 0.5f) * p.ao_inv));
+      c = edl_colour<FMT>(g, x, y) * shade;
+    }
+    if (hdr) store_hdr<HDR>(hdr, hdr_pitch, x, y, c);
+    if (LDR) ((unsigned*)(ldr + (size_t)y * ldr_pitch))[x] = pack_rgba8(c, exposure, op);
+  }
 }
 
 template <int FMT, int HDR>
 static void launch_edl(dim3 grd, dim3 blk, cudaStream_t s, const GbufDev& g, const EdlDev& p, void* hdr,
                        long long hp, float exposure, int op, uint8_t* ldr, long long lp) {
-  if (ldr)
-    k_edl<FMT, HDR, true><<<grd, blk, 0, s>>>(g, p, hdr, hp, exposure, op, ldr, lp);
-  else
-    k_edl<FMT, HDR, false><<<grd, blk, 0, s>>>(g, p, hdr, hp, exposure, op, ldr, lp);
+  if (p.N == 8) {  // the usual eight directions: neighbour loop unrolled
+    if (ldr)
+      k_edl<FMT, HDR, true, 8><<<grd, blk, 0, s>>>(g, p, hdr, hp, exposure, op, ldr, lp);
+    else
+      k_edl<FMT, HDR, false, 8><<<grd, blk, 0, s>>>(g, p, hdr, hp, exposure, op, ldr, lp);
+  } else {
+    if (ldr)
+      k_edl<FMT, HDR, true, 0><<<grd, blk, 0, s>>>(g, p, hdr, hp, exposure, op, ldr, lp);
+    else
+      k_edl<FMT, HDR, false, 0><<<grd, blk, 0, s>>>(g, p, hdr, hp, exposure, op, ldr, lp);
+  }
 }
 
 }  // namespace epbr
@@ -141,7 +164,7 @@ extern "C" epbr_status epbr_edl(const epbr_gbuffer* g, const epbr_edl_params* pa
     p.dy[k] = (signed char)std::lround(params->radius * std::sin(t));
   }
   GbufDev gd = make_gbuf(*g);
-  dim3 blk(kEdlBX, kEdlBY), grd((g->width + kEdlBX - 1) / kEdlBX, (g->height + kEdlBY - 1) / kEdlBY);
+  dim3 blk(kEdlBX, kEdlBY), grd((g->width + kEdlBX - 1) / kEdlBX, (g->height + kEdlTileH - 1) / kEdlTileH);
   cudaStream_t s = (cudaStream_t)stream;
   float exposure = tp ? tp->exposure : 1.0f;
   int op = tp ? tp->op : 0;
