@@ -102,6 +102,7 @@ def lib():
                                            C.c_int, C.POINTER(Shadows), lp, C.c_long, dp, dp, dp, C.c_int]
             L.or_shadow_vis.argtypes = [C.POINTER(Shadows), C.c_int, dp, dp]
             L.or_shadow_vis.restype = None
+            L.or_raster.argtypes = [dp, C.c_int, ip, C.c_long, C.POINTER(Camera), C.c_double, dp, ip]
             L.or_edl.argtypes = [dp, C.c_int, C.c_int, C.POINTER(EdlParams), dp, C.c_int, dp]
             L.or_bloom.argtypes = [dp, C.c_int, C.c_int, C.POINTER(BloomParams), dp, dp, dp]
             _lib = L
@@ -326,6 +327,19 @@ def edl(gb, strength: float = 8.0, radius: int = 1, directions: int = 8, ao=None
     aop = keep.ptr(ao) if ao is not None else None
     assert lib().or_edl(_dp(g), W, H, C.byref(EdlParams(strength, radius, directions)), aop, ao_scale, _dp(out)) == 0
     return out
+
+
+def raster(verts, tris, cam: Camera, near: float = 0.05):
+    """G-buffer pass of mesh rendering (Sec. 4.1; readings in epbr_oracle.c).  verts: (V, 12)
+    position, normal, albedo, metal, rough, unused (FP32-representable); tris: (T, 3) int.
+    Returns (gb (H, W, 9) decoded G-buffer, ids (H, W) triangle index or -1)."""
+    v = _f64(verts).reshape(-1, 12)
+    t = np.ascontiguousarray(tris, dtype=np.int32).reshape(-1, 3)
+    gb = np.zeros((cam.H, cam.W, 9))
+    ids = np.zeros((cam.H, cam.W), np.int32)
+    assert lib().or_raster(_dp(v), v.shape[0], t.ctypes.data_as(C.POINTER(C.c_int)), t.shape[0], C.byref(cam), near,
+                           _dp(gb), ids.ctypes.data_as(C.POINTER(C.c_int))) == 0
+    return gb, ids
 
 
 def tonemap(hdr, exposure: float = 1.0, op: int = 0):

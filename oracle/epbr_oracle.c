@@ -20,6 +20,8 @@
  *   - shadow maps with 3x3 percentage-closer filtering for the point lights (Sec. 5.1;
  *     Williams 1978, Reeves et al. 1987);
  *   - eye-dome lighting for point clouds (Sec. 4.2; Boucheny 2009);
+ *   - the G-buffer pass of mesh rendering (Sec. 4.1): triangle rasterisation with a depth test
+ *     and perspective-correct attribute interpolation;
  *   - bloom (Sec. 5.3): bright map, an image pyramid of up to six levels, a Gaussian blur of
  *     every level from the second one up, the blurred levels added onto the image.
  * Conventions the paper leaves open (equirect mapping, sample sets, SSAO constants, rounding)
@@ -1106,5 +1108,166 @@ int or_edl(const double* gb, int W, int H, const or_edl_params* ep, const double
       if (ao) sh *= ao[(long)(y / s) * Wa + x / s];
       for (int c = 0; c < 3; ++c) out[3 * p + c] = gb[p * 9 + c] * sh;
     }
+  return 0;
+}
+
+/* ------------------------------------------------------------------------------------------ */
+/* Mesh rendering into the G-buffer (Sec. 4.1)                                                 */
+/* ------------------------------------------------------------------------------------------ */
+/* Readings (the paper rasterises with OpenGL): pixel (x, y) is covered by a triangle when its
+ * centre lies inside it; the nearest covering triangle (smallest eye depth, then smallest index)
+ * writes the pixel; attributes are interpolated perspective-correctly (affine in 1/z).  Which
+ * triangle covers a pixel is decided exactly: vertices go to view space and the screen in FP32
+ * with every product, sum and quotient rounded (the CUDA path evaluates the same expressions),
+ * are snapped to 1/256 pixel (round half to even), and coverage uses 64-bit integer edge
+ * functions with a top-left rule on shared edges; the depth of the test is the FP32 value
+ * A / ((b0 iz0 + b1 iz1) + b2 iz2) (b_i the integer edge functions, A their sum, iz_i = 1/z_i).
+ * No clipping: a triangle with a vertex at eye depth below `near`, or projecting beyond 2^22
+ * pixels, is not drawn; no back-face culling.  Vertices: 12 values each, position xyz, normal
+ * xyz, albedo rgb, metal, rough, unused.  Attributes are interpolated in FP64 with the weights
+ * b_i iz_i / sum_j b_j iz_j; the normal is normalised. */
+typedef struct {
+  float ax, ay, az;   /* view-space position */
+  long long qx, qy;   /* snapped screen position, 1/256 px */
+  float iz;           /* 1 / eye depth */
+  int ok;
+} or_rvert;
+
+static or_rvert raster_vertex(const double* v, const or_camera* cam, float kx, float ky, float hw, float hh, float near) {
+  /* view = R^T (p - eye), R's columns are the view axes in world space */
+  float px = (float)v[0], py = (float)v[1], pz = (float)v[2];
+  float ex = (float)cam->v2w[12], ey = (float)cam->v2w[13], ez = (float)cam->v2w[14];
+  float dx = px - ex, dy = py - ey, dz = pz - ez;
+  float r[9];
+  for (int c = 0; c < 3; ++c)
+    for (int i = 0; i < 3; ++i) r[3 * c + i] = (float)cam->v2w[4 * c + i]; /* column c, row i */
+  or_rvert o;
+  float t0, t1;
+  t0 = r[0] * dx; t1 = r[1] * dy; o.ax = (t0 + t1); t0 = r[2] * dz; o.ax = o.ax + t0;
+  t0 = r[3] * dx; t1 = r[4] * dy; o.ay = (t0 + t1); t0 = r[5] * dz; o.ay = o.ay + t0;
+  t0 = r[6] * dx; t1 = r[7] * dy; o.az = (t0 + t1); t0 = r[8] * dz; o.az = o.az + t0;
+  float e = -o.az;
+  o.ok = e >= near;
+  o.iz = 1.0f / e;
+  float u = o.ax * o.iz, w = o.ay * o.iz;
+  float X = hw * (1.0f + u * kx), Y = hh * (1.0f - w * ky);
+  o.ok = o.ok && fabsf(X) < 4194304.0f && fabsf(Y) < 4194304.0f;
+  o.qx = o.ok ? (long long)lrintf(X * 256.0f) : 0;
+  o.qy = o.ok ? (long long)lrintf(Y * 256.0f) : 0;
+  return o;
+}
+
+static long long edge_fn(long long ax, long long ay, long long bx, long long by, long long px, long long py) {
+  return (bx - ax) * (py - ay) - (by - ay) * (px - ax);
+}
+
+/* top-left rule for edge a -> b of a triangle with positive area in this orientation */
+static int edge_bias(long long ax, long long ay, long long bx, long long by) {
+  long long dx = bx - ax, dy = by - ay;
+  return (dy < 0 || (dy == 0 && dx > 0)) ? 0 : -1;
+}
+
+/* verts: V*12, tris: T*3.  gb: W*H*9 (albedo 0..2, metal 3, normal 4..6, rough 7, depth 8;
+ * background: zeros and depth +inf); ids: W*H triangle index or -1 (NULL allowed). */
+int or_raster(const double* verts, int V, const int* tris, long T, const or_camera* cam, double near, double* gb,
+              int* ids) {
+  int W = cam->W, H = cam->H;
+  double t = tan(0.5 * cam->fov_y);
+  float ky = (float)(1.0 / t), kx = (float)((double)H / ((double)W * t));
+  float hw = (float)(0.5 * W), hh = (float)(0.5 * H), nearf = (float)near;
+  unsigned long long* best = (unsigned long long*)malloc(sizeof(unsigned long long) * (size_t)W * H);
+  for (long p = 0; p < (long)W * H; ++p) best[p] = ~0ULL;
+  for (long tr = 0; tr < T; ++tr) {
+    int i0 = tris[3 * tr], i1 = tris[3 * tr + 1], i2 = tris[3 * tr + 2];
+    if (i0 < 0 || i1 < 0 || i2 < 0 || i0 >= V || i1 >= V || i2 >= V) continue;
+    or_rvert a = raster_vertex(verts + 12 * (long)i0, cam, kx, ky, hw, hh, nearf);
+    or_rvert b = raster_vertex(verts + 12 * (long)i1, cam, kx, ky, hw, hh, nearf);
+    or_rvert c = raster_vertex(verts + 12 * (long)i2, cam, kx, ky, hw, hh, nearf);
+    if (!a.ok || !b.ok || !c.ok) continue;
+    long long area = edge_fn(a.qx, a.qy, b.qx, b.qy, c.qx, c.qy);
+    if (area == 0) continue;
+    if (area < 0) { /* orient so that the area is positive */
+      or_rvert tmp = b;
+      b = c;
+      c = tmp;
+      area = -area;
+    }
+    long long xmin = a.qx < b.qx ? (a.qx < c.qx ? a.qx : c.qx) : (b.qx < c.qx ? b.qx : c.qx);
+    long long xmax = a.qx > b.qx ? (a.qx > c.qx ? a.qx : c.qx) : (b.qx > c.qx ? b.qx : c.qx);
+    long long ymin = a.qy < b.qy ? (a.qy < c.qy ? a.qy : c.qy) : (b.qy < c.qy ? b.qy : c.qy);
+    long long ymax = a.qy > b.qy ? (a.qy > c.qy ? a.qy : c.qy) : (b.qy > c.qy ? b.qy : c.qy);
+    /* pixels whose centre (256 x + 128) lies in [min, max] */
+    long long x0 = (xmin - 128 + 255) >> 8, x1 = (xmax - 128) >> 8, y0 = (ymin - 128 + 255) >> 8, y1 = (ymax - 128) >> 8;
+    if (x0 < 0) x0 = 0;
+    if (y0 < 0) y0 = 0;
+    if (x1 > W - 1) x1 = W - 1;
+    if (y1 > H - 1) y1 = H - 1;
+    int bab = edge_bias(a.qx, a.qy, b.qx, b.qy), bbc = edge_bias(b.qx, b.qy, c.qx, c.qy),
+        bca = edge_bias(c.qx, c.qy, a.qx, a.qy);
+    float areaf = (float)area;
+    for (long long y = y0; y <= y1; ++y)
+      for (long long x = x0; x <= x1; ++x) {
+        long long px = 256 * x + 128, py = 256 * y + 128;
+        long long wc = edge_fn(a.qx, a.qy, b.qx, b.qy, px, py); /* weight of c */
+        long long wa = edge_fn(b.qx, b.qy, c.qx, c.qy, px, py); /* weight of a */
+        long long wb = edge_fn(c.qx, c.qy, a.qx, a.qy, px, py); /* weight of b */
+        /* inside: every weight positive, or zero on a top-left edge */
+        if (wc < 0 || wa < 0 || wb < 0) continue;
+        if ((wc == 0 && bab) || (wa == 0 && bbc) || (wb == 0 && bca)) continue;
+        float fa = (float)wa, fb = (float)wb, fc = (float)wc;
+        float s0 = fa * a.iz, s1 = fb * b.iz, s2 = fc * c.iz;
+        float sum = (s0 + s1) + s2;
+        float z = areaf / sum;
+        unsigned zb;
+        memcpy(&zb, &z, 4);
+        unsigned long long key = ((unsigned long long)zb << 32) | (unsigned long long)tr;
+        long p = (long)y * W + x;
+        if (key < best[p]) best[p] = key;
+      }
+  }
+  for (long p = 0; p < (long)W * H; ++p) {
+    double* o = gb + 9 * p;
+    if (best[p] == ~0ULL) {
+      for (int q = 0; q < 8; ++q) o[q] = 0.0;
+      o[8] = INFINITY;
+      if (ids) ids[p] = -1;
+      continue;
+    }
+    long tr = (long)(best[p] & 0xffffffffULL);
+    unsigned zb = (unsigned)(best[p] >> 32);
+    float z;
+    memcpy(&z, &zb, 4);
+    int vi[3] = {tris[3 * tr], tris[3 * tr + 1], tris[3 * tr + 2]};
+    or_rvert r3[3];
+    for (int k = 0; k < 3; ++k) r3[k] = raster_vertex(verts + 12 * (long)vi[k], cam, kx, ky, hw, hh, nearf);
+    long long px = 256 * (p % W) + 128, py = 256 * (p / W) + 128;
+    /* barycentric weights in FP64 from the exact edge functions (orientation-independent) */
+    double bw[3];
+    bw[0] = (double)edge_fn(r3[1].qx, r3[1].qy, r3[2].qx, r3[2].qy, px, py);
+    bw[1] = (double)edge_fn(r3[2].qx, r3[2].qy, r3[0].qx, r3[0].qy, px, py);
+    bw[2] = (double)edge_fn(r3[0].qx, r3[0].qy, r3[1].qx, r3[1].qy, px, py);
+    double wsum = 0.0, w[3];
+    for (int k = 0; k < 3; ++k) {
+      w[k] = bw[k] / (-(double)r3[k].az);
+      wsum += w[k];
+    }
+    for (int k = 0; k < 3; ++k) w[k] /= wsum;
+    double attr[11] = {0};
+    for (int k = 0; k < 3; ++k)
+      for (int q = 0; q < 11; ++q) attr[q] += w[k] * verts[12 * (long)vi[k] + q];
+    double n[3] = {attr[3], attr[4], attr[5]};
+    normalize3(n);
+    o[0] = attr[6];
+    o[1] = attr[7];
+    o[2] = attr[8];
+    o[3] = attr[9];
+    o[4] = n[0];
+    o[5] = n[1];
+    o[6] = n[2];
+    o[7] = attr[10];
+    o[8] = z;
+    if (ids) ids[p] = (int)tr;
+  }
+  free(best);
   return 0;
 }

@@ -388,6 +388,57 @@ def make_hdr_field(seed: int, width: int, height: int) -> np.ndarray:
     return x.astype(np.float32)
 
 
+def make_mesh_scene(scene: "Scene", n_lat: int = 16, n_lon: int = 32, ground_cells: int = 64):
+    """Triangle-mesh version of the analytic scene for the G-buffer pass: every sphere as a UV
+    sphere (n_lat x n_lon quads, poles as fans) with its exact normals, the ground square as a
+    ground_cells^2 grid; per-vertex albedo, metal, rough of the object.  Returns (verts (V, 12)
+    float32: position, normal, albedo, metal, rough, 0; tris (T, 3) int32)."""
+    verts, tris = [], []
+    base = 0
+    th = np.linspace(0.0, math.pi, n_lat + 1)
+    ph = np.linspace(0.0, 2.0 * math.pi, n_lon + 1)[:-1]
+    T, P = np.meshgrid(th, ph, indexing="ij")
+    nrm = np.stack([np.sin(T) * np.cos(P), np.cos(T), np.sin(T) * np.sin(P)], -1).reshape(-1, 3)
+    grid = np.arange((n_lat + 1) * n_lon).reshape(n_lat + 1, n_lon)
+    q = []
+    for i in range(n_lat):
+        for j in range(n_lon):
+            a, b, c, d = grid[i, j], grid[i, (j + 1) % n_lon], grid[i + 1, j], grid[i + 1, (j + 1) % n_lon]
+            if i > 0:
+                q.append((a, c, b))
+            if i < n_lat - 1:
+                q.append((b, c, d))
+    q = np.asarray(q, np.int64)
+    for sidx in range(len(scene.radii)):
+        v = np.zeros((len(nrm), 12))
+        v[:, 0:3] = scene.centers[sidx] + scene.radii[sidx] * nrm
+        v[:, 3:6] = nrm
+        v[:, 6:9] = scene.albedo[sidx]
+        v[:, 9] = scene.metal[sidx]
+        v[:, 10] = scene.rough[sidx]
+        verts.append(v)
+        tris.append(q + base)
+        base += len(v)
+    n = ground_cells + 1
+    gx = np.linspace(-scene.ground_half, scene.ground_half, n)
+    X, Z = np.meshgrid(gx, gx, indexing="ij")
+    v = np.zeros((n * n, 12))
+    v[:, 0], v[:, 2] = X.reshape(-1), Z.reshape(-1)
+    v[:, 4] = 1.0
+    v[:, 6:9] = scene.albedo[-1]
+    v[:, 9] = scene.metal[-1]
+    v[:, 10] = scene.rough[-1]
+    idx = np.arange(n * n).reshape(n, n)
+    gq = []
+    for i in range(ground_cells):
+        for j in range(ground_cells):
+            a, b, c, d = idx[i, j], idx[i + 1, j], idx[i, j + 1], idx[i + 1, j + 1]
+            gq += [(a, b, c), (b, d, c)]
+    verts.append(v)
+    tris.append(np.asarray(gq, np.int64) + base)
+    return np.concatenate(verts).astype(np.float32), np.concatenate(tris).astype(np.int32)
+
+
 def make_point_cloud_gbuffer(seed: int, width: int, height: int, fill: float = 0.7) -> GBuffer:
     """Synthetic point-cloud G-buffer for eye-dome lighting: colour and depth only (normals 0):
     several depth layers (rough surfaces at depths 2..40 with per-pixel jitter) covering `fill` of
