@@ -319,6 +319,38 @@ epbr_status epbr_shade_tonemap(const epbr_gbuffer* gbuffer, const epbr_camera* c
                                uint8_t* ldr, int64_t ldr_pitch, void* stream);
 
 /* ---------------------------------------------------------------------------------------- */
+/* The G-buffer pass of mesh rendering (Sec. 4.1): triangles rasterised into the G-buffer    */
+/* ---------------------------------------------------------------------------------------- */
+typedef struct epbr_mesh {
+  const float* vertices;     /* DEVICE float[num_vertices * 12], 16-byte aligned: world position xyz,
+                                normal xyz, albedo rgb, metal, rough, unused */
+  int32_t num_vertices;      /* 0 .. 2^28 */
+  const int32_t* triangles;  /* DEVICE int32[num_triangles * 3] vertex indices (any winding) */
+  int32_t num_triangles;
+} epbr_mesh;
+
+/* Device workspace epbr_raster_gbuffer needs: 8 B per pixel (nearest (depth, triangle) key),
+ * 80 B and 8 B per triangle (set-up, item offsets), each part 256-byte aligned. */
+epbr_status epbr_raster_workspace_size(int32_t num_triangles, int32_t width, int32_t height, size_t* bytes);
+
+/* Writes the FP32 G-buffer `out` (rt[0] albedo + metal, rt[1] normal + rough, rt[3] eye depth;
+ * background: zeros and depth +inf) of the mesh seen by `camera`.  Pixel (x, y) is covered by
+ * a triangle when its centre lies inside it: vertices are transformed to view space and
+ * projected in FP32 with every product, sum and quotient rounded, snapped to 1/256 pixel (round
+ * half to even), and tested with 64-bit integer edge functions under a top-left rule, so that a
+ * centre on an edge shared by two triangles belongs to exactly one.  The nearest covering
+ * triangle writes the pixel: smallest FP32 eye depth A / ((b_a iz_a + b_b iz_b) + b_c iz_c)
+ * (b the edge functions, A their sum, iz = 1/z), then smallest index.  Attributes are
+ * interpolated perspective-correctly (weights b_i iz_i normalised), the normal normalised.  No
+ * clipping and no back-face culling: a triangle with a vertex at eye depth below `near_depth`
+ * (> 0), or projecting beyond 2^22 pixels, is not drawn.  `ids` (DEVICE int32, NULL allowed)
+ * receives the winning triangle index, -1 for background.  `workspace` DEVICE, 256-byte
+ * aligned, at least epbr_raster_workspace_size bytes.  Stream-ordered; no allocation. */
+epbr_status epbr_raster_gbuffer(const epbr_mesh* mesh, const epbr_camera* camera, float near_depth,
+                                const epbr_gbuffer* out, int32_t* ids, int64_t ids_pitch, void* workspace,
+                                size_t workspace_bytes, void* stream);
+
+/* ---------------------------------------------------------------------------------------- */
 /* Eye-dome lighting for point clouds (Sec. 4.2; Boucheny 2009): shading from depth alone    */
 /* ---------------------------------------------------------------------------------------- */
 typedef struct epbr_edl_params {

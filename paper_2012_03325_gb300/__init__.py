@@ -284,6 +284,40 @@ def epbr_tonemap(hdr: torch.Tensor, hdr_format: int, tp: F.epbr_tonemap_params, 
 
 
 # ------------------------------------------------------------------------------------------
+# mesh rendering: the G-buffer pass (Sec. 4.1)
+# ------------------------------------------------------------------------------------------
+class Mesh:
+    """Owns the vertex (V, 12) float32 and triangle (T, 3) int32 tensors and their epbr_mesh."""
+
+    def __init__(self, vertices: torch.Tensor, triangles: torch.Tensor):
+        _dev(vertices, torch.float32, "vertices")
+        _dev(triangles, torch.int32, "triangles")
+        if vertices.dim() != 2 or vertices.shape[1] != 12 or not vertices.is_contiguous():
+            raise ValueError("vertices must be a contiguous (V, 12) tensor")
+        if triangles.dim() != 2 or triangles.shape[1] != 3 or not triangles.is_contiguous():
+            raise ValueError("triangles must be a contiguous (T, 3) tensor")
+        self.tensors = (vertices, triangles)
+        self.struct = F.epbr_mesh(vertices.data_ptr(), vertices.shape[0], triangles.data_ptr(), triangles.shape[0])
+
+
+def epbr_raster_workspace_size(num_triangles: int, W: int, H: int) -> int:
+    n = C.c_size_t()
+    _check(lib().epbr_raster_workspace_size(num_triangles, W, H, C.byref(n)))
+    return n.value
+
+
+def epbr_raster_gbuffer(mesh: Mesh, cam: F.epbr_camera, near: float, out: GBuffer, ids: torch.Tensor | None = None,
+                        workspace: torch.Tensor | None = None, stream=None):
+    W, H = out.struct.width, out.struct.height
+    need = epbr_raster_workspace_size(mesh.struct.num_triangles, W, H)
+    ws = workspace if workspace is not None else _workspace(need, mesh.tensors[0].device)
+    ip = _dev(ids, torch.int32, "ids") if ids is not None else None
+    _check(lib().epbr_raster_gbuffer(C.byref(mesh.struct), C.byref(cam), near, C.byref(out.struct), ip,
+                                     _pitch(ids, 1) if ids is not None else 0, _aligned(ws),
+                                     ws.numel() - (_aligned(ws) - ws.data_ptr()), _stream(stream)))
+
+
+# ------------------------------------------------------------------------------------------
 # eye-dome lighting for point clouds (Sec. 4.2)
 # ------------------------------------------------------------------------------------------
 def edl_params(strength: float = 8.0, radius: int = 1, directions: int = 8) -> F.epbr_edl_params:

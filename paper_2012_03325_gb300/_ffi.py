@@ -83,6 +83,11 @@ class epbr_tonemap_params(C.Structure):
     _fields_ = [("exposure", C.c_float), ("op", C.c_int32)]
 
 
+class epbr_mesh(C.Structure):
+    _fields_ = [("vertices", C.c_void_p), ("num_vertices", C.c_int32), ("triangles", C.c_void_p),
+                ("num_triangles", C.c_int32)]
+
+
 class epbr_edl_params(C.Structure):
     _fields_ = [("strength", C.c_float), ("radius", C.c_int32), ("directions", C.c_int32)]
 
@@ -155,6 +160,8 @@ PROTOTYPES = {
     "epbr_shade_tonemap": [P(epbr_gbuffer), P(epbr_camera), vp, i32, P(epbr_ibl), P(epbr_shade_params), vp,
                            i32, i64, P(epbr_tonemap_params), vp, i64, vp],
     "epbr_tonemap": [vp, i32, i32, i32, i64, P(epbr_tonemap_params), vp, i64, vp],
+    "epbr_raster_workspace_size": [i32, i32, i32, P(sz)],
+    "epbr_raster_gbuffer": [P(epbr_mesh), P(epbr_camera), C.c_float, P(epbr_gbuffer), vp, i64, vp, sz, vp],
     "epbr_edl": [P(epbr_gbuffer), P(epbr_edl_params), vp, i64, i32, vp, i32, i64, P(epbr_tonemap_params), vp, i64,
                  vp],
     "epbr_shade_shadows": [P(epbr_gbuffer), P(epbr_camera), vp, i32, P(epbr_ibl), P(epbr_shade_params),

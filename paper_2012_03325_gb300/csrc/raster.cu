@@ -1,0 +1,374 @@
+// The G-buffer pass of mesh rendering (Sec. 4.1): triangles rasterised into the FP32 G-buffer.
+//   k_raster_setup     one thread per triangle: view transform and projection in FP32 with every
+//                      operation rounded, vertices snapped to 1/256 px, orientation, pixel
+//                      bounding box; the triangle's work item count is its box area (0: culled)
+//   k_scan_*           exclusive int64 prefix sum of the item counts (block scan, scan of the
+//                      block totals, add)
+//   k_raster_cover     one work item per (triangle, box pixel): threads take runs of 8 items (one
+//                      binary search per run), test the pixel centre with 64-bit integer edge
+//                      functions and a top-left rule, and keep the nearest (depth bits, index)
+//                      with a 64-bit atomicMin per pixel
+//   k_raster_resolve   one thread per pixel: the winning triangle's perspective-correct weights
+//                      and interpolated attributes, written as the FP32 G-buffer
+// The coverage and depth decisions evaluate exactly the expressions of the oracle (integer edge
+// functions; FP32 products, sums and quotients each rounded), so the covering triangle of every
+// pixel is reproducible bit for bit.
+#include <string.h>
+
+#include <cmath>
+
+#include "epbr_internal.cuh"
+
+namespace epbr {
+
+constexpr int kScanThreads = 256, kScanItems = 4, kScanBlock = kScanThreads * kScanItems;
+constexpr int kRunItems = 8;
+
+struct TriSetup {
+  int4 qab;    // snapped screen positions of a and b (1/256 px)
+  int4 qc_xy;  // c, then the box origin x0, y0
+  int4 box;    // box width, height, then the vertex indices of a and b
+  int4 vc;     // vertex index of c, unused x3
+  float4 iz;   // 1/z of a, b, c, then the area as a float
+};
+
+struct RasterCam {
+  float r[9];  // view_to_world rotation, row-major
+  float eye[3];
+  float kx, ky, hw, hh, near;
+  int W, H;
+};
+
+struct RVert {
+  float az, iz;
+  int qx, qy;
+  bool ok;
+};
+
+__device__ __forceinline__ RVert raster_vertex(const float* __restrict__ v, const RasterCam& c) {
+  float dx = __fsub_rn(v[0], c.eye[0]), dy = __fsub_rn(v[1], c.eye[1]), dz = __fsub_rn(v[2], c.eye[2]);
+  // view axis k = column k of the view_to_world rotation: r[k], r[3 + k], r[6 + k]
+  float ax = __fadd_rn(__fadd_rn(__fmul_rn(c.r[0], dx), __fmul_rn(c.r[3], dy)), __fmul_rn(c.r[6], dz));
+  float ay = __fadd_rn(__fadd_rn(__fmul_rn(c.r[1], dx), __fmul_rn(c.r[4], dy)), __fmul_rn(c.r[7], dz));
+  float az = __fadd_rn(__fadd_rn(__fmul_rn(c.r[2], dx), __fmul_rn(c.r[5], dy)), __fmul_rn(c.r[8], dz));
+  RVert o;
+  float e = -az;
+  o.az = az;
+  o.iz = __fdiv_rn(1.0f, e);
+  float u = __fmul_rn(ax, o.iz), w = __fmul_rn(ay, o.iz);
+  float X = __fmul_rn(c.hw, __fadd_rn(1.0f, __fmul_rn(u, c.kx)));
+  float Y = __fmul_rn(c.hh, __fsub_rn(1.0f, __fmul_rn(w, c.ky)));
+  o.ok = e >= c.near && fabsf(X) < 4194304.0f && fabsf(Y) < 4194304.0f;
+  o.qx = o.ok ? __float2int_rn(X * 256.0f) : 0;
+  o.qy = o.ok ? __float2int_rn(Y * 256.0f) : 0;
+  return o;
+}
+
+__device__ __forceinline__ long long edge_fn(long long ax, long long ay, long long bx, long long by, long long px,
+                                             long long py) {
+  return (bx - ax) * (py - ay) - (by - ay) * (px - ax);
+}
+
+// top-left rule: 0 for an edge whose zero-weight centres belong to the triangle, else 1
+__device__ __forceinline__ int edge_excl(int ax, int ay, int bx, int by) {
+  int dx = bx - ax, dy = by - ay;
+  return (dy < 0 || (dy == 0 && dx > 0)) ? 0 : 1;
+}
+
+__global__ void __launch_bounds__(256) k_raster_setup(const float* __restrict__ verts, int V, const int* __restrict__ tris,
+                                                      int T, RasterCam cam, TriSetup* __restrict__ setup,
+                                                      long long* __restrict__ counts) {
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= T) return;
+  int i[3] = {__ldg(tris + 3 * (size_t)t), __ldg(tris + 3 * (size_t)t + 1), __ldg(tris + 3 * (size_t)t + 2)};
+  long long cnt = 0;
+  TriSetup s;
+  memset(&s, 0, sizeof(s));
+  if (i[0] >= 0 && i[1] >= 0 && i[2] >= 0 && i[0] < V && i[1] < V && i[2] < V) {
+    RVert a = raster_vertex(verts + 12 * (size_t)i[0], cam), b = raster_vertex(verts + 12 * (size_t)i[1], cam),
+          c = raster_vertex(verts + 12 * (size_t)i[2], cam);
+    long long area = a.ok && b.ok && c.ok ? edge_fn(a.qx, a.qy, b.qx, b.qy, c.qx, c.qy) : 0;
+    if (area != 0) {
+      int ia = i[0], ib = i[1], ic = i[2];
+      if (area < 0) {  // orient so that the area is positive
+        RVert tmp = b;
+        b = c;
+        c = tmp;
+        ib = i[2];
+        ic = i[1];
+        area = -area;
+      }
+      long long xmin = min(a.qx, min(b.qx, c.qx)), xmax = max(a.qx, max(b.qx, c.qx));
+      long long ymin = min(a.qy, min(b.qy, c.qy)), ymax = max(a.qy, max(b.qy, c.qy));
+      // pixels whose centre 256 x + 128 lies in [min, max], clipped to the image
+      long long x0 = max((xmin - 128 + 255) >> 8, 0LL), x1 = min((xmax - 128) >> 8, (long long)cam.W - 1);
+      long long y0 = max((ymin - 128 + 255) >> 8, 0LL), y1 = min((ymax - 128) >> 8, (long long)cam.H - 1);
+      if (x1 >= x0 && y1 >= y0) {
+        cnt = (x1 - x0 + 1) * (y1 - y0 + 1);
+        s.qab = make_int4(a.qx, a.qy, b.qx, b.qy);
+        s.qc_xy = make_int4(c.qx, c.qy, (int)x0, (int)y0);
+        s.box = make_int4((int)(x1 - x0 + 1), (int)(y1 - y0 + 1), ia, ib);
+        s.vc = make_int4(ic, 0, 0, 0);
+        s.iz = make_float4(a.iz, b.iz, c.iz, __ll2float_rn(area));
+      }
+    }
+  }
+  setup[t] = s;
+  counts[t] = cnt;
+}
+
+// ---- exclusive int64 scan ------------------------------------------------------------------
+__device__ __forceinline__ long long warp_incl_scan(long long v) {
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    long long n = __shfl_up_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) >= o) v += n;
+  }
+  return v;
+}
+
+// Scans kScanBlock values per block in place (exclusive) and writes the block total.
+__global__ void __launch_bounds__(kScanThreads) k_scan_block(long long* __restrict__ data, long long n,
+                                                             long long* __restrict__ block_sums) {
+  __shared__ long long s_warp[kScanThreads / 32];
+  const long long base = (long long)blockIdx.x * kScanBlock + (long long)threadIdx.x * kScanItems;
+  long long v[kScanItems], run = 0;
+#pragma unroll
+  for (int k = 0; k < kScanItems; ++k) {
+    v[k] = base + k < n ? data[base + k] : 0;
+    run += v[k];
+  }
+  long long incl = warp_incl_scan(run);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (lane == 31) s_warp[warp] = incl;
+  __syncthreads();
+  if (warp == 0) {
+    long long w = lane < kScanThreads / 32 ? s_warp[lane] : 0;
+    w = warp_incl_scan(w);
+    if (lane < kScanThreads / 32) s_warp[lane] = w;
+  }
+  __syncthreads();
+  long long prefix = incl - run + (warp > 0 ? s_warp[warp - 1] : 0);
+#pragma unroll
+  for (int k = 0; k < kScanItems; ++k) {
+    if (base + k < n) data[base + k] = prefix;
+    prefix += v[k];
+  }
+  if (threadIdx.x == kScanThreads - 1) block_sums[blockIdx.x] = prefix;
+}
+
+// One block: exclusive scan of the block totals in place; total at sums[nb].
+__global__ void __launch_bounds__(kScanThreads) k_scan_sums(long long* __restrict__ sums, int nb) {
+  __shared__ long long s_warp[kScanThreads / 32];
+  __shared__ long long s_carry;
+  if (threadIdx.x == 0) s_carry = 0;
+  __syncthreads();
+  for (int b0 = 0; b0 < nb; b0 += kScanThreads) {
+    int i = b0 + threadIdx.x;
+    long long v = i < nb ? sums[i] : 0;
+    long long incl = warp_incl_scan(v);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 31) s_warp[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+      long long w = lane < kScanThreads / 32 ? s_warp[lane] : 0;
+      w = warp_incl_scan(w);
+      if (lane < kScanThreads / 32) s_warp[lane] = w;
+    }
+    __syncthreads();
+    long long excl = s_carry + incl - v + (warp > 0 ? s_warp[warp - 1] : 0);
+    if (i < nb) sums[i] = excl;
+    __syncthreads();
+    if (threadIdx.x == kScanThreads - 1) s_carry = excl + v;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) sums[nb] = s_carry;
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_add(long long* __restrict__ data, long long n,
+                                                           const long long* __restrict__ sums) {
+  const long long base = (long long)blockIdx.x * kScanBlock;
+  const long long add = sums[blockIdx.x];
+  for (int k = threadIdx.x; k < kScanBlock; k += kScanThreads)
+    if (base + k < n) data[base + k] += add;
+}
+
+// ---- coverage --------------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_raster_cover(const TriSetup* __restrict__ setup,
+                                                      const long long* __restrict__ offsets, int T,
+                                                      const long long* __restrict__ total_p, int W,
+                                                      unsigned long long* __restrict__ keys) {
+  const long long total = *total_p;
+  const long long runs = (total + kRunItems - 1) / kRunItems;
+  for (long long run = blockIdx.x * (long long)blockDim.x + threadIdx.x; run < runs;
+       run += (long long)gridDim.x * blockDim.x) {
+    long long item = run * kRunItems;
+    // the triangle holding `item`: the last t with offsets[t] <= item
+    int lo = 0, hi = T - 1;
+    while (lo < hi) {
+      int mid = (lo + hi + 1) >> 1;
+      if (__ldg(offsets + mid) <= item) lo = mid;
+      else hi = mid - 1;
+    }
+    int t = lo;
+    long long t_end = t + 1 < T ? __ldg(offsets + t + 1) : total;
+    TriSetup s = setup[t];
+    const long long stop = min(item + kRunItems, total);
+    for (; item < stop; ++item) {
+      while (item >= t_end) {  // next triangle with items
+        ++t;
+        t_end = t + 1 < T ? __ldg(offsets + t + 1) : total;
+        s = setup[t];
+      }
+      const long long local = item - (t_end - (long long)s.box.x * s.box.y);
+      const int ly = (int)(local / s.box.x), lx = (int)(local - (long long)ly * s.box.x);
+      const int x = s.qc_xy.z + lx, y = s.qc_xy.w + ly;
+      const long long px = 256LL * x + 128, py = 256LL * y + 128;
+      const long long wc = edge_fn(s.qab.x, s.qab.y, s.qab.z, s.qab.w, px, py);
+      const long long wa = edge_fn(s.qab.z, s.qab.w, s.qc_xy.x, s.qc_xy.y, px, py);
+      const long long wb = edge_fn(s.qc_xy.x, s.qc_xy.y, s.qab.x, s.qab.y, px, py);
+      if (wc < 0 || wa < 0 || wb < 0) continue;
+      if ((wc == 0 && edge_excl(s.qab.x, s.qab.y, s.qab.z, s.qab.w)) ||
+          (wa == 0 && edge_excl(s.qab.z, s.qab.w, s.qc_xy.x, s.qc_xy.y)) ||
+          (wb == 0 && edge_excl(s.qc_xy.x, s.qc_xy.y, s.qab.x, s.qab.y)))
+        continue;
+      float s0 = __fmul_rn(__ll2float_rn(wa), s.iz.x), s1 = __fmul_rn(__ll2float_rn(wb), s.iz.y);
+      float s2 = __fmul_rn(__ll2float_rn(wc), s.iz.z);
+      float z = __fdiv_rn(s.iz.w, __fadd_rn(__fadd_rn(s0, s1), s2));
+      unsigned long long key = ((unsigned long long)__float_as_uint(z) << 32) | (unsigned)t;
+      atomicMin(keys + (size_t)y * W + x, key);
+    }
+  }
+}
+
+// ---- resolve ---------------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_raster_resolve(const float* __restrict__ verts,
+                                                        const TriSetup* __restrict__ setup,
+                                                        const unsigned long long* __restrict__ keys, int W, int H,
+                                                        GbufDev g, int* __restrict__ ids, long long ids_pitch) {
+  int x = blockIdx.x * 32 + threadIdx.x, y = blockIdx.y * 8 + threadIdx.y;
+  if (x >= W || y >= H) return;
+  unsigned long long key = keys[(size_t)y * W + x];
+  float4* rt0 = (float4*)(const_cast<char*>(g.rt[0]) + (size_t)y * g.pitch[0]) + x;
+  float4* rt1 = (float4*)(const_cast<char*>(g.rt[1]) + (size_t)y * g.pitch[1]) + x;
+  float* dep = (float*)(const_cast<char*>(g.rt[3]) + (size_t)y * g.pitch[3]) + x;
+  int* idp = ids ? (int*)((char*)ids + (size_t)y * ids_pitch) + x : nullptr;
+  if (key == ~0ULL) {
+    *rt0 = make_float4(0, 0, 0, 0);
+    *rt1 = make_float4(0, 0, 0, 0);
+    *dep = __int_as_float(0x7f800000);
+    if (idp) *idp = -1;
+    return;
+  }
+  const int t = (int)(key & 0xffffffffULL);
+  const TriSetup s = setup[t];
+  const long long px = 256LL * x + 128, py = 256LL * y + 128;
+  // perspective-correct weights b_i / z_i normalised, from the exact edge functions
+  float wa = __ll2float_rn(edge_fn(s.qab.z, s.qab.w, s.qc_xy.x, s.qc_xy.y, px, py)) * s.iz.x;
+  float wb = __ll2float_rn(edge_fn(s.qc_xy.x, s.qc_xy.y, s.qab.x, s.qab.y, px, py)) * s.iz.y;
+  float wc = __ll2float_rn(edge_fn(s.qab.x, s.qab.y, s.qab.z, s.qab.w, px, py)) * s.iz.z;
+  float inv = 1.0f / (wa + wb + wc);
+  wa *= inv;
+  wb *= inv;
+  wc *= inv;
+  const float* A = verts + 12 * (size_t)s.box.z;
+  const float* B = verts + 12 * (size_t)s.box.w;
+  const float* C = verts + 12 * (size_t)s.vc.x;
+  float at[8];  // normal xyz, albedo rgb, metal, rough: vertex values 3 .. 10
+#pragma unroll
+  for (int q = 0; q < 8; ++q) at[q] = fmaf(wa, __ldg(A + 3 + q), fmaf(wb, __ldg(B + 3 + q), wc * __ldg(C + 3 + q)));
+  float3 n = f3(at[0], at[1], at[2]);
+  n = n * (1.0f / sqrtf(dot3(n, n)));
+  *rt0 = make_float4(at[3], at[4], at[5], at[6]);
+  *rt1 = make_float4(n.x, n.y, n.z, at[7]);
+  *dep = __uint_as_float((unsigned)(key >> 32));
+  if (idp) *idp = t;
+}
+
+static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+struct RasterLayout {
+  size_t keys, setup, offsets, sums, bytes;
+};
+
+static RasterLayout raster_layout(long long T, int W, int H) {
+  RasterLayout l;
+  size_t off = 0;
+  l.keys = off;
+  off = align256(off + sizeof(unsigned long long) * (size_t)W * H);
+  l.setup = off;
+  off = align256(off + sizeof(TriSetup) * (size_t)T);
+  l.offsets = off;
+  off = align256(off + sizeof(long long) * (size_t)(T + 1));
+  l.sums = off;
+  long long nb = (T + kScanBlock - 1) / kScanBlock;
+  off = align256(off + sizeof(long long) * (size_t)(nb + 1));
+  l.bytes = off;
+  return l;
+}
+
+}  // namespace epbr
+
+using namespace epbr;
+
+extern "C" epbr_status epbr_raster_workspace_size(int32_t num_triangles, int32_t width, int32_t height, size_t* bytes) {
+  if (!bytes || num_triangles < 0 || width < 1 || height < 1 || width > (1 << 15) || height > (1 << 15))
+    return fail(EPBR_ERR_INVALID_ARG, "raster: bytes NULL, num_triangles < 0 or size outside [1, 32768]");
+  *bytes = raster_layout(num_triangles, width, height).bytes;
+  return ok();
+}
+
+extern "C" epbr_status epbr_raster_gbuffer(const epbr_mesh* mesh, const epbr_camera* camera, float near_depth,
+                                           const epbr_gbuffer* out, int32_t* ids, int64_t ids_pitch, void* workspace,
+                                           size_t workspace_bytes, void* stream) {
+  if (!mesh || !out) return fail(EPBR_ERR_INVALID_ARG, "raster: mesh or gbuffer is NULL");
+  epbr_status st = validate_camera(camera, out);
+  if (st) return st;
+  if (out->format != EPBR_GBUFFER_FP32) return fail(EPBR_ERR_INVALID_ARG, "raster: the output G-buffer must be FP32");
+  if ((st = validate_gbuffer(out, true))) return st;
+  if (mesh->num_vertices < 0 || mesh->num_triangles < 0 || mesh->num_vertices > (1 << 28) ||
+      (mesh->num_triangles > 0 && (!mesh->vertices || !mesh->triangles)) || (uintptr_t)mesh->vertices % 16 ||
+      (uintptr_t)mesh->triangles % 4)
+    return fail(EPBR_ERR_INVALID_ARG, "raster: vertices / triangles NULL, misaligned or counts out of range");
+  if (!(near_depth > 0.0f) || !std::isfinite(near_depth)) return fail(EPBR_ERR_INVALID_ARG, "raster: near must be > 0");
+  if (ids && (ids_pitch < 4LL * out->width || ids_pitch % 4 || (uintptr_t)ids % 4))
+    return fail(EPBR_ERR_INVALID_ARG, "raster: ids misaligned or pitch too small");
+  const int W = out->width, H = out->height, T = mesh->num_triangles;
+  RasterLayout l = raster_layout(T, W, H);
+  if (!workspace || (uintptr_t)workspace % 256 || workspace_bytes < l.bytes)
+    return fail(EPBR_ERR_INVALID_ARG, "raster: workspace NULL, not 256-byte aligned or below %zu bytes", l.bytes);
+  char* ws = (char*)workspace;
+  unsigned long long* keys = (unsigned long long*)(ws + l.keys);
+  TriSetup* setup = (TriSetup*)(ws + l.setup);
+  long long* offsets = (long long*)(ws + l.offsets);
+  long long* sums = (long long*)(ws + l.sums);
+  RasterCam rc;
+  CamDev cd = make_cam(*camera);
+  for (int i = 0; i < 9; ++i) rc.r[i] = cd.r[i];
+  for (int i = 0; i < 3; ++i) rc.eye[i] = cd.eye[i];
+  double t = std::tan(0.5 * (double)camera->fov_y);
+  rc.ky = (float)(1.0 / t);
+  rc.kx = (float)((double)H / ((double)W * t));
+  rc.hw = (float)(0.5 * W);
+  rc.hh = (float)(0.5 * H);
+  rc.near = near_depth;
+  rc.W = W;
+  rc.H = H;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (cudaMemsetAsync(keys, 0xff, sizeof(unsigned long long) * (size_t)W * H, s) != cudaSuccess)
+    return fail(EPBR_ERR_CUDA, "raster: memset failed");
+  GbufDev gd = make_gbuf(*out);
+  if (T > 0) {
+    k_raster_setup<<<(T + 255) / 256, 256, 0, s>>>(mesh->vertices, mesh->num_vertices, mesh->triangles, T, rc, setup,
+                                                   offsets);
+    const long long nb = (T + kScanBlock - 1) / kScanBlock;
+    k_scan_block<<<(unsigned)nb, kScanThreads, 0, s>>>(offsets, T, sums);
+    k_scan_sums<<<1, kScanThreads, 0, s>>>(sums, (int)nb);
+    k_scan_add<<<(unsigned)nb, kScanThreads, 0, s>>>(offsets, T, sums);
+    k_raster_cover<<<num_sms() * 8, 256, 0, s>>>(setup, offsets, T, sums + nb, W, keys);
+  }
+  dim3 blk(32, 8), grd((W + 31) / 32, (H + 7) / 8);
+  k_raster_resolve<<<grd, blk, 0, s>>>(mesh->vertices, setup, keys, W, H, gd, ids, ids_pitch);
+  if ((st = check_launch("raster"))) return st;
+  return ok();
+}
