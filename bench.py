@@ -44,6 +44,9 @@ def parse():
     ap.add_argument("--serve-seconds", type=float, default=3.0, help="arrival window per rate (serve workload)")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="CPU-baseline time budget")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--mesh", action="store_true",
+                    help="produce the G-buffer on the device every frame by rasterising the scene's triangle mesh "
+                         "(Sec. 4.1) instead of uploading it; the mesh stays resident")
     ap.add_argument("--shadows", action="store_true",
                     help="shade with per-light shadow maps and 3x3 PCF (Sec. 5.1); maps stay resident")
     ap.add_argument("--bloom", action="store_true",
@@ -124,6 +127,8 @@ FLOP_TONEMAP = 36        # every pixel: exposure, ACES fit, clamp, sRGB transfer
 FLOP_SHADOW = 40         # lit pair with shadows: light-view transform (18), 1/z, texel coordinates (6),
                          # threshold (2), nine depth compares, the visibility scale (3)
 SHADOW = {"size": 512, "fov_deg": 90.0, "bias_const": 0.02, "bias_slope": 0.01}
+MESH = {"n_lat": 16, "n_lon": 32, "ground_cells": 64, "near": 0.05}
+RASTER_LAUNCHES = 7  # key reset, set-up, three scan kernels, coverage, resolve
 
 
 def compose_flops(sc, g, n_lights) -> tuple[float, dict]:
@@ -261,7 +266,7 @@ def sources_sha(files=SHADE_SOURCES):
 # CPU oracle baseline
 # ------------------------------------------------------------------------------------------
 def oracle_frame_rate(c, sc, g, env, k, nz, seconds: float, oracle_ibl=None, threads: int = 0, bloom=False,
-                      shadow_maps=None):
+                      shadow_maps=None, mesh=None):
     """The FP64 oracle's per-frame path (blurred SSAO, compose, tone map) on horizontal bands of
     the frame until `seconds` elapse; returns (Mpixels/s, cores, sample description).  With
     `bloom`, the oracle's bloom of one whole frame (it needs the whole image) is timed as well and
@@ -303,6 +308,14 @@ def oracle_frame_rate(c, sc, g, env, k, nz, seconds: float, oracle_ibl=None, thr
         px_done += pixels.size
         y0 = (y0 + band) % H
     dt = time.perf_counter() - t0
+    if mesh is not None:  # the oracle's G-buffer pass of one whole frame, one thread
+        tr = time.perf_counter()
+        oracle.raster(mesh[0], mesh[1], oracle.camera(sc.camera_array(), float(np.float32(sc.fov_y)), W, H),
+                      MESH["near"])
+        tr = time.perf_counter() - tr
+        rate = 1.0 / (dt / px_done + tr / (W * H)) / 1e6
+        return rate, cores, (f"{px_done} px in {px_done // W} full-width rows ({dt:.1f} s wall) + the G-buffer pass "
+                             f"of one {W}x{H} frame from {len(mesh[1])} triangles ({tr:.2f} s, one thread)")
     if bloom:
         frame = synth.make_bloom_field(1, W, H)
         tb = time.perf_counter()
@@ -370,6 +383,13 @@ def run_gpu(args):
         host_rts = [g.rt0, g.rt1, None, g.depth]
     dev_rts = [t(a) if a is not None else None for a in host_rts]
     gb = ep.GBuffer.compact(*dev_rts) if compact else ep.GBuffer.fp32(dev_rts[0], dev_rts[1], dev_rts[3])
+    mesh = ws_raster = None
+    if args.mesh:
+        if compact:
+            raise SystemExit("--mesh writes the FP32 G-buffer; use it with an FP32 workload")
+        mv, mt = synth.make_mesh_scene(sc, MESH["n_lat"], MESH["n_lon"], MESH["ground_cells"])
+        mesh = ep.Mesh(t(mv), t(mt))
+        ws_raster = torch.empty(ep.epbr_raster_workspace_size(len(mt), W, H) + 256, dtype=torch.uint8, device=dev)
     cam = ep.camera(sc.camera_array(), sc.fov_y, W, H)
     lights = t(sc.lights)
     env_t = t(env)
@@ -433,12 +453,25 @@ def run_gpu(args):
                 b2.record(stream)
                 ev_bloom.append((a2, b2))
 
+    ev_raster = []
+
+    def raster(g_, record=False):
+        if record:
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+        ep.epbr_raster_gbuffer(mesh, cam, MESH["near"], g_, None, ws_raster, stream=stream)
+        if record:
+            b.record(stream)
+            ev_raster.append((a, b))
+
     def step(record=False):
+        if args.mesh:
+            raster(gb, record)
         ep.epbr_ssao_raw(gb, cam, sp, ao_raw, stream=stream)
         ep.epbr_ssao_blur(gb, sp, ao_raw, ao, stream=stream)
         compose(gb, shp, hdr, ldr, lights, record)
 
-    launches_per_step = 3 + (BLOOM_LAUNCHES if args.bloom else 0)
+    launches_per_step = 3 + (BLOOM_LAUNCHES if args.bloom else 0) + (RASTER_LAUNCHES if args.mesh else 0)
     with torch.cuda.stream(stream):
         for _ in range(max(3, args.warmup)):
             step()
@@ -474,7 +507,8 @@ def run_gpu(args):
     pinned = [torch.from_numpy(np.ascontiguousarray(a)).pin_memory() if a is not None else None for a in host_rts]
     lights_h = torch.from_numpy(sc.lights).pin_memory()
     ldr_h = [torch.empty(H, W, 4, dtype=torch.uint8).pin_memory() for _ in range(2)]
-    h2d = sum(p.numel() * p.element_size() for p in pinned if p is not None) + lights_h.numel() * 4
+    h2d = (0 if args.mesh else sum(p.numel() * p.element_size() for p in pinned if p is not None)) + \
+        lights_h.numel() * 4
     d2h = ldr_h[0].numel()
 
     def buffer_set():
@@ -498,7 +532,7 @@ def run_gpu(args):
         go = ev()
         go.record(s_up)
         ups = []
-        for k_, (p_, d_) in enumerate((p_, d_) for p_, d_ in zip(pinned, b["rts"]) if p_ is not None):
+        for k_, (p_, d_) in enumerate((p_, d_) for p_, d_ in zip(pinned, b["rts"]) if p_ is not None and not args.mesh):
             sk = s_planes[k_ % len(s_planes)]
             sk.wait_event(go)
             with torch.cuda.stream(sk):
@@ -517,6 +551,8 @@ def run_gpu(args):
             stream.wait_event(done_dn[i % 2])  # the set's previous image has been downloaded
         with torch.cuda.stream(stream):
             flush.zero_()  # L2 flush inside the timed window
+            if args.mesh:
+                raster(b["gb"])
             ep.epbr_ssao_raw(b["gb"], cam, sp, b["ao_raw"], stream=stream)
             ep.epbr_ssao_blur(b["gb"], sp, b["ao_raw"], b["ao"], stream=stream)
             compose(b["gb"], b["shp"], b["hdr"], b["ldr"], b["lights"])
@@ -556,7 +592,11 @@ def run_gpu(args):
     clocks = clk.summary()
     props = torch.cuda.get_device_properties(dev)
     sms = props.multi_processor_count
-    flops, counts = compose_flops(sc, g, c["lights"])
+    if args.mesh:  # count the work on the rasterised G-buffer the frames shade
+        g_cnt = synth.GBuffer(dev_rts[0].cpu().numpy(), dev_rts[1].cpu().numpy(), dev_rts[3].cpu().numpy())
+    else:
+        g_cnt = g
+    flops, counts = compose_flops(sc, g_cnt, c["lights"])
     if args.shadows:
         flops += counts["lit_pairs"] * FLOP_SHADOW
     clock_mhz = clocks["sm_mhz"] if clocks else 2070.0
@@ -581,7 +621,9 @@ def run_gpu(args):
                                                 "bloom": BLOOM} if args.bloom else {}),
                                             **({"shadows": dict(SHADOW, maps="one per light, resident (static "
                                                                 "scene), generated by the ray caster")}
-                                               if args.shadows else {})}),
+                                               if args.shadows else {}),
+                                            **({"gbuffer": "fp32 36 B/px, rasterised on the device every frame from "
+                                                           "the resident triangle mesh"} if args.mesh else {})}),
             "roofline": roofline,
             "e2e": {"value": e2e_value, "unit": "Mpixels/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                     "how": "pinned host G-buffer + lights uploaded and RGBA8 downloaded every step; frames "
@@ -589,6 +631,12 @@ def run_gpu(args):
                            "streams with 2 buffer sets; L2 flush inside the window"},
             "gpu_launches": launches_per_step * args.steps,
             "clocks": clocks}
+    if args.mesh:
+        line["raster"] = {"ms": statistics.mean(a.elapsed_time(b) for a, b in ev_raster),
+                          "triangles": mesh.struct.num_triangles, "vertices": mesh.struct.num_vertices,
+                          "launches": RASTER_LAUNCHES, **MESH}
+        line["e2e"]["how"] = ("mesh resident; lights uploaded and RGBA8 downloaded every step; frames pipelined "
+                              "over upload, compute (raster + SSAO + compose) and download streams")
     if args.bloom:
         bloom_ms = statistics.mean(a.elapsed_time(b) for a, b in ev_bloom)
         hdr_bytes = 8 if compact else 16
@@ -602,7 +650,8 @@ def run_gpu(args):
     if not args.no_cpu_baseline and world == 1:
         rate, cores, sample = oracle_frame_rate(dict(c, name=name), sc, g, env, k, nz, args.cpu_seconds,
                                                 bloom=args.bloom,
-                                                shadow_maps=(maps, cams) if args.shadows else None)
+                                                shadow_maps=(maps, cams) if args.shadows else None,
+                                                mesh=(mv, mt) if args.mesh else None)
         line["cpu_baseline"] = {"value": rate, "unit": "Mpixels/s", "cores": cores, "kind": "oracle",
                                 "sample": sample}
     print(json.dumps(line), flush=True)

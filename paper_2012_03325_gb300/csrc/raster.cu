@@ -5,7 +5,8 @@
 //   k_scan_*           exclusive int64 prefix sum of the item counts (block scan, scan of the
 //                      block totals, add)
 //   k_raster_cover     one work item per (triangle, box pixel): threads take runs of 8 items (one
-//                      binary search per run), test the pixel centre with 64-bit integer edge
+//                      binary search per run, then a walk along the box rows), test the pixel
+//                      centre with 64-bit integer edge
 //                      functions and a top-left rule, and keep the nearest (depth bits, index)
 //                      with a 64-bit atomicMin per pixel
 //   k_raster_resolve   one thread per pixel: the winning triangle's perspective-correct weights
@@ -194,39 +195,65 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_add(long long* __restrict
 }
 
 // ---- coverage --------------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) k_raster_cover(const TriSetup* __restrict__ setup,
-                                                      const long long* __restrict__ offsets, int T,
-                                                      const long long* __restrict__ total_p, int W,
-                                                      unsigned long long* __restrict__ keys) {
+constexpr int kCoverThreads = 256;
+
+// Threads take runs of 8 consecutive items: one binary search per run for the first item's
+// triangle, then a walk along the box rows (and on to the next triangles).
+__global__ void __launch_bounds__(kCoverThreads) k_raster_cover(const TriSetup* __restrict__ setup,
+                                                                const long long* __restrict__ offsets, int T,
+                                                                const long long* __restrict__ total_p, int W,
+                                                                unsigned long long* __restrict__ keys) {
   const long long total = *total_p;
   const long long runs = (total + kRunItems - 1) / kRunItems;
   for (long long run = blockIdx.x * (long long)blockDim.x + threadIdx.x; run < runs;
        run += (long long)gridDim.x * blockDim.x) {
     long long item = run * kRunItems;
-    // the triangle holding `item`: the last t with offsets[t] <= item
-    int lo = 0, hi = T - 1;
+    int lo = 0, hi = T - 1;  // the last t with offsets[t] <= item
     while (lo < hi) {
       int mid = (lo + hi + 1) >> 1;
       if (__ldg(offsets + mid) <= item) lo = mid;
       else hi = mid - 1;
     }
     int t = lo;
+    long long t_begin = __ldg(offsets + t);
     long long t_end = t + 1 < T ? __ldg(offsets + t + 1) : total;
     TriSetup s = setup[t];
     const long long stop = min(item + kRunItems, total);
+    int lx = 0, ly = 0;
+    bool fresh = true;
+    long long wc = 0, wa = 0, wb = 0;     // edge functions at the current pixel centre
+    long long dc = 0, da = 0, db = 0;     // their change per pixel along a row
     for (; item < stop; ++item) {
       while (item >= t_end) {  // next triangle with items
         ++t;
+        t_begin = t_end;
         t_end = t + 1 < T ? __ldg(offsets + t + 1) : total;
         s = setup[t];
+        fresh = true;
       }
-      const long long local = item - (t_end - (long long)s.box.x * s.box.y);
-      const int ly = (int)(local / s.box.x), lx = (int)(local - (long long)ly * s.box.x);
+      if (fresh) {  // position of this item in the triangle's box
+        const long long local = item - t_begin;
+        ly = (int)(local / s.box.x);
+        lx = (int)(local - (long long)ly * s.box.x);
+        // E(p) = (b.x - a.x)(p.y - a.y) - (b.y - a.y)(p.x - a.x): a step of one pixel in x adds
+        // -256 (b.y - a.y)
+        dc = -256LL * (s.qab.w - s.qab.y);
+        da = -256LL * (s.qc_xy.y - s.qab.w);
+        db = -256LL * (s.qab.y - s.qc_xy.y);
+      }
       const int x = s.qc_xy.z + lx, y = s.qc_xy.w + ly;
-      const long long px = 256LL * x + 128, py = 256LL * y + 128;
-      const long long wc = edge_fn(s.qab.x, s.qab.y, s.qab.z, s.qab.w, px, py);
-      const long long wa = edge_fn(s.qab.z, s.qab.w, s.qc_xy.x, s.qc_xy.y, px, py);
-      const long long wb = edge_fn(s.qc_xy.x, s.qc_xy.y, s.qab.x, s.qab.y, px, py);
+      if (fresh || lx == 0) {  // a run's first item, a new triangle or a new box row: evaluate
+        const long long px = 256LL * x + 128, py = 256LL * y + 128;
+        wc = edge_fn(s.qab.x, s.qab.y, s.qab.z, s.qab.w, px, py);
+        wa = edge_fn(s.qab.z, s.qab.w, s.qc_xy.x, s.qc_xy.y, px, py);
+        wb = edge_fn(s.qc_xy.x, s.qc_xy.y, s.qab.x, s.qab.y, px, py);
+        fresh = false;
+      } else {
+        wc += dc;
+        wa += da;
+        wb += db;
+      }
+      if (++lx == s.box.x) lx = 0, ++ly;
       if (wc < 0 || wa < 0 || wb < 0) continue;
       if ((wc == 0 && edge_excl(s.qab.x, s.qab.y, s.qab.z, s.qab.w)) ||
           (wa == 0 && edge_excl(s.qab.z, s.qab.w, s.qc_xy.x, s.qc_xy.y)) ||
@@ -365,7 +392,7 @@ extern "C" epbr_status epbr_raster_gbuffer(const epbr_mesh* mesh, const epbr_cam
     k_scan_block<<<(unsigned)nb, kScanThreads, 0, s>>>(offsets, T, sums);
     k_scan_sums<<<1, kScanThreads, 0, s>>>(sums, (int)nb);
     k_scan_add<<<(unsigned)nb, kScanThreads, 0, s>>>(offsets, T, sums);
-    k_raster_cover<<<num_sms() * 8, 256, 0, s>>>(setup, offsets, T, sums + nb, W, keys);
+    k_raster_cover<<<num_sms() * 8, kCoverThreads, 0, s>>>(setup, offsets, T, sums + nb, W, keys);
   }
   dim3 blk(32, 8), grd((W + 31) / 32, (H + 7) / 8);
   k_raster_resolve<<<grd, blk, 0, s>>>(mesh->vertices, setup, keys, W, H, gd, ids, ids_pitch);
