@@ -42,6 +42,8 @@ def parse():
     ap.add_argument("--workload", default=WORKLOAD, choices=sorted(synth.CONFIGS) + ["batch", "serve", "edl"])
     ap.add_argument("--serve-requests", type=int, default=300, help="requests per rate (serve workload)")
     ap.add_argument("--serve-seconds", type=float, default=3.0, help="arrival window per rate (serve workload)")
+    ap.add_argument("--serve-streams", type=int, default=8, help="server streams (serve workload)")
+    ap.add_argument("--serve-inflight", type=int, default=16, help="server requests in flight (serve workload)")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="CPU-baseline time budget")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--mesh", action="store_true",
@@ -986,7 +988,8 @@ def run_serve(args):
                 "offered_req_s": rate, "achieved_req_s": len(results) / (t_end - t0)}
 
     budget = 6 << 30
-    served = ep.Server(ibls, sp, memory_budget=budget, max_in_flight=16, num_streams=8)
+    served = ep.Server(ibls, sp, memory_budget=budget, max_in_flight=args.serve_inflight,
+                       num_streams=args.serve_streams)
     fifo = ep.Server(ibls, sp, memory_budget=budget, max_in_flight=1, num_streams=1)
     run(served, make_requests(20, 1), None)  # warm-up
     run(fifo, make_requests(10, 2), None)
@@ -1009,7 +1012,8 @@ def run_serve(args):
             "config": {"workload": "serve: Poisson arrivals, resolution {256^2, 512^2, 1920x1080, 3840x2160} with "
                                    "weights .4/.3/.2/.1, 1-256 lights (log-uniform), 16 resident 1024x512 "
                                    "lighting sets, FP32 G-buffer from pinned host memory, RGBA8 back to host",
-                       "server": {"memory_budget": budget, "max_in_flight": 16, "streams": 8},
+                       "server": {"memory_budget": budget, "max_in_flight": args.serve_inflight,
+                                  "streams": args.serve_streams},
                        "value": "saturation throughput: all requests submitted at once"},
             "rates": rates, "saturation": burst, "fifo_one_at_a_time": burst_fifo,
             "speedup_vs_fifo": burst["mpx_s"] / burst_fifo["mpx_s"],
