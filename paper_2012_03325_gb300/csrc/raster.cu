@@ -294,18 +294,29 @@ __global__ void __launch_bounds__(256) k_raster_resolve(const float* __restrict_
   float wa = __ll2float_rn(edge_fn(s.qab.z, s.qab.w, s.qc_xy.x, s.qc_xy.y, px, py)) * s.iz.x;
   float wb = __ll2float_rn(edge_fn(s.qc_xy.x, s.qc_xy.y, s.qab.x, s.qab.y, px, py)) * s.iz.y;
   float wc = __ll2float_rn(edge_fn(s.qab.x, s.qab.y, s.qab.z, s.qab.w, px, py)) * s.iz.z;
-  float inv = 1.0f / (wa + wb + wc);
+  const float inv = rcp_ftz(wa + wb + wc);
   wa *= inv;
   wb *= inv;
   wc *= inv;
-  const float* A = verts + 12 * (size_t)s.box.z;
-  const float* B = verts + 12 * (size_t)s.box.w;
-  const float* C = verts + 12 * (size_t)s.vc.x;
-  float at[8];  // normal xyz, albedo rgb, metal, rough: vertex values 3 .. 10
+  // vertex values 3 .. 10 (normal, albedo, metal, rough) read as three float4 of each 48-byte
+  // record (16-byte aligned, checked on the host): normal.x is the w of the first, normal.yz and
+  // albedo.rg fill the second, albedo.b, metal and rough lead the third
+  const float4* A = (const float4*)(verts + 12 * (size_t)s.box.z);
+  const float4* B = (const float4*)(verts + 12 * (size_t)s.box.w);
+  const float4* C = (const float4*)(verts + 12 * (size_t)s.vc.x);
+  float at[8];
+  {
+    const float4 a0 = __ldg(A), a1 = __ldg(A + 1), a2 = __ldg(A + 2);
+    const float4 b0 = __ldg(B), b1 = __ldg(B + 1), b2 = __ldg(B + 2);
+    const float4 c0 = __ldg(C), c1 = __ldg(C + 1), c2 = __ldg(C + 2);
+    const float va[8] = {a0.w, a1.x, a1.y, a1.z, a1.w, a2.x, a2.y, a2.z};
+    const float vb[8] = {b0.w, b1.x, b1.y, b1.z, b1.w, b2.x, b2.y, b2.z};
+    const float vc[8] = {c0.w, c1.x, c1.y, c1.z, c1.w, c2.x, c2.y, c2.z};
 #pragma unroll
-  for (int q = 0; q < 8; ++q) at[q] = fmaf(wa, __ldg(A + 3 + q), fmaf(wb, __ldg(B + 3 + q), wc * __ldg(C + 3 + q)));
+    for (int q = 0; q < 8; ++q) at[q] = fmaf(wa, va[q], fmaf(wb, vb[q], wc * vc[q]));
+  }
   float3 n = f3(at[0], at[1], at[2]);
-  n = n * (1.0f / sqrtf(dot3(n, n)));
+  n = n * rsqrt_ftz(dot3(n, n));
   *rt0 = make_float4(at[3], at[4], at[5], at[6]);
   *rt1 = make_float4(n.x, n.y, n.z, at[7]);
   *dep = __uint_as_float((unsigned)(key >> 32));

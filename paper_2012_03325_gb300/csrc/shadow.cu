@@ -37,6 +37,13 @@ __device__ __forceinline__ float shadow_visibility(const float4* cam, float3 P, 
   int i0 = __float2int_rd(s), j0 = __float2int_rd(t);
   float thr = fmaf(-b1, z, z) - b0;  // lit when d >= z - b1 z - b0
   int lit = 0;
+  if (i0 >= 1 && i0 < S - 1 && j0 >= 1 && j0 < S - 1) {  // the whole block inside: no per-tap bounds
+    const float* p0 = map + (size_t)(j0 - 1) * S + (i0 - 1);
+#pragma unroll
+    for (int dy = 0; dy < 3; ++dy, p0 += S)
+      lit += (int)(__ldg(p0) >= thr) + (int)(__ldg(p0 + 1) >= thr) + (int)(__ldg(p0 + 2) >= thr);
+    return (float)lit * (1.0f / 9.0f);
+  }
 #pragma unroll
   for (int dy = -1; dy <= 1; ++dy) {
     int j = j0 + dy;
