@@ -60,7 +60,7 @@ __device__ __forceinline__ float shadow_visibility(const float4* cam, float3 P, 
 }
 
 template <int FMT, int HDR, bool LDR>
-__global__ void __launch_bounds__(256, 3)
+__global__ void __launch_bounds__(256, 4)
     k_shade_shadow(GbufDev g, CamDev cam, const float4* __restrict__ lights, int NL, IblDev ibl, ShadeDev p,
                    ShadowDev sh, void* hdr, long long hdr_pitch, uint8_t* ldr, long long ldr_pitch) {
   __shared__ float4 s_lights[2 * kShadowChunk];

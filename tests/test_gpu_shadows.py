@@ -78,7 +78,7 @@ def test_empty_maps_equal_the_unshadowed_oracle():
 
 
 def test_coloured_lights_over_several_chunks():
-    # 300 lights: three chunks of the 128-light staging; colours per channel
+    # 300 lights with colours per channel: every chunk takes the per-pixel colour loop
     inp = make_inputs("small", W=96, H=64, lights=300)
     lights = inp.scene.lights.copy()
     rng = np.random.default_rng(8)
@@ -89,6 +89,24 @@ def test_coloured_lights_over_several_chunks():
     g, _ = run(inp, maps, cams, ep.EPBR_SHADE_ALL, lights=lights)
     _, lo, hi = oracle_of(inp, maps, cams, ep.EPBR_SHADE_ALL, lights=lights)
     check_bounds(g, lo, hi)
+
+
+@pytest.mark.parametrize("flags", [ep.EPBR_SHADE_ALL, ep.EPBR_SHADE_DIRECT | ep.EPBR_SHADE_DIFFUSE_ONLY])
+def test_mixed_monochrome_and_coloured_chunks_ragged_view(flags):
+    # 37 lights, 16..31 coloured (a light set that mixes monochrome and coloured lights); 131 x 67
+    # leaves ragged tiles in both directions
+    inp = make_inputs("small", W=131, H=67, lights=37)
+    lights = inp.scene.lights.copy()
+    rng = np.random.default_rng(9)
+    lights[16:32, 4:7] = rng.uniform(0.2, 1.0, (16, 3)).astype(np.float32)
+    lights[:, 3] *= 0.3
+    maps, cams = synth.make_shadow_maps(inp.scene, 64)
+    g, _ = run(inp, maps, cams, flags, lights=lights)
+    out, lo, hi = oracle_of(inp, maps, cams, flags, lights=lights)
+    check_bounds(g, lo, hi)
+    unlit = oracle.shade(decoded(inp), oracle_camera(inp), lights,
+                         oracle_ibl(inp) if flags & ep.EPBR_SHADE_IBL else None, flags)
+    assert (out < unlit - 1e-6).any()
 
 
 def test_tonemapped_output_where_no_decision_is_tied():
