@@ -242,7 +242,8 @@ epbr_status epbr_ssao_workspace_size(const epbr_gbuffer* gbuffer,
  * S_k = P + radius * TBN * kernel[k] is projected to pixel (floor X, floor Y); its depth e_b is
  * fetched; the sample occludes by [e_b <= e_S - bias] * smoothstep(0, 1, radius / |e_P - e_b|).
  * Off-screen, behind-camera and background samples do not occlude.  AO = 1 - sum / K.  AO of a
- * background pixel is 1.  `ao` is DEVICE float, rows of `ao_pitch` bytes. */
+ * background pixel is 1.  `ao` is DEVICE float, rows of `ao_pitch` bytes.  EPBR_ERR_UNSUPPORTED
+ * when the depth plane spans more than 2^32 texels (height x pitch[3] / 4). */
 epbr_status epbr_ssao_raw(const epbr_gbuffer* gbuffer, const epbr_camera* camera,
                           const epbr_ssao_params* params, float* ao, int64_t ao_pitch,
                           void* stream);

@@ -1,7 +1,8 @@
 // Screen-space ambient occlusion (paper Sec. 5.2: normal-oriented hemisphere of Bavoil &
 // Sainz 2008, at half resolution, then a bilateral blur).
-//   k_ssao_raw   one thread per AO texel; the K kernel offsets sit in shared memory and the
-//                depth taps go through the read-only cache (per-texel math in ssao_core.cuh)
+//   k_ssao_raw   two AO texels per thread, the sample loop in packed FP32x2 arithmetic; the K
+//                kernel offsets sit in shared memory and the depth taps go through the
+//                read-only cache
 //   k_ssao_blur  one thread per AO texel; (2R+1)^2 depth-aware taps read from a shared-memory
 //                tile of AO values and depths with an R-texel halo
 #include "ssao_core.cuh"
@@ -12,16 +13,99 @@ namespace epbr {
 #define EPBR_SSAO_MIN_BLOCKS 4  // resident 256-thread blocks per SM the register budget targets
 #endif
 
+
+// Two AO texels per thread, (i, j) and (i, j + 8) of a 32 x 16 texel tile.  Per texel the
+// hemisphere frame is set up as in ssao_texel, then pre-scaled so that a sample k gives its pixel
+// coordinates as X / eS + W/2, Y / eS + H/2 with X = ix_scale S.x, Y = -iy_scale S.y, eS = -S.z,
+// each three FMAs of the kernel offset; the sample loop runs for both texels in packed FP32x2
+// arithmetic.  Depth taps are addressed by a 32-bit texel index (the depth plane holds at most
+// 2^32 texels of its pitch, checked on the host).
+struct SsaoRows {
+  float x[4], y[4], z[4];  // coefficients of (k.x, k.y, k.z, 1)
+};
+
 template <int FMT>
-__global__ void __launch_bounds__(256, EPBR_SSAO_MIN_BLOCKS) k_ssao_raw(GbufDev g, CamDev cam, SsaoDev p, float* __restrict__ ao,
-                                                  long long ao_pitch, int Wa, int Ha) {
+__device__ __forceinline__ float ssao_rows(const GbufDev& g, const CamDev& cam, const SsaoDev& p, int i, int j,
+                                           bool in, SsaoRows& r) {
+#pragma unroll
+  for (int q = 0; q < 4; ++q) r.x[q] = r.y[q] = r.z[q] = 0.0f;  // an unused half projects nowhere
+  if (!in) return __int_as_float(0x7f800000);
+  const int X0 = p.scale * i, Y0 = p.scale * j;
+  const float e = gb_depth(g, X0, Y0);
+  if (!is_surface(e)) return e;
+  const float3 P = e * view_ray(cam, X0, Y0);
+  const float3 n = rot_t(cam, gb_normal<FMT>(g, X0, Y0));
+  const float2 nz = __ldg(p.noise + ((j & 3) * 4 + (i & 3)));
+  const float3 rv = f3(nz.x, nz.y, 0.0f);
+  float3 t = rv - n * dot3(rv, n), b;
+  const float tt = dot3(t, t);
+  if (tt < 1e-8f) {  // |t| < 1e-4
+    onb(n, t, b);
+  } else {
+    t = t * rsqrt_ftz(tt);
+    b = cross3(n, t);
+  }
+  const float3 rt = t * p.radius, rb = b * p.radius, rn = n * p.radius;
+  const float sx = cam.ix_scale, sy = -cam.iy_scale;
+  r.x[0] = rt.x * sx, r.x[1] = rb.x * sx, r.x[2] = rn.x * sx, r.x[3] = P.x * sx;
+  r.y[0] = rt.y * sy, r.y[1] = rb.y * sy, r.y[2] = rn.y * sy, r.y[3] = P.y * sy;
+  r.z[0] = -rt.z, r.z[1] = -rb.z, r.z[2] = -rn.z, r.z[3] = -P.z;
+  return e;
+}
+
+__device__ __forceinline__ float2 pk(float a, float b) { return make_float2(a, b); }
+
+template <int FMT>
+__global__ void __launch_bounds__(256, EPBR_SSAO_MIN_BLOCKS)
+    k_ssao_raw(GbufDev g, CamDev cam, SsaoDev p, float* __restrict__ ao, long long ao_pitch, int Wa, int Ha) {
   __shared__ float4 s_kernel[kMaxSsaoSamples];
-  int tid = threadIdx.y * blockDim.x + threadIdx.x;
-  for (int k = tid; k < p.K; k += blockDim.x * blockDim.y) s_kernel[k] = __ldg(p.kernel + k);
+  const int tid = threadIdx.y * 32 + threadIdx.x;
+  for (int k = tid; k < p.K; k += 256) s_kernel[k] = __ldg(p.kernel + k);
+  const int i = blockIdx.x * 32 + threadIdx.x, j0 = blockIdx.y * 16 + threadIdx.y, j1 = j0 + 8;
+  const bool in0 = i < Wa && j0 < Ha, in1 = i < Wa && j1 < Ha;
+  SsaoRows a, b;
+  const float e0 = ssao_rows<FMT>(g, cam, p, i, j0, in0, a);
+  const float e1 = ssao_rows<FMT>(g, cam, p, i, j1, in1, b);
   __syncthreads();
-  int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y;
-  if (i >= Wa || j >= Ha) return;
-  ((float*)((char*)ao + (size_t)j * ao_pitch))[i] = ssao_texel<FMT>(g, cam, p, s_kernel, i, j).x;
+  const bool s0 = in0 && is_surface(e0), s1 = in1 && is_surface(e1);
+  if (s0 || s1) {
+    const float2 tx = pk(a.x[0], b.x[0]), bx = pk(a.x[1], b.x[1]), nx = pk(a.x[2], b.x[2]), px = pk(a.x[3], b.x[3]);
+    const float2 ty = pk(a.y[0], b.y[0]), by = pk(a.y[1], b.y[1]), ny = pk(a.y[2], b.y[2]), py = pk(a.y[3], b.y[3]);
+    const float2 tz = pk(a.z[0], b.z[0]), bz = pk(a.z[1], b.z[1]), nz = pk(a.z[2], b.z[2]), pz = pk(a.z[3], b.z[3]);
+    const float2 hw = pk(0.5f * cam.W, 0.5f * cam.W), hh = pk(0.5f * cam.H, 0.5f * cam.H);
+    const float2 m2 = pk(-2.0f, -2.0f), c3 = pk(3.0f, 3.0f);
+    const float* dep = (const float*)g.rt[3];
+    const unsigned dp = (unsigned)(g.pitch[3] >> 2);
+    const unsigned W = (unsigned)cam.W, H = (unsigned)cam.H;
+    float2 occ = pk(0.0f, 0.0f);
+    // branch-free as in ssao_texel: an invalid sample reads texel 0 and is masked out
+#pragma unroll(kSsaoUnroll)
+    for (int k = 0; k < p.K; ++k) {
+      const float4 ks = s_kernel[k];
+      const float2 KX = pk(ks.x, ks.x), KY = pk(ks.y, ks.y), KZ = pk(ks.z, ks.z);
+      const float2 X = __ffma2_rn(tx, KX, __ffma2_rn(bx, KY, __ffma2_rn(nx, KZ, px)));
+      const float2 Y = __ffma2_rn(ty, KX, __ffma2_rn(by, KY, __ffma2_rn(ny, KZ, py)));
+      const float2 Z = __ffma2_rn(tz, KX, __ffma2_rn(bz, KY, __ffma2_rn(nz, KZ, pz)));  // eS
+      const float2 inv = pk(rcp_ftz(Z.x), rcp_ftz(Z.y));
+      const float2 fx = __ffma2_rn(X, inv, hw), fy = __ffma2_rn(Y, inv, hh);
+      const int ix0 = __float2int_rd(fx.x), iy0 = __float2int_rd(fy.x);
+      const int ix1 = __float2int_rd(fx.y), iy1 = __float2int_rd(fy.y);
+      const bool v0 = Z.x > 0.0f && (unsigned)ix0 < W && (unsigned)iy0 < H;
+      const bool v1 = Z.y > 0.0f && (unsigned)ix1 < W && (unsigned)iy1 < H;
+      const float eb0 = __ldg(dep + (v0 ? (unsigned)iy0 * dp + (unsigned)ix0 : 0u));
+      const float eb1 = __ldg(dep + (v1 ? (unsigned)iy1 * dp + (unsigned)ix1 : 0u));
+      const bool h0 = v0 && eb0 > 0.0f && eb0 <= Z.x - p.bias;
+      const bool h1 = v1 && eb1 > 0.0f && eb1 <= Z.y - p.bias;
+      const float2 x = pk(__saturatef(p.radius * rcp_ftz(fabsf(e0 - eb0))),
+                          __saturatef(p.radius * rcp_ftz(fabsf(e1 - eb1))));
+      const float2 sm = __fmul2_rn(__fmul2_rn(x, x), __ffma2_rn(m2, x, c3));  // smoothstep
+      occ = __fadd2_rn(occ, pk(h0 ? sm.x : 0.0f, h1 ? sm.y : 0.0f));
+    }
+    if (s0) ((float*)((char*)ao + (size_t)j0 * ao_pitch))[i] = fmaf(-occ.x, p.inv_k, 1.0f);
+    if (s1) ((float*)((char*)ao + (size_t)j1 * ao_pitch))[i] = fmaf(-occ.y, p.inv_k, 1.0f);
+  }
+  if (in0 && !s0) ((float*)((char*)ao + (size_t)j0 * ao_pitch))[i] = 1.0f;
+  if (in1 && !s1) ((float*)((char*)ao + (size_t)j1 * ao_pitch))[i] = 1.0f;
 }
 
 // Blur tile: 32x8 AO texels plus a halo of R <= 8 texels, AO values and the depths of their
@@ -113,7 +197,9 @@ extern "C" epbr_status epbr_ssao_raw(const epbr_gbuffer* g, const epbr_camera* c
   int Wa, Ha;
   ao_dims(g, p, &Wa, &Ha);
   if ((st = check_ao_buffer(ao, ao_pitch, Wa, "ssao_raw"))) return st;
-  dim3 blk(32, 8), grd((Wa + 31) / 32, (Ha + 7) / 8);
+  if ((uint64_t)g->height * (uint64_t)(g->pitch[3] / 4) > 0xffffffffull)
+    return fail(EPBR_ERR_UNSUPPORTED, "ssao_raw: depth plane of more than 2^32 texels (height x pitch / 4)");
+  dim3 blk(32, 8), grd((Wa + 31) / 32, (Ha + 15) / 16);
   GbufDev gd = make_gbuf(*g);
   CamDev cd = make_cam(*cam);
   SsaoDev sd = make_ssao(*p);

@@ -1,5 +1,6 @@
 // SSAO per-texel arithmetic (paper Sec. 5.2, normal-oriented hemisphere of Bavoil & Sainz
-// 2008) shared by the per-view kernels (ssao.cu) and the fused multi-view kernel (batch.cu).
+// 2008): ssao_texel is the one-texel form of the fused multi-view kernel (batch.cu), which the
+// per-view k_ssao_raw (ssao.cu) restates for two texels in packed arithmetic; the blur is shared.
 #pragma once
 
 #include "epbr_internal.cuh"
