@@ -1,0 +1,192 @@
+"""Host-side argument checks of the C ABI: every call below is rejected during validation, before
+anything is enqueued, so it needs no GPU.  The device pointers are fake, 256-byte aligned
+addresses that are never dereferenced; on a machine with a CUDA device the module is skipped so
+that a check that wrongly passed could never hand such a pointer to a kernel."""
+import ctypes as C
+
+import pytest
+
+from paper_2012_03325_gb300 import _ffi as F
+
+try:
+    import torch
+    _HAS_GPU = torch.cuda.is_available()
+except ImportError:  # pragma: no cover
+    _HAS_GPU = False
+
+pytestmark = pytest.mark.skipif(_HAS_GPU, reason="fake device pointers: host-only checks")
+
+FAKE = 1 << 40  # never dereferenced
+INVALID, UNSUPPORTED = F.EPBR_ERR_INVALID_ARG, F.EPBR_ERR_UNSUPPORTED
+
+
+@pytest.fixture(scope="module")
+def lib():
+    return F.load()
+
+
+def last_error(lib):
+    return lib.epbr_last_error().decode()
+
+
+def gbuf(W=64, H=32, fmt=F.EPBR_GBUFFER_FP32):
+    g = F.epbr_gbuffer()
+    g.format, g.width, g.height = fmt, W, H
+    bpp = [16, 16, 0, 4] if fmt == F.EPBR_GBUFFER_FP32 else [4, 4, 2, 4]
+    for i in range(4):
+        g.rt[i] = FAKE + (i << 32) if bpp[i] else None
+        g.pitch[i] = bpp[i] * W
+    return g
+
+
+def camera(W=64, H=32):
+    c = F.epbr_camera()
+    for i in range(16):
+        c.view_to_world[i] = 1.0 if i % 5 == 0 else 0.0
+    c.fov_y, c.width, c.height = 1.0, W, H
+    return c
+
+
+def ssao(K=32, scale=2):
+    p = F.epbr_ssao_params()
+    p.num_samples, p.scale, p.radius, p.bias = K, scale, 0.5, 0.025
+    p.blur_radius, p.sigma_s, p.sigma_z = 3, 2.0, 0.1
+    p.kernel, p.noise = FAKE, FAKE
+    return p
+
+
+def test_ssao_size_and_workspace(lib):
+    g, p = gbuf(257, 129), ssao()
+    w, h, n = C.c_int32(), C.c_int32(), C.c_size_t()
+    assert lib.epbr_ssao_size(C.byref(g), C.byref(p), C.byref(w), C.byref(h)) == F.EPBR_OK
+    assert (w.value, h.value) == (129, 65)
+    assert lib.epbr_ssao_workspace_size(C.byref(g), C.byref(p), C.byref(n)) == F.EPBR_OK
+    assert n.value == 129 * 65 * 4
+    p1 = ssao(scale=1)
+    assert lib.epbr_ssao_size(C.byref(g), C.byref(p1), C.byref(w), C.byref(h)) == F.EPBR_OK
+    assert (w.value, h.value) == (257, 129)
+
+
+def test_ssao_raw_rejects_a_depth_plane_over_2_32_texels(lib):
+    # 32768 rows of 131073 texels' pitch: the 32-bit depth-tap index would wrap
+    W, H = 1024, 32768
+    g = gbuf(W, H)
+    g.pitch[3] = 4 * 131073
+    p, cam = ssao(), camera(W, H)
+    st = lib.epbr_ssao_raw(C.byref(g), C.byref(cam), C.byref(p), FAKE, (W // 2) * 4, None)
+    assert st == UNSUPPORTED and "2^32" in last_error(lib)
+
+
+@pytest.mark.parametrize("field,value", [("num_samples", 0), ("num_samples", 257), ("scale", 3), ("radius", 0.0),
+                                         ("bias", -1.0), ("sigma_z", 0.0), ("blur_radius", 9), ("kernel", FAKE + 4),
+                                         ("noise", 0)])
+def test_ssao_parameter_checks(lib, field, value):
+    g, cam, p = gbuf(), camera(), ssao()
+    setattr(p, field, value)
+    assert lib.epbr_ssao_raw(C.byref(g), C.byref(cam), C.byref(p), FAKE, 32 * 4, None) == INVALID
+
+
+def test_ssao_output_checks(lib):
+    g, cam, p = gbuf(), camera(), ssao()
+    assert lib.epbr_ssao_raw(C.byref(g), C.byref(cam), C.byref(p), FAKE + 2, 32 * 4, None) == INVALID
+    assert lib.epbr_ssao_raw(C.byref(g), C.byref(cam), C.byref(p), FAKE, 31 * 4, None) == INVALID
+    assert lib.epbr_ssao_raw(C.byref(g), C.byref(cam), C.byref(p), None, 32 * 4, None) == INVALID
+
+
+@pytest.mark.parametrize("mutate", [
+    lambda g: setattr(g, "width", 0),
+    lambda g: setattr(g, "height", 40000),
+    lambda g: setattr(g, "format", 7),
+    lambda g: g.rt.__setitem__(3, None),
+    lambda g: g.pitch.__setitem__(1, 16 * 63),
+    lambda g: g.pitch.__setitem__(3, 4 * 64 + 2),
+    lambda g: g.rt.__setitem__(1, FAKE + 8),
+])
+def test_gbuffer_checks(lib, mutate):
+    g, cam, p = gbuf(), camera(), ssao()
+    mutate(g)
+    assert lib.epbr_ssao_raw(C.byref(g), C.byref(cam), C.byref(p), FAKE, 32 * 4, None) == INVALID
+
+
+def test_camera_checks(lib):
+    g, p = gbuf(), ssao()
+    for mutate in (lambda c: setattr(c, "width", 65), lambda c: setattr(c, "fov_y", 0.0),
+                   lambda c: c.view_to_world.__setitem__(3, float("nan"))):
+        cam = camera()
+        mutate(cam)
+        assert lib.epbr_ssao_raw(C.byref(g), C.byref(cam), C.byref(p), FAKE, 32 * 4, None) == INVALID
+
+
+def shade_call(lib, g=None, cam=None, lights=FAKE, nl=4, flags=F.EPBR_SHADE_DIRECT, hdr=FAKE, fmt=F.EPBR_HDR_RGBA32F,
+               hdr_pitch=64 * 16, tp=None, ldr=None, ldr_pitch=64 * 4, shadows=None):
+    g = g or gbuf()
+    cam = cam or camera()
+    sp = F.epbr_shade_params(flags, 2, None, 0)
+    if shadows is not None:
+        return lib.epbr_shade_shadows(C.byref(g), C.byref(cam), lights, nl, None, C.byref(sp), C.byref(shadows), hdr,
+                                      fmt, hdr_pitch, C.byref(tp) if tp else None, ldr, ldr_pitch, None)
+    if ldr is not None:
+        return lib.epbr_shade_tonemap(C.byref(g), C.byref(cam), lights, nl, None, C.byref(sp), hdr, fmt, hdr_pitch,
+                                      C.byref(tp) if tp else None, ldr, ldr_pitch, None)
+    return lib.epbr_shade(C.byref(g), C.byref(cam), lights, nl, None, C.byref(sp), hdr, fmt, hdr_pitch, None)
+
+
+def test_shade_checks(lib):
+    assert shade_call(lib, flags=0x10) == INVALID                     # unknown flag bit
+    assert shade_call(lib, flags=F.EPBR_SHADE_ALL) == INVALID         # IBL requested, no lighting set
+    assert shade_call(lib, nl=-1) == INVALID
+    assert shade_call(lib, nl=65537) == INVALID
+    assert shade_call(lib, lights=None) == INVALID                    # NL > 0 without lights
+    assert shade_call(lib, lights=FAKE + 8) == INVALID                # lights not 16-byte aligned
+    assert shade_call(lib, fmt=5) == INVALID
+    assert shade_call(lib, hdr=FAKE + 4) == INVALID
+    assert shade_call(lib, hdr_pitch=63 * 16) == INVALID
+    tp = F.epbr_tonemap_params(1.0, 9)
+    assert shade_call(lib, ldr=FAKE, tp=tp) == INVALID                # unknown tone-map operator
+    assert shade_call(lib, ldr=FAKE + 2, tp=F.epbr_tonemap_params(1.0, 0)) == INVALID
+    assert shade_call(lib, ldr=FAKE, tp=F.epbr_tonemap_params(-1.0, 0)) == INVALID
+
+
+def test_shadow_checks(lib):
+    def shadows(**kw):
+        s = F.epbr_shadows()
+        s.maps, s.cameras, s.size, s.bias_const, s.bias_slope = FAKE, FAKE, 64, 0.02, 0.01
+        for k, v in kw.items():
+            setattr(s, k, v)
+        return s
+    for s in (shadows(size=0), shadows(size=8193), shadows(bias_const=-0.1), shadows(bias_slope=float("inf")),
+              shadows(maps=FAKE + 2), shadows(cameras=FAKE + 4), shadows(maps=0)):
+        assert shade_call(lib, shadows=s) == INVALID
+    assert "shadows" in last_error(lib)
+
+
+def test_bloom_checks(lib):
+    def params(**kw):
+        p = F.epbr_bloom_params(1.0, 0.1, 2.0, 4, 6)
+        for k, v in kw.items():
+            setattr(p, k, v)
+        return p
+    n = C.c_size_t()
+    assert lib.epbr_bloom_workspace_size(640, 360, C.byref(params()), C.byref(n)) == F.EPBR_OK and n.value > 0
+    for p in (params(levels=1), params(sigma=0.0), params(radius=-1), params(threshold=float("nan"))):
+        assert lib.epbr_bloom_workspace_size(640, 360, C.byref(p), C.byref(n)) == INVALID
+    assert lib.epbr_bloom_workspace_size(0, 360, C.byref(params()), C.byref(n)) == INVALID
+
+
+def test_raster_checks(lib):
+    a, b = C.c_size_t(), C.c_size_t()
+    assert lib.epbr_raster_workspace_size(1000, 64, 32, C.byref(a)) == F.EPBR_OK
+    assert lib.epbr_raster_workspace_size(2000, 64, 32, C.byref(b)) == F.EPBR_OK and b.value > a.value
+    assert lib.epbr_raster_workspace_size(-1, 64, 32, C.byref(a)) == INVALID
+    g, cam = gbuf(), camera()
+    mesh = F.epbr_mesh(FAKE, 3, FAKE, 1)
+    ws = lib.epbr_raster_workspace_size(1, 64, 32, C.byref(a))
+    assert ws == F.EPBR_OK
+    call = lambda m, near=0.1, ws_ptr=FAKE, ws_bytes=a.value, out=g: lib.epbr_raster_gbuffer(
+        C.byref(m), C.byref(cam), near, C.byref(out), None, 0, ws_ptr, ws_bytes, None)
+    assert call(mesh, near=0.0) == INVALID
+    assert call(F.epbr_mesh(FAKE + 4, 3, FAKE, 1)) == INVALID          # vertices not 16-byte aligned
+    assert call(F.epbr_mesh(FAKE, -1, FAKE, 1)) == INVALID
+    assert call(mesh, ws_bytes=a.value - 1) == INVALID
+    assert call(mesh, ws_ptr=FAKE + 16) == INVALID                      # workspace not 256-byte aligned
+    assert call(mesh, out=gbuf(fmt=F.EPBR_GBUFFER_COMPACT)) == INVALID
