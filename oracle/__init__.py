@@ -103,6 +103,7 @@ def lib():
             L.or_shadow_vis.argtypes = [C.POINTER(Shadows), C.c_int, dp, dp]
             L.or_shadow_vis.restype = None
             L.or_raster.argtypes = [dp, C.c_int, ip, C.c_long, C.POINTER(Camera), C.c_double, dp, ip]
+            L.or_surfels.argtypes = [dp, C.c_long, C.POINTER(Camera), C.c_double, C.c_double, dp, dp]
             L.or_edl.argtypes = [dp, C.c_int, C.c_int, C.POINTER(EdlParams), dp, C.c_int, dp]
             L.or_bloom.argtypes = [dp, C.c_int, C.c_int, C.POINTER(BloomParams), dp, dp, dp]
             _lib = L
@@ -340,6 +341,17 @@ def raster(verts, tris, cam: Camera, near: float = 0.05):
     assert lib().or_raster(_dp(v), v.shape[0], t.ctypes.data_as(C.POINTER(C.c_int)), t.shape[0], C.byref(cam), near,
                            _dp(gb), ids.ctypes.data_as(C.POINTER(C.c_int))) == 0
     return gb, ids
+
+
+def surfels(records, cam: Camera, near: float = 0.05, tol: float = 0.01):
+    """G-buffer pass of surfel rendering (Sec. 4.3; readings in epbr_oracle.c).  records: (N, 16)
+    centre, semi-axis a, normal, semi-axis b, tangent, metal, albedo, rough (FP32-representable).
+    Returns (gb (H, W, 9) decoded G-buffer, weight (H, W) number of blended surfels)."""
+    r = _f64(records).reshape(-1, 16)
+    gb = np.zeros((cam.H, cam.W, 9))
+    w = np.zeros((cam.H, cam.W))
+    assert lib().or_surfels(_dp(r), r.shape[0], C.byref(cam), near, tol, _dp(gb), _dp(w)) == 0
+    return gb, w
 
 
 def tonemap(hdr, exposure: float = 1.0, op: int = 0):

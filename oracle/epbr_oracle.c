@@ -23,7 +23,9 @@
  *   - the G-buffer pass of mesh rendering (Sec. 4.1): triangle rasterisation with a depth test
  *     and perspective-correct attribute interpolation;
  *   - bloom (Sec. 5.3): bright map, an image pyramid of up to six levels, a Gaussian blur of
- *     every level from the second one up, the blurred levels added onto the image.
+ *     every level from the second one up, the blurred levels added onto the image;
+ *   - surfel splatting into the G-buffer (Sec. 4.3): elliptical disks on their (normal, tangent,
+ *     bitangent) basis, the surfels within a small depth window of the nearest one blended.
  * Conventions the paper leaves open (equirect mapping, sample sets, SSAO constants, rounding)
  * are stated beside the code that uses them.
  *
@@ -1269,5 +1271,220 @@ int or_raster(const double* verts, int V, const int* tris, long T, const or_came
     if (ids) ids[p] = (int)tr;
   }
   free(best);
+  return 0;
+}
+
+/* ------------------------------------------------------------------------------------------ */
+/* surfel splatting into the G-buffer (Sec. 4.3)                                              */
+/* ------------------------------------------------------------------------------------------ */
+/* A surfel is an oriented elliptical disk.  Record of 16 values: centre p.xyz, semi-axis a (along
+ * the tangent), normal n.xyz, semi-axis b (along the bitangent), tangent t.xyz, metal,
+ * albedo.rgb, rough.  The paper draws each surfel as a rectangle on its (normal, tangent,
+ * bitangent) basis, discards the fragments outside the ellipse, and lets surfels that overlap
+ * within a small depth distance accumulate their attributes and a weight, the composing pass
+ * dividing by the weight.  Readings:
+ *   - the surfel's frame in view space: centre c = R^T (p - eye), unit normal n^ = R^T n / |R^T n|,
+ *     unit tangent t^ = the part of R^T t orthogonal to n^, normalised, bitangent b^ = n^ x t^.  A
+ *     surfel is dropped when its normal or orthogonalised tangent is zero, a semi-axis is not a
+ *     positive finite number, or its nearest possible point is nearer than `near` (eye depth of c
+ *     minus (a + b) below near);
+ *   - the ray through a pixel centre, (u_x, u_y, -1) at eye depth 1 with u_x = ((x + 1/2) / hw - 1)
+ *     / k_x and u_y = (1 - (y + 1/2) / hh) / k_y, meets the surfel's plane at eye depth
+ *     s = (n^ . c) / (n^ . u); the pixel is covered when 0 < s < inf and the hit point's
+ *     coordinates u, v along t^ and b^ satisfy u^2 / a^2 + v^2 / b^2 <= 1 (both faces count);
+ *   - the pixel's depth is the smallest s over the covering surfels; every covering surfel with
+ *     s <= (that depth) * (1 + tol) adds its albedo, world-space unit normal, metal and rough with
+ *     weight 1; the G-buffer holds the weighted means (the summed normal renormalised, a zero sum
+ *     left zero) and the smallest depth; a pixel no surfel covers is background (zeros, depth
+ *     +inf), and its weight is 0.
+ * The decisions (which surfels survive, which pixels they cover, the smallest depth, the depth
+ * window) are evaluated in FP32, each product, sum, quotient and square root rounded, in the
+ * order written here; the sums and means are FP64.  The pixel box searched per surfel is the
+ * bounding box of its rectangle's projected corners (FP64) widened by two pixels. */
+typedef struct {
+  float c[3], n[3], t[3], b[3];
+  float nc, ia2, ib2;
+  double nw[3];
+  double box[4]; /* x0, y0, x1, y1 */
+  int ok;
+} or_surfel;
+
+static float dot3f(const float* a, const float* b) {
+  float t0 = a[0] * b[0];
+  float t1 = a[1] * b[1];
+  float s = t0 + t1;
+  float t2 = a[2] * b[2];
+  return s + t2;
+}
+
+static or_surfel surfel_setup(const double* rec, const float* axes /* 3 view axes in world space */,
+                              const float* eye, float near, float kx, float ky, float hw, float hh) {
+  or_surfel o;
+  memset(&o, 0, sizeof(o));
+  float p[3] = {(float)rec[0], (float)rec[1], (float)rec[2]};
+  float nw[3] = {(float)rec[4], (float)rec[5], (float)rec[6]};
+  float tw[3] = {(float)rec[8], (float)rec[9], (float)rec[10]};
+  float a = (float)rec[3], b = (float)rec[7];
+  float d[3] = {p[0] - eye[0], p[1] - eye[1], p[2] - eye[2]};
+  float nv[3], tv[3];
+  for (int k = 0; k < 3; ++k) {
+    o.c[k] = dot3f(axes + 3 * k, d);
+    nv[k] = dot3f(axes + 3 * k, nw);
+    tv[k] = dot3f(axes + 3 * k, tw);
+  }
+  if (!(a > 0.0f) || !(b > 0.0f) || !(a < INFINITY) || !(b < INFINITY)) return o;
+  float nn = dot3f(nv, nv);
+  if (!(nn > 0.0f) || !(nn < INFINITY)) return o;
+  float inv = 1.0f / sqrtf(nn);
+  for (int k = 0; k < 3; ++k) o.n[k] = nv[k] * inv;
+  float dt = dot3f(tv, o.n);
+  float tp[3];
+  for (int k = 0; k < 3; ++k) {
+    float m = o.n[k] * dt;
+    tp[k] = tv[k] - m;
+  }
+  float tt = dot3f(tp, tp);
+  if (!(tt > 0.0f) || !(tt < INFINITY)) return o;
+  float invt = 1.0f / sqrtf(tt);
+  for (int k = 0; k < 3; ++k) o.t[k] = tp[k] * invt;
+  {
+    float m0, m1;
+    m0 = o.n[1] * o.t[2]; m1 = o.n[2] * o.t[1]; o.b[0] = m0 - m1;
+    m0 = o.n[2] * o.t[0]; m1 = o.n[0] * o.t[2]; o.b[1] = m0 - m1;
+    m0 = o.n[0] * o.t[1]; m1 = o.n[1] * o.t[0]; o.b[2] = m0 - m1;
+  }
+  float ec = -o.c[2];
+  float reach = a + b;
+  if (!(ec - reach >= near)) return o;
+  o.nc = dot3f(o.n, o.c);
+  float a2 = a * a, b2 = b * b;
+  o.ia2 = 1.0f / a2;
+  o.ib2 = 1.0f / b2;
+  /* world-space unit normal for the sums */
+  double ln = sqrt(rec[4] * rec[4] + rec[5] * rec[5] + rec[6] * rec[6]);
+  for (int k = 0; k < 3; ++k) o.nw[k] = rec[4 + k] / ln;
+  /* pixel box: projected corners c +- a t^ +- b b^ (FP64), widened by two pixels */
+  double xmin = INFINITY, xmax = -INFINITY, ymin = INFINITY, ymax = -INFINITY;
+  for (int sa = -1; sa <= 1; sa += 2)
+    for (int sb = -1; sb <= 1; sb += 2) {
+      double q[3];
+      for (int k = 0; k < 3; ++k) q[k] = (double)o.c[k] + sa * (double)a * o.t[k] + sb * (double)b * o.b[k];
+      double e = -q[2];
+      double X = hw * (1.0 + q[0] / e * kx), Y = hh * (1.0 - q[1] / e * ky);
+      if (X < xmin) xmin = X;
+      if (X > xmax) xmax = X;
+      if (Y < ymin) ymin = Y;
+      if (Y > ymax) ymax = Y;
+    }
+  o.box[0] = floor(xmin - 0.5) - 2.0;
+  o.box[1] = floor(ymin - 0.5) - 2.0;
+  o.box[2] = ceil(xmax - 0.5) + 2.0;
+  o.box[3] = ceil(ymax - 0.5) + 2.0;
+  o.ok = 1;
+  return o;
+}
+
+/* eye depth at which the ray (ux, uy, -1) meets the surfel inside its ellipse, else 0 */
+static float surfel_hit(const or_surfel* s, float ux, float uy) {
+  float t0 = s->n[0] * ux;
+  float t1 = s->n[1] * uy;
+  float nd = t0 + t1;
+  nd = nd - s->n[2];
+  float sd = s->nc / nd;
+  if (!(sd > 0.0f) || !(sd < INFINITY)) return 0.0f;
+  float q[3];
+  q[0] = sd * ux;
+  q[0] = q[0] - s->c[0];
+  q[1] = sd * uy;
+  q[1] = q[1] - s->c[1];
+  q[2] = -sd - s->c[2];
+  float u = dot3f(q, s->t), v = dot3f(q, s->b);
+  float pu = u * u, pv = v * v;
+  pu = pu * s->ia2;
+  pv = pv * s->ib2;
+  float e = pu + pv;
+  return e <= 1.0f ? sd : 0.0f;
+}
+
+/* recs: N*16.  gb: W*H*9 as or_raster; weight: W*H (NULL allowed). */
+int or_surfels(const double* recs, long N, const or_camera* cam, double near, double tol, double* gb, double* weight) {
+  int W = cam->W, H = cam->H;
+  double t = tan(0.5 * cam->fov_y);
+  float ky = (float)(1.0 / t), kx = (float)((double)H / ((double)W * t));
+  float hw = (float)(0.5 * W), hh = (float)(0.5 * H), nearf = (float)near;
+  float f = 1.0f + (float)tol;
+  float axes[9], eye[3];
+  for (int c = 0; c < 3; ++c) {
+    for (int i = 0; i < 3; ++i) axes[3 * c + i] = (float)cam->v2w[4 * c + i];
+    eye[c] = (float)cam->v2w[12 + c];
+  }
+  float* ux = (float*)malloc(sizeof(float) * W);
+  float* uy = (float*)malloc(sizeof(float) * H);
+  for (int x = 0; x < W; ++x) {
+    float q = ((float)x + 0.5f) / hw;
+    q = q - 1.0f;
+    ux[x] = q / kx;
+  }
+  for (int y = 0; y < H; ++y) {
+    float q = ((float)y + 0.5f) / hh;
+    q = 1.0f - q;
+    uy[y] = q / ky;
+  }
+  float* emin = (float*)malloc(sizeof(float) * (size_t)W * H);
+  double* acc = (double*)calloc((size_t)W * H * 9, sizeof(double));
+  for (long p = 0; p < (long)W * H; ++p) emin[p] = INFINITY;
+  or_surfel* S = (or_surfel*)malloc(sizeof(or_surfel) * (N > 0 ? N : 1));
+  for (long i = 0; i < N; ++i) S[i] = surfel_setup(recs + 16 * i, axes, eye, nearf, kx, ky, hw, hh);
+  for (int pass = 0; pass < 2; ++pass)
+    for (long i = 0; i < N; ++i) {
+      const or_surfel* s = &S[i];
+      if (!s->ok) continue;
+      long x0 = s->box[0] < 0 ? 0 : (long)s->box[0], y0 = s->box[1] < 0 ? 0 : (long)s->box[1];
+      long x1 = s->box[2] > W - 1 ? W - 1 : (long)s->box[2], y1 = s->box[3] > H - 1 ? H - 1 : (long)s->box[3];
+      for (long y = y0; y <= y1; ++y)
+        for (long x = x0; x <= x1; ++x) {
+          float sd = surfel_hit(s, ux[x], uy[y]);
+          if (sd == 0.0f) continue;
+          long p = y * W + x;
+          if (pass == 0) {
+            if (sd < emin[p]) emin[p] = sd;
+            continue;
+          }
+          float thr = emin[p] * f;
+          if (!(sd <= thr)) continue;
+          const double* r = recs + 16 * i;
+          double* a = acc + 9 * p;
+          a[0] += r[12];
+          a[1] += r[13];
+          a[2] += r[14];
+          a[3] += r[11];
+          a[4] += s->nw[0];
+          a[5] += s->nw[1];
+          a[6] += s->nw[2];
+          a[7] += r[15];
+          a[8] += 1.0;
+        }
+    }
+  for (long p = 0; p < (long)W * H; ++p) {
+    double* o = gb + 9 * p;
+    const double* a = acc + 9 * p;
+    if (weight) weight[p] = a[8];
+    if (a[8] == 0.0) {
+      for (int q = 0; q < 8; ++q) o[q] = 0.0;
+      o[8] = INFINITY;
+      continue;
+    }
+    for (int q = 0; q < 4; ++q) o[q] = a[q] / a[8];
+    double n[3] = {a[4], a[5], a[6]};
+    double ln = sqrt(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
+    for (int k = 0; k < 3; ++k) o[4 + k] = ln > 0.0 ? n[k] / ln : 0.0;
+    o[7] = a[7] / a[8];
+    o[8] = emin[p];
+  }
+  free(S);
+  free(acc);
+  free(emin);
+  free(uy);
+  free(ux);
   return 0;
 }

@@ -439,6 +439,56 @@ def make_mesh_scene(scene: "Scene", n_lat: int = 16, n_lon: int = 32, ground_cel
     return np.concatenate(verts).astype(np.float32), np.concatenate(tris).astype(np.int32)
 
 
+def make_surfel_scene(scene: "Scene", seed: int = 0, per_sphere: int = 2000, ground: int = 200000,
+                      overlap: float = 1.2):
+    """Surfel version of the analytic scene for the G-buffer pass of surfel rendering: per sphere
+    `per_sphere` surfels at uniformly random surface points, on the ground square `ground` surfels
+    on a jittered grid; normal = the surface normal, tangent random in the tangent plane, semi-axes
+    a = overlap * spacing * U(0.8, 1.2) and b = a * U(0.6, 1.0) with spacing = sqrt(area / count),
+    so that neighbours overlap; the object's material with a small albedo jitter (U(-0.05, 0.05)).
+    Returns records (N, 16) float32: centre, a, normal, b, tangent, metal, albedo, rough."""
+    g = np.random.Generator(np.random.PCG64(seed))
+    out = []
+
+    def frame(n):
+        # a random unit tangent perpendicular to each unit normal
+        r = g.normal(size=n.shape)
+        t = r - n * np.sum(r * n, axis=1, keepdims=True)
+        return t / np.linalg.norm(t, axis=1, keepdims=True)
+
+    def records(P, n, spacing, k_mat):
+        m = len(P)
+        r = np.zeros((m, 16))
+        a = overlap * spacing * g.uniform(0.8, 1.2, m)
+        r[:, 0:3], r[:, 3] = P, a
+        r[:, 4:7], r[:, 7] = n, a * g.uniform(0.6, 1.0, m)
+        r[:, 8:11] = frame(n)
+        r[:, 11] = scene.metal[k_mat]
+        r[:, 12:15] = np.clip(scene.albedo[k_mat] + g.uniform(-0.05, 0.05, (m, 3)), 0.0, 1.0)
+        r[:, 15] = scene.rough[k_mat]
+        return r
+
+    for sidx in range(len(scene.radii)):
+        n = g.normal(size=(per_sphere, 3))
+        n /= np.linalg.norm(n, axis=1, keepdims=True)
+        R = scene.radii[sidx]
+        spacing = math.sqrt(4.0 * math.pi * R * R / per_sphere)
+        out.append(records(scene.centers[sidx] + R * n, n, spacing, sidx))
+    if ground > 0:
+        side = max(1, int(round(math.sqrt(ground))))
+        h = scene.ground_half
+        spacing = 2.0 * h / side
+        cells = (np.arange(side) + 0.5) * spacing - h
+        X, Z = np.meshgrid(cells, cells, indexing="ij")
+        P = np.zeros((side * side, 3))
+        P[:, 0] = X.reshape(-1) + g.uniform(-0.3, 0.3, side * side) * spacing
+        P[:, 2] = Z.reshape(-1) + g.uniform(-0.3, 0.3, side * side) * spacing
+        n = np.zeros_like(P)
+        n[:, 1] = 1.0
+        out.append(records(P, n, spacing, -1))
+    return np.concatenate(out).astype(np.float32)
+
+
 def make_point_cloud_gbuffer(seed: int, width: int, height: int, fill: float = 0.7) -> GBuffer:
     """Synthetic point-cloud G-buffer for eye-dome lighting: colour and depth only (normals 0):
     several depth layers (rough surfaces at depths 2..40 with per-pixel jitter) covering `fill` of
