@@ -49,6 +49,9 @@ def parse():
     ap.add_argument("--mesh", action="store_true",
                     help="produce the G-buffer on the device every frame by rasterising the scene's triangle mesh "
                          "(Sec. 4.1) instead of uploading it; the mesh stays resident")
+    ap.add_argument("--surfels", action="store_true",
+                    help="produce the G-buffer on the device every frame by splatting the scene's surfels "
+                         "(Sec. 4.3) instead of uploading it; the surfels stay resident")
     ap.add_argument("--shadows", action="store_true",
                     help="shade with per-light shadow maps and 3x3 PCF (Sec. 5.1); maps stay resident")
     ap.add_argument("--bloom", action="store_true",
@@ -131,6 +134,8 @@ FLOP_SHADOW = 40         # lit pair with shadows: light-view transform (18), 1/z
 SHADOW = {"size": 512, "fov_deg": 90.0, "bias_const": 0.02, "bias_slope": 0.01}
 MESH = {"n_lat": 16, "n_lon": 32, "ground_cells": 64, "near": 0.05}
 RASTER_LAUNCHES = 7  # key reset, set-up, three scan kernels, coverage, resolve
+SURFELS = {"per_sphere": 4000, "ground": 400000, "overlap": 1.2, "seed": 11, "near": 0.05, "tolerance": 0.01}
+SURFEL_LAUNCHES = 10  # depth and sum resets, pixel rays, set-up, three scan kernels, two coverage passes, resolve
 
 
 def compose_flops(sc, g, n_lights) -> tuple[float, dict]:
@@ -268,7 +273,7 @@ def sources_sha(files=SHADE_SOURCES):
 # CPU oracle baseline
 # ------------------------------------------------------------------------------------------
 def oracle_frame_rate(c, sc, g, env, k, nz, seconds: float, oracle_ibl=None, threads: int = 0, bloom=False,
-                      shadow_maps=None, mesh=None):
+                      shadow_maps=None, mesh=None, surfels=None):
     """The FP64 oracle's per-frame path (blurred SSAO, compose, tone map) on horizontal bands of
     the frame until `seconds` elapse; returns (Mpixels/s, cores, sample description).  With
     `bloom`, the oracle's bloom of one whole frame (it needs the whole image) is timed as well and
@@ -318,6 +323,14 @@ def oracle_frame_rate(c, sc, g, env, k, nz, seconds: float, oracle_ibl=None, thr
         rate = 1.0 / (dt / px_done + tr / (W * H)) / 1e6
         return rate, cores, (f"{px_done} px in {px_done // W} full-width rows ({dt:.1f} s wall) + the G-buffer pass "
                              f"of one {W}x{H} frame from {len(mesh[1])} triangles ({tr:.2f} s, one thread)")
+    if surfels is not None:  # the oracle's G-buffer pass of one whole frame, one thread
+        tr = time.perf_counter()
+        oracle.surfels(surfels, oracle.camera(sc.camera_array(), float(np.float32(sc.fov_y)), W, H), SURFELS["near"],
+                       SURFELS["tolerance"])
+        tr = time.perf_counter() - tr
+        rate = 1.0 / (dt / px_done + tr / (W * H)) / 1e6
+        return rate, cores, (f"{px_done} px in {px_done // W} full-width rows ({dt:.1f} s wall) + the G-buffer pass "
+                             f"of one {W}x{H} frame from {len(surfels)} surfels ({tr:.2f} s, one thread)")
     if bloom:
         frame = synth.make_bloom_field(1, W, H)
         tb = time.perf_counter()
@@ -385,10 +398,18 @@ def run_gpu(args):
         host_rts = [g.rt0, g.rt1, None, g.depth]
     dev_rts = [t(a) if a is not None else None for a in host_rts]
     gb = ep.GBuffer.compact(*dev_rts) if compact else ep.GBuffer.fp32(dev_rts[0], dev_rts[1], dev_rts[3])
-    mesh = ws_raster = None
+    mesh = ws_raster = surf = ws_surf = srec = None
+    produced = args.mesh or args.surfels  # the G-buffer is made on the device every frame
+    if args.mesh and args.surfels:
+        raise SystemExit("--mesh and --surfels are two producers of the same G-buffer: pick one")
+    if produced and compact:
+        raise SystemExit("--mesh and --surfels write the FP32 G-buffer; use them with an FP32 workload")
+    if args.surfels:
+        srec = synth.make_surfel_scene(sc, SURFELS["seed"], SURFELS["per_sphere"], SURFELS["ground"],
+                                       SURFELS["overlap"])
+        surf = ep.Surfels(t(srec))
+        ws_surf = torch.empty(ep.epbr_surfel_workspace_size(len(srec), W, H) + 256, dtype=torch.uint8, device=dev)
     if args.mesh:
-        if compact:
-            raise SystemExit("--mesh writes the FP32 G-buffer; use it with an FP32 workload")
         mv, mt = synth.make_mesh_scene(sc, MESH["n_lat"], MESH["n_lon"], MESH["ground_cells"])
         mesh = ep.Mesh(t(mv), t(mt))
         ws_raster = torch.empty(ep.epbr_raster_workspace_size(len(mt), W, H) + 256, dtype=torch.uint8, device=dev)
@@ -461,19 +482,23 @@ def run_gpu(args):
         if record:
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             a.record(stream)
-        ep.epbr_raster_gbuffer(mesh, cam, MESH["near"], g_, None, ws_raster, stream=stream)
+        if args.mesh:
+            ep.epbr_raster_gbuffer(mesh, cam, MESH["near"], g_, None, ws_raster, stream=stream)
+        else:
+            ep.epbr_surfel_gbuffer(surf, cam, SURFELS["near"], SURFELS["tolerance"], g_, None, ws_surf, stream=stream)
         if record:
             b.record(stream)
             ev_raster.append((a, b))
 
     def step(record=False):
-        if args.mesh:
+        if produced:
             raster(gb, record)
         ep.epbr_ssao_raw(gb, cam, sp, ao_raw, stream=stream)
         ep.epbr_ssao_blur(gb, sp, ao_raw, ao, stream=stream)
         compose(gb, shp, hdr, ldr, lights, record)
 
-    launches_per_step = 3 + (BLOOM_LAUNCHES if args.bloom else 0) + (RASTER_LAUNCHES if args.mesh else 0)
+    launches_per_step = 3 + (BLOOM_LAUNCHES if args.bloom else 0) + (RASTER_LAUNCHES if args.mesh else 0) + \
+        (SURFEL_LAUNCHES if args.surfels else 0)
     with torch.cuda.stream(stream):
         for _ in range(max(3, args.warmup)):
             step()
@@ -509,7 +534,7 @@ def run_gpu(args):
     pinned = [torch.from_numpy(np.ascontiguousarray(a)).pin_memory() if a is not None else None for a in host_rts]
     lights_h = torch.from_numpy(sc.lights).pin_memory()
     ldr_h = [torch.empty(H, W, 4, dtype=torch.uint8).pin_memory() for _ in range(2)]
-    h2d = (0 if args.mesh else sum(p.numel() * p.element_size() for p in pinned if p is not None)) + \
+    h2d = (0 if produced else sum(p.numel() * p.element_size() for p in pinned if p is not None)) + \
         lights_h.numel() * 4
     d2h = ldr_h[0].numel()
 
@@ -534,7 +559,7 @@ def run_gpu(args):
         go = ev()
         go.record(s_up)
         ups = []
-        for k_, (p_, d_) in enumerate((p_, d_) for p_, d_ in zip(pinned, b["rts"]) if p_ is not None and not args.mesh):
+        for k_, (p_, d_) in enumerate((p_, d_) for p_, d_ in zip(pinned, b["rts"]) if p_ is not None and not produced):
             sk = s_planes[k_ % len(s_planes)]
             sk.wait_event(go)
             with torch.cuda.stream(sk):
@@ -553,7 +578,7 @@ def run_gpu(args):
             stream.wait_event(done_dn[i % 2])  # the set's previous image has been downloaded
         with torch.cuda.stream(stream):
             flush.zero_()  # L2 flush inside the timed window
-            if args.mesh:
+            if produced:
                 raster(b["gb"])
             ep.epbr_ssao_raw(b["gb"], cam, sp, b["ao_raw"], stream=stream)
             ep.epbr_ssao_blur(b["gb"], sp, b["ao_raw"], b["ao"], stream=stream)
@@ -583,7 +608,12 @@ def run_gpu(args):
     torch.cuda.synchronize()
     e2e_total = max_over_ranks(e_start.elapsed_time(e_end), dev)
     # the result of the last frame equals the device-only frame's (same inputs)
-    assert torch.equal(ldr_h[(args.steps - 1) % 2], ldr.cpu()), "end-to-end frame differs from the device frame"
+    if args.surfels:  # the blended attributes are float atomics: their order, and so the last bits, vary
+        diff = (ldr_h[(args.steps - 1) % 2].int() - ldr.cpu().int()).abs()
+        assert int(diff.max()) <= 1 and float((diff > 0).float().mean()) < 1e-3, \
+            "end-to-end frame differs from the device frame"
+    else:
+        assert torch.equal(ldr_h[(args.steps - 1) % 2], ldr.cpu()), "end-to-end frame differs from the device frame"
 
     if rank != 0:
         if world > 1:
@@ -594,7 +624,7 @@ def run_gpu(args):
     clocks = clk.summary()
     props = torch.cuda.get_device_properties(dev)
     sms = props.multi_processor_count
-    if args.mesh:  # count the work on the rasterised G-buffer the frames shade
+    if produced:  # count the work on the device-made G-buffer the frames shade
         g_cnt = synth.GBuffer(dev_rts[0].cpu().numpy(), dev_rts[1].cpu().numpy(), dev_rts[3].cpu().numpy())
     else:
         g_cnt = g
@@ -625,7 +655,9 @@ def run_gpu(args):
                                                                 "scene), generated by the ray caster")}
                                                if args.shadows else {}),
                                             **({"gbuffer": "fp32 36 B/px, rasterised on the device every frame from "
-                                                           "the resident triangle mesh"} if args.mesh else {})}),
+                                                           "the resident triangle mesh"} if args.mesh else {}),
+                                            **({"gbuffer": "fp32 36 B/px, splatted on the device every frame from "
+                                                           "the resident surfels"} if args.surfels else {})}),
             "roofline": roofline,
             "e2e": {"value": e2e_value, "unit": "Mpixels/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                     "how": "pinned host G-buffer + lights uploaded and RGBA8 downloaded every step; frames "
@@ -639,6 +671,11 @@ def run_gpu(args):
                           "launches": RASTER_LAUNCHES, **MESH}
         line["e2e"]["how"] = ("mesh resident; lights uploaded and RGBA8 downloaded every step; frames pipelined "
                               "over upload, compute (raster + SSAO + compose) and download streams")
+    if args.surfels:
+        line["surfels"] = {"ms": statistics.mean(a.elapsed_time(b) for a, b in ev_raster), "surfels": len(srec),
+                           "launches": SURFEL_LAUNCHES, **SURFELS}
+        line["e2e"]["how"] = ("surfels resident; lights uploaded and RGBA8 downloaded every step; frames pipelined "
+                              "over upload, compute (surfel splatting + SSAO + compose) and download streams")
     if args.bloom:
         bloom_ms = statistics.mean(a.elapsed_time(b) for a, b in ev_bloom)
         hdr_bytes = 8 if compact else 16
@@ -653,7 +690,8 @@ def run_gpu(args):
         rate, cores, sample = oracle_frame_rate(dict(c, name=name), sc, g, env, k, nz, args.cpu_seconds,
                                                 bloom=args.bloom,
                                                 shadow_maps=(maps, cams) if args.shadows else None,
-                                                mesh=(mv, mt) if args.mesh else None)
+                                                mesh=(mv, mt) if args.mesh else None,
+                                                surfels=srec if args.surfels else None)
         line["cpu_baseline"] = {"value": rate, "unit": "Mpixels/s", "cores": cores, "kind": "oracle",
                                 "sample": sample}
     print(json.dumps(line), flush=True)

@@ -352,6 +352,41 @@ epbr_status epbr_raster_gbuffer(const epbr_mesh* mesh, const epbr_camera* camera
                                 size_t workspace_bytes, void* stream);
 
 /* ---------------------------------------------------------------------------------------- */
+/* The G-buffer pass of surfel rendering (Sec. 4.3): elliptical disks splatted and blended   */
+/* ---------------------------------------------------------------------------------------- */
+typedef struct epbr_surfels {
+  const float* records;  /* DEVICE float[num_surfels * 16], 16-byte aligned: centre xyz, semi-axis a
+                            (along the tangent), normal xyz, semi-axis b (along the bitangent),
+                            tangent xyz, metal, albedo rgb, rough (world space) */
+  int32_t num_surfels;   /* 0 .. 2^28 */
+  int32_t reserved;
+} epbr_surfels;
+
+/* Device workspace epbr_surfel_gbuffer needs: 40 B per pixel (nearest depth, nine attribute
+ * sums), 4 B per pixel column and row (pixel rays), 96 B and 8 B per surfel (set-up, task
+ * offsets), each part 256-byte aligned. */
+epbr_status epbr_surfel_workspace_size(int32_t num_surfels, int32_t width, int32_t height, size_t* bytes);
+
+/* Writes the FP32 G-buffer `out` (rt[0] albedo + metal, rt[1] normal + rough, rt[3] eye depth;
+ * background: zeros and depth +inf) of the surfels seen by `camera`.  A surfel is the ellipse of
+ * semi-axes a, b in the plane through its centre with its normal, a along the tangent made
+ * orthogonal to the normal, b along the bitangent normal x tangent; both faces are drawn.  A
+ * surfel is dropped when its normal or orthogonalised tangent is zero, a semi-axis is not a
+ * positive finite number, or (eye depth of its centre) - (a + b) < near_depth.  Pixel (x, y) is
+ * covered when the ray through its centre meets the surfel's plane at eye depth s > 0 inside the
+ * ellipse.  The pixel's depth is the smallest s; every covering surfel with
+ * s <= depth * (1 + depth_tolerance) adds its albedo, unit normal, metal and rough with weight 1,
+ * and the G-buffer holds their means (the normal renormalised).  These decisions are evaluated in
+ * FP32 with every product, sum, quotient and square root rounded, in a fixed order, so they are
+ * reproducible bit for bit; the sums are float atomics (their order varies).  `weight` (DEVICE
+ * float, NULL allowed, rows of weight_pitch bytes) receives the number of blended surfels, 0 for
+ * background.  `workspace` DEVICE, 256-byte aligned, at least epbr_surfel_workspace_size bytes.
+ * Stream-ordered; no allocation. */
+epbr_status epbr_surfel_gbuffer(const epbr_surfels* surfels, const epbr_camera* camera, float near_depth,
+                                float depth_tolerance, const epbr_gbuffer* out, float* weight,
+                                int64_t weight_pitch, void* workspace, size_t workspace_bytes, void* stream);
+
+/* ---------------------------------------------------------------------------------------- */
 /* Eye-dome lighting for point clouds (Sec. 4.2; Boucheny 2009): shading from depth alone    */
 /* ---------------------------------------------------------------------------------------- */
 typedef struct epbr_edl_params {

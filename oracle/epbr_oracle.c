@@ -1288,10 +1288,14 @@ int or_raster(const double* verts, int V, const int* tris, long T, const or_came
  *     surfel is dropped when its normal or orthogonalised tangent is zero, a semi-axis is not a
  *     positive finite number, or its nearest possible point is nearer than `near` (eye depth of c
  *     minus (a + b) below near);
- *   - the ray through a pixel centre, (u_x, u_y, -1) at eye depth 1 with u_x = ((x + 1/2) / hw - 1)
- *     / k_x and u_y = (1 - (y + 1/2) / hh) / k_y, meets the surfel's plane at eye depth
- *     s = (n^ . c) / (n^ . u); the pixel is covered when 0 < s < inf and the hit point's
- *     coordinates u, v along t^ and b^ satisfy u^2 / a^2 + v^2 / b^2 <= 1 (both faces count);
+ *   - the ray through a pixel centre, d = (u_x, u_y, -1) at eye depth 1 with
+ *     u_x = ((x + 1/2) / hw - 1) / k_x and u_y = (1 - (y + 1/2) / hh) / k_y, meets the surfel's
+ *     plane at eye depth s = (n^ . c) / (n^ . d); the pixel is covered when 0 < s < inf and the
+ *     hit point's coordinates u = s (d . t^) - c . t^ and v = s (d . b^) - c . b^ satisfy
+ *     u^2 / a^2 + v^2 / b^2 <= 1 (both faces count).  The test is evaluated multiplied through by
+ *     (n^ . d)^2, without the quotient: U = (n^ . c)(d . t^) - (n^ . d)(c . t^), V likewise with
+ *     b^, covered when (n^ . c)(n^ . d) > 0 and U^2 / a^2 + V^2 / b^2 <= (n^ . d)^2; s itself is
+ *     formed only for a covered pixel;
  *   - the pixel's depth is the smallest s over the covering surfels; every covering surfel with
  *     s <= (that depth) * (1 + tol) adds its albedo, world-space unit normal, metal and rough with
  *     weight 1; the G-buffer holds the weighted means (the summed normal renormalised, a zero sum
@@ -1303,7 +1307,7 @@ int or_raster(const double* verts, int V, const int* tris, long T, const or_came
  * bounding box of its rectangle's projected corners (FP64) widened by two pixels. */
 typedef struct {
   float c[3], n[3], t[3], b[3];
-  float nc, ia2, ib2;
+  float nc, ct, cb, ia2, ib2;
   double nw[3];
   double box[4]; /* x0, y0, x1, y1 */
   int ok;
@@ -1357,6 +1361,8 @@ static or_surfel surfel_setup(const double* rec, const float* axes /* 3 view axe
   float reach = a + b;
   if (!(ec - reach >= near)) return o;
   o.nc = dot3f(o.n, o.c);
+  o.ct = dot3f(o.c, o.t);
+  o.cb = dot3f(o.c, o.b);
   float a2 = a * a, b2 = b * b;
   o.ia2 = 1.0f / a2;
   o.ib2 = 1.0f / b2;
@@ -1386,24 +1392,22 @@ static or_surfel surfel_setup(const double* rec, const float* axes /* 3 view axe
 
 /* eye depth at which the ray (ux, uy, -1) meets the surfel inside its ellipse, else 0 */
 static float surfel_hit(const or_surfel* s, float ux, float uy) {
-  float t0 = s->n[0] * ux;
-  float t1 = s->n[1] * uy;
-  float nd = t0 + t1;
-  nd = nd - s->n[2];
-  float sd = s->nc / nd;
-  if (!(sd > 0.0f) || !(sd < INFINITY)) return 0.0f;
-  float q[3];
-  q[0] = sd * ux;
-  q[0] = q[0] - s->c[0];
-  q[1] = sd * uy;
-  q[1] = q[1] - s->c[1];
-  q[2] = -sd - s->c[2];
-  float u = dot3f(q, s->t), v = dot3f(q, s->b);
-  float pu = u * u, pv = v * v;
+  float m0, m1;
+  m0 = s->n[0] * ux; m1 = s->n[1] * uy; float nd = m0 + m1; nd = nd - s->n[2]; /* n^ . d */
+  m0 = s->t[0] * ux; m1 = s->t[1] * uy; float dt = m0 + m1; dt = dt - s->t[2]; /* d . t^ */
+  m0 = s->b[0] * ux; m1 = s->b[1] * uy; float db = m0 + m1; db = db - s->b[2]; /* d . b^ */
+  float sign = s->nc * nd;
+  if (!(sign > 0.0f)) return 0.0f;
+  m0 = s->nc * dt; m1 = nd * s->ct; float U = m0 - m1;
+  m0 = s->nc * db; m1 = nd * s->cb; float V = m0 - m1;
+  float pu = U * U, pv = V * V;
   pu = pu * s->ia2;
   pv = pv * s->ib2;
   float e = pu + pv;
-  return e <= 1.0f ? sd : 0.0f;
+  float n2 = nd * nd;
+  if (!(e <= n2)) return 0.0f;
+  float sd = s->nc / nd;
+  return (sd > 0.0f && sd < INFINITY) ? sd : 0.0f;
 }
 
 /* recs: N*16.  gb: W*H*9 as or_raster; weight: W*H (NULL allowed). */

@@ -317,6 +317,34 @@ def epbr_raster_gbuffer(mesh: Mesh, cam: F.epbr_camera, near: float, out: GBuffe
                                      ws.numel() - (_aligned(ws) - ws.data_ptr()), _stream(stream)))
 
 
+class Surfels:
+    """Owns the surfel (N, 16) float32 tensor and its epbr_surfels."""
+
+    def __init__(self, records: torch.Tensor):
+        _dev(records, torch.float32, "records")
+        if records.dim() != 2 or records.shape[1] != 16 or not records.is_contiguous():
+            raise ValueError("surfel records must be a contiguous (N, 16) tensor")
+        self.tensors = (records,)
+        self.struct = F.epbr_surfels(records.data_ptr(), records.shape[0], 0)
+
+
+def epbr_surfel_workspace_size(num_surfels: int, W: int, H: int) -> int:
+    n = C.c_size_t()
+    _check(lib().epbr_surfel_workspace_size(num_surfels, W, H, C.byref(n)))
+    return n.value
+
+
+def epbr_surfel_gbuffer(surfels: Surfels, cam: F.epbr_camera, near: float, tolerance: float, out: GBuffer,
+                        weight: torch.Tensor | None = None, workspace: torch.Tensor | None = None, stream=None):
+    W, H = out.struct.width, out.struct.height
+    need = epbr_surfel_workspace_size(surfels.struct.num_surfels, W, H)
+    ws = workspace if workspace is not None else _workspace(need, surfels.tensors[0].device)
+    wp = _dev(weight, torch.float32, "weight") if weight is not None else None
+    _check(lib().epbr_surfel_gbuffer(C.byref(surfels.struct), C.byref(cam), near, tolerance, C.byref(out.struct), wp,
+                                     _pitch(weight, 1) if weight is not None else 0, _aligned(ws),
+                                     ws.numel() - (_aligned(ws) - ws.data_ptr()), _stream(stream)))
+
+
 # ------------------------------------------------------------------------------------------
 # eye-dome lighting for point clouds (Sec. 4.2)
 # ------------------------------------------------------------------------------------------

@@ -88,6 +88,10 @@ class epbr_mesh(C.Structure):
                 ("num_triangles", C.c_int32)]
 
 
+class epbr_surfels(C.Structure):
+    _fields_ = [("records", C.c_void_p), ("num_surfels", C.c_int32), ("reserved", C.c_int32)]
+
+
 class epbr_edl_params(C.Structure):
     _fields_ = [("strength", C.c_float), ("radius", C.c_int32), ("directions", C.c_int32)]
 
@@ -162,6 +166,9 @@ PROTOTYPES = {
     "epbr_tonemap": [vp, i32, i32, i32, i64, P(epbr_tonemap_params), vp, i64, vp],
     "epbr_raster_workspace_size": [i32, i32, i32, P(sz)],
     "epbr_raster_gbuffer": [P(epbr_mesh), P(epbr_camera), C.c_float, P(epbr_gbuffer), vp, i64, vp, sz, vp],
+    "epbr_surfel_workspace_size": [i32, i32, i32, P(sz)],
+    "epbr_surfel_gbuffer": [P(epbr_surfels), P(epbr_camera), C.c_float, C.c_float, P(epbr_gbuffer), vp, i64, vp, sz,
+                            vp],
     "epbr_edl": [P(epbr_gbuffer), P(epbr_edl_params), vp, i64, i32, vp, i32, i64, P(epbr_tonemap_params), vp, i64,
                  vp],
     "epbr_shade_shadows": [P(epbr_gbuffer), P(epbr_camera), vp, i32, P(epbr_ibl), P(epbr_shade_params),

@@ -18,6 +18,11 @@ epbr_status ok();
 epbr_status check_launch(const char* what);
 int num_sms();
 
+// Exclusive int64 prefix sum of data[0 .. n) in place (raster.cu); sums needs
+// scan_num_blocks(n) + 1 entries and receives the total at sums[scan_num_blocks(n)].
+long long scan_num_blocks(long long n);
+void launch_exclusive_scan(long long* data, long long n, long long* sums, cudaStream_t s);
+
 constexpr float kPi = 3.14159265358979323846f;
 constexpr float kInvPi = 0.318309886183790671538f;
 constexpr float kInv2Pi = 0.159154943091895335769f;

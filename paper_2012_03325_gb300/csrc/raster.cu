@@ -194,6 +194,15 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_add(long long* __restrict
     if (base + k < n) data[base + k] += add;
 }
 
+long long scan_num_blocks(long long n) { return (n + kScanBlock - 1) / kScanBlock; }
+
+void launch_exclusive_scan(long long* data, long long n, long long* sums, cudaStream_t s) {
+  const long long nb = scan_num_blocks(n);
+  k_scan_block<<<(unsigned)nb, kScanThreads, 0, s>>>(data, n, sums);
+  k_scan_sums<<<1, kScanThreads, 0, s>>>(sums, (int)nb);
+  k_scan_add<<<(unsigned)nb, kScanThreads, 0, s>>>(data, n, sums);
+}
+
 // ---- coverage --------------------------------------------------------------------------------
 constexpr int kCoverThreads = 256;
 
@@ -339,7 +348,7 @@ static RasterLayout raster_layout(long long T, int W, int H) {
   l.offsets = off;
   off = align256(off + sizeof(long long) * (size_t)(T + 1));
   l.sums = off;
-  long long nb = (T + kScanBlock - 1) / kScanBlock;
+  long long nb = scan_num_blocks(T);
   off = align256(off + sizeof(long long) * (size_t)(nb + 1));
   l.bytes = off;
   return l;
@@ -399,10 +408,8 @@ extern "C" epbr_status epbr_raster_gbuffer(const epbr_mesh* mesh, const epbr_cam
   if (T > 0) {
     k_raster_setup<<<(T + 255) / 256, 256, 0, s>>>(mesh->vertices, mesh->num_vertices, mesh->triangles, T, rc, setup,
                                                    offsets);
-    const long long nb = (T + kScanBlock - 1) / kScanBlock;
-    k_scan_block<<<(unsigned)nb, kScanThreads, 0, s>>>(offsets, T, sums);
-    k_scan_sums<<<1, kScanThreads, 0, s>>>(sums, (int)nb);
-    k_scan_add<<<(unsigned)nb, kScanThreads, 0, s>>>(offsets, T, sums);
+    const long long nb = scan_num_blocks(T);
+    launch_exclusive_scan(offsets, T, sums, s);
     k_raster_cover<<<num_sms() * 8, kCoverThreads, 0, s>>>(setup, offsets, T, sums + nb, W, keys);
   }
   dim3 blk(32, 8), grd((W + 31) / 32, (H + 7) / 8);

@@ -44,6 +44,7 @@ def test_binding_covers_every_symbol_and_matches_struct_sizes():
     assert ctypes.sizeof(_ffi.epbr_shadows) == 32
     assert ctypes.sizeof(_ffi.epbr_edl_params) == 12
     assert ctypes.sizeof(_ffi.epbr_mesh) == 32
+    assert ctypes.sizeof(_ffi.epbr_surfels) == 16
     assert ctypes.sizeof(_ffi.epbr_gbuffer) == 16 + 32 + 32
     assert ctypes.sizeof(_ffi.epbr_ssao_params) == 48
     assert ctypes.sizeof(_ffi.epbr_ibl) == 8 + 8 + 8 + 8 + 16 * 8 + 16 * 4 * 2

@@ -190,3 +190,27 @@ def test_raster_checks(lib):
     assert call(mesh, ws_bytes=a.value - 1) == INVALID
     assert call(mesh, ws_ptr=FAKE + 16) == INVALID                      # workspace not 256-byte aligned
     assert call(mesh, out=gbuf(fmt=F.EPBR_GBUFFER_COMPACT)) == INVALID
+
+
+def test_surfel_checks(lib):
+    a, b = C.c_size_t(), C.c_size_t()
+    assert lib.epbr_surfel_workspace_size(1000, 64, 32, C.byref(a)) == F.EPBR_OK
+    assert lib.epbr_surfel_workspace_size(2000, 64, 32, C.byref(b)) == F.EPBR_OK and b.value > a.value
+    assert lib.epbr_surfel_workspace_size(-1, 64, 32, C.byref(a)) == INVALID
+    assert lib.epbr_surfel_workspace_size(1, 64, 0, C.byref(a)) == INVALID
+    assert lib.epbr_surfel_workspace_size(1, 64, 32, C.byref(a)) == F.EPBR_OK
+    g, cam = gbuf(), camera()
+    call = lambda s, near=0.1, tol=0.01, ws_ptr=FAKE, ws_bytes=a.value, out=g, wp=None, wpitch=0: \
+        lib.epbr_surfel_gbuffer(C.byref(s), C.byref(cam), near, tol, C.byref(out), wp, wpitch, ws_ptr, ws_bytes, None)
+    ok = F.epbr_surfels(FAKE, 1, 0)
+    assert call(ok, near=0.0) == INVALID
+    assert call(ok, tol=-0.5) == INVALID
+    assert call(ok, tol=float("nan")) == INVALID
+    assert call(F.epbr_surfels(FAKE + 8, 1, 0)) == INVALID            # records not 16-byte aligned
+    assert call(F.epbr_surfels(None, 1, 0)) == INVALID
+    assert call(F.epbr_surfels(FAKE, -1, 0)) == INVALID
+    assert call(ok, ws_bytes=a.value - 1) == INVALID
+    assert call(ok, ws_ptr=FAKE + 64) == INVALID                        # workspace not 256-byte aligned
+    assert call(ok, out=gbuf(fmt=F.EPBR_GBUFFER_COMPACT)) == INVALID
+    assert call(ok, wp=FAKE + 2, wpitch=64 * 4) == INVALID              # weight misaligned
+    assert call(ok, wp=FAKE, wpitch=63 * 4) == INVALID                  # weight pitch too small
