@@ -5,6 +5,8 @@
 //                read-only cache
 //   k_ssao_blur  one thread per AO texel; (2R+1)^2 depth-aware taps read from a shared-memory
 //                tile of AO values and depths with an R-texel halo
+//   k_ssao_blur2 the same for R = 3 with two vertically adjacent texels per thread sharing their
+//                tap rows
 #include "ssao_core.cuh"
 
 namespace epbr {
@@ -141,6 +143,66 @@ __global__ void __launch_bounds__(kBlurBX* kBlurBY) k_ssao_blur(GbufDev g, SsaoD
       ssao_blur_texel(p, &s_ao[threadIdx.y + R][threadIdx.x + R], &s_e[threadIdx.y + R][threadIdx.x + R], kBlurTW);
 }
 
+// The 7x7 blur (R = 3) with two vertically adjacent AO texels per thread, (i, 2 ty') and
+// (i, 2 ty' + 1) of a 32 x 16 texel tile: the (AO, depth) pairs of the tile and its 3-texel halo sit
+// in shared memory as float2, and the 8 rows x 7 columns a thread reads serve both texels (6 of the
+// 7 rows are shared), 56 loads instead of 2 x 2 x 49.  Each texel's sum runs over the taps in the
+// order of ssao_blur_texel_r, so the result is that function's bit for bit.
+constexpr int kBlur2R = 3, kBlur2TW = kBlurBX + 2 * kBlur2R, kBlur2TH = 2 * kBlurBY + 2 * kBlur2R;
+
+template <int FMT>
+__global__ void __launch_bounds__(kBlurBX* kBlurBY) k_ssao_blur2(GbufDev g, SsaoDev p, const float* __restrict__ in,
+                                                                 long long in_pitch, float* __restrict__ out,
+                                                                 long long out_pitch, int Wa, int Ha) {
+  __shared__ float2 s_ae[kBlur2TH][kBlur2TW];
+  const int i0 = blockIdx.x * kBlurBX - kBlur2R, j0 = blockIdx.y * (2 * kBlurBY) - kBlur2R;
+  const float inf = __int_as_float(0x7f800000);
+  for (int q = threadIdx.y * kBlurBX + threadIdx.x; q < kBlur2TW * kBlur2TH; q += kBlurBX * kBlurBY) {
+    const int ty = q / kBlur2TW, tx = q - ty * kBlur2TW;
+    const int qi = i0 + tx, qj = j0 + ty;
+    float a = 0.0f, e = inf;
+    if (qi >= 0 && qi < Wa && qj >= 0 && qj < Ha) {
+      a = __ldg((const float*)((const char*)in + (size_t)qj * in_pitch) + qi);
+      e = gb_depth(g, p.scale * qi, p.scale * qj);
+    }
+    s_ae[ty][tx] = make_float2(a, e);
+  }
+  __syncthreads();
+  const int i = blockIdx.x * kBlurBX + threadIdx.x, ja = blockIdx.y * (2 * kBlurBY) + 2 * threadIdx.y, jb = ja + 1;
+  if (i >= Wa || ja >= Ha) return;
+  // tile row 2 ty' + k holds texel row ja - 3 + k: texel a reads k = 0..6 (dy = k - 3), b k = 1..7
+  const float epa = s_ae[2 * threadIdx.y + kBlur2R][threadIdx.x + kBlur2R].y;
+  const float epb = s_ae[2 * threadIdx.y + kBlur2R + 1][threadIdx.x + kBlur2R].y;
+  const bool sa = is_surface(epa), sb = jb < Ha && is_surface(epb);
+  const float ks = p.blur_ks;
+  const float kza = -1.4426950408889634f * rcp_ftz(p.sigma_z * epa);
+  const float kzb = -1.4426950408889634f * rcp_ftz(p.sigma_z * epb);
+  float na = 0.0f, da = 0.0f, nb = 0.0f, db = 0.0f;
+#pragma unroll
+  for (int k = 0; k < 2 * kBlur2R + 2; ++k) {
+    const float2* row = &s_ae[2 * threadIdx.y + k][threadIdx.x];
+#pragma unroll
+    for (int c = 0; c < 2 * kBlur2R + 1; ++c) {
+      const float2 v = row[c];
+      const int dx = c - kBlur2R;
+      if (k <= 2 * kBlur2R) {
+        const int dy = k - kBlur2R;
+        const float w = ex2_ftz(fmaf(fabsf(v.y - epa), kza, (float)(dx * dx + dy * dy) * ks));
+        na = fmaf(w, v.x, na);
+        da += w;
+      }
+      if (k >= 1) {
+        const int dy = k - 1 - kBlur2R;
+        const float w = ex2_ftz(fmaf(fabsf(v.y - epb), kzb, (float)(dx * dx + dy * dy) * ks));
+        nb = fmaf(w, v.x, nb);
+        db += w;
+      }
+    }
+  }
+  ((float*)((char*)out + (size_t)ja * out_pitch))[i] = sa ? na * rcp_ftz(da) : 1.0f;
+  if (jb < Ha) ((float*)((char*)out + (size_t)jb * out_pitch))[i] = sb ? nb * rcp_ftz(db) : 1.0f;
+}
+
 static epbr_status validate_ssao(const epbr_ssao_params* p) {
   if (!p) return fail(EPBR_ERR_INVALID_ARG, "ssao params is NULL");
   if (p->num_samples < 1 || p->num_samples > kMaxSsaoSamples)
@@ -226,10 +288,17 @@ extern "C" epbr_status epbr_ssao_blur(const epbr_gbuffer* g, const epbr_ssao_par
   GbufDev gd = make_gbuf(*g);
   SsaoDev sd = make_ssao(*p);
   cudaStream_t s = (cudaStream_t)stream;
-  if (g->format == EPBR_GBUFFER_FP32)
+  if (p->blur_radius == kBlur2R) {  // the 7x7 blur: two texels per thread
+    dim3 grd2((Wa + kBlurBX - 1) / kBlurBX, (Ha + 2 * kBlurBY - 1) / (2 * kBlurBY));
+    if (g->format == EPBR_GBUFFER_FP32)
+      k_ssao_blur2<EPBR_GBUFFER_FP32><<<grd2, blk, 0, s>>>(gd, sd, in, in_pitch, out, out_pitch, Wa, Ha);
+    else
+      k_ssao_blur2<EPBR_GBUFFER_COMPACT><<<grd2, blk, 0, s>>>(gd, sd, in, in_pitch, out, out_pitch, Wa, Ha);
+  } else if (g->format == EPBR_GBUFFER_FP32) {
     k_ssao_blur<EPBR_GBUFFER_FP32><<<grd, blk, 0, s>>>(gd, sd, in, in_pitch, out, out_pitch, Wa, Ha);
-  else
+  } else {
     k_ssao_blur<EPBR_GBUFFER_COMPACT><<<grd, blk, 0, s>>>(gd, sd, in, in_pitch, out, out_pitch, Wa, Ha);
+  }
   if ((st = check_launch("k_ssao_blur"))) return st;
   return ok();
 }
