@@ -490,11 +490,21 @@ def run_gpu(args):
             b.record(stream)
             ev_raster.append((a, b))
 
+    ev_ssao = []  # (start, after raw, after blur) per timed step
+
     def step(record=False):
         if produced:
             raster(gb, record)
+        if record:
+            e3 = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+            e3[0].record(stream)
         ep.epbr_ssao_raw(gb, cam, sp, ao_raw, stream=stream)
+        if record:
+            e3[1].record(stream)
         ep.epbr_ssao_blur(gb, sp, ao_raw, ao, stream=stream)
+        if record:
+            e3[2].record(stream)
+            ev_ssao.append(e3)
         compose(gb, shp, hdr, ldr, lights, record)
 
     launches_per_step = 3 + (BLOOM_LAUNCHES if args.bloom else 0) + (RASTER_LAUNCHES if args.mesh else 0) + \
@@ -524,6 +534,8 @@ def run_gpu(args):
     step_ms = [a.elapsed_time(b) for a, b in ev]
     total_ms = sum(step_ms)
     shade_ms = statistics.mean(a.elapsed_time(b) for a, b in ev_shade)
+    ssao_raw_ms = statistics.mean(e[0].elapsed_time(e[1]) for e in ev_ssao)
+    ssao_blur_ms = statistics.mean(e[1].elapsed_time(e[2]) for e in ev_ssao)
     total_ms = max_over_ranks(total_ms, dev)
     if world > 1:
         dist.barrier()
@@ -647,6 +659,8 @@ def run_gpu(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": config_dict(c, name, {"precompute_ms": precompute_ms,
                                             "median_step_ms": statistics.median(step_ms),
+                                            "ssao_raw_ms": ssao_raw_ms, "ssao_blur_ms": ssao_blur_ms,
+                                            "ssao_tiled": ep.epbr_ssao_tiled(gb, sp),
                                             "wall_s": wall,
                                             **({"step": "ssao_raw + ssao_blur + shade (HDR) + bloom with the tone map "
                                                         "fused per frame; lighting set precomputed once",

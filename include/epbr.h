@@ -248,6 +248,20 @@ epbr_status epbr_ssao_raw(const epbr_gbuffer* gbuffer, const epbr_camera* camera
                           const epbr_ssao_params* params, float* ao, int64_t ao_pitch,
                           void* stream);
 
+/* Whether epbr_ssao_raw takes its tiled form for this G-buffer (*tiled = 1) or not (0).  The
+ * tiled form (the same values bit for bit) copies each block's depth footprint plus a 32-pixel
+ * halo into shared memory with one TMA tile load, and a warp whose samples all project inside
+ * that tile reads its taps from it; it applies at scale 2 when the depth plane
+ * rt[3] starts on a 16-byte boundary and its pitch is a multiple of 16 bytes (below 2^40) and
+ * the driver provides cuTensorMapEncodeTiled.  Synchronous, enqueues nothing. */
+epbr_status epbr_ssao_tiled(const epbr_gbuffer* gbuffer, const epbr_ssao_params* params,
+                            int32_t* tiled);
+
+/* Number of tiled-form warps whose wait for their depth tile ran out (50 ms) since the last call,
+ * then reset to 0.  Such warps read every tap from the depth plane instead, so their AO is
+ * unaffected; a nonzero count means a copy stalled.  Synchronous (device-wide copy). */
+epbr_status epbr_ssao_tile_timeouts(uint32_t* count);
+
 /* Depth-aware blur of an AO image: out_p = sum_q w_q ao_q / sum_q w_q over the
  * (2R+1)^2 window (clipped to the image) with w_q = exp(-(dx^2+dy^2)/(2 sigma_s^2)) *
  * exp(-|e_q - e_p| / (sigma_z e_p)), background taps weighted 0; background pixels get 1. */

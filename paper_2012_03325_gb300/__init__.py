@@ -219,6 +219,20 @@ def epbr_ssao_raw(g: GBuffer, cam: F.epbr_camera, p: SsaoParams, ao: torch.Tenso
                                _pitch(ao, 1), _stream(stream)))
 
 
+def epbr_ssao_tiled(g: GBuffer, p: SsaoParams) -> bool:
+    """Whether epbr_ssao_raw takes its TMA-tiled form for this G-buffer."""
+    t = C.c_int32()
+    _check(lib().epbr_ssao_tiled(C.byref(g.struct), C.byref(p.struct), C.byref(t)))
+    return bool(t.value)
+
+
+def epbr_ssao_tile_timeouts() -> int:
+    """Tiled-form warps whose depth-tile wait ran out since the last call (then reset)."""
+    n = C.c_uint32()
+    _check(lib().epbr_ssao_tile_timeouts(C.byref(n)))
+    return n.value
+
+
 def epbr_ssao_blur(g: GBuffer, p: SsaoParams, ao_in: torch.Tensor, ao_out: torch.Tensor, stream=None):
     _dev(ao_in, torch.float32, "ao_in")
     _dev(ao_out, torch.float32, "ao_out")

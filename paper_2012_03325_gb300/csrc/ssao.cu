@@ -1,18 +1,28 @@
 // Screen-space ambient occlusion (paper Sec. 5.2: normal-oriented hemisphere of Bavoil &
 // Sainz 2008, at half resolution, then a bilateral blur).
 //   k_ssao_raw   two AO texels per thread, the sample loop in packed FP32x2 arithmetic; the K
-//                kernel offsets sit in shared memory and the depth taps go through the
-//                read-only cache
+//                kernel offsets sit in shared memory.  TILED: the block's depth footprint plus a
+//                kSsaoHalo-pixel halo is copied into shared memory by one TMA tile load
+//                (cp.async.bulk.tensor, completion on an mbarrier) while the texels' frames are
+//                set up, and the depth taps read that tile; taps outside it (about 0.1% at the
+//                1080p scene) and the untiled form read the depth plane through the read-only
+//                cache
 //   k_ssao_blur  one thread per AO texel; (2R+1)^2 depth-aware taps read from a shared-memory
 //                tile of AO values and depths with an R-texel halo
 //   k_ssao_blur2 the same for R = 3 with two vertically adjacent texels per thread sharing their
 //                tap rows
+#include <cuda.h>  // CUtensorMap and its encoder's enums (the encoder is fetched at run time)
+#include <string.h>
+
 #include "ssao_core.cuh"
 
 namespace epbr {
 
 #ifndef EPBR_SSAO_MIN_BLOCKS
 #define EPBR_SSAO_MIN_BLOCKS 4  // resident 256-thread blocks per SM the register budget targets
+#endif
+#ifndef EPBR_SSAO_TILED_MIN_BLOCKS
+#define EPBR_SSAO_TILED_MIN_BLOCKS 3  // the same for the tiled form (48 KB of tile per block)
 #endif
 
 
@@ -57,57 +67,190 @@ __device__ __forceinline__ float ssao_rows(const GbufDev& g, const CamDev& cam, 
 
 __device__ __forceinline__ float2 pk(float a, float b) { return make_float2(a, b); }
 
-template <int FMT>
-__global__ void __launch_bounds__(256, EPBR_SSAO_MIN_BLOCKS)
-    k_ssao_raw(GbufDev g, CamDev cam, SsaoDev p, float* __restrict__ ao, long long ao_pitch, int Wa, int Ha) {
+// Depth tile of the TILED form: the block's 64 x 32 pixel footprint (32 x 16 AO texels at scale
+// 2) plus kSsaoHalo pixels on every side, 48 KB of dynamic shared memory.  The halo is a multiple
+// of 4 so that the tile's x origin 64 bx - kSsaoHalo is a multiple of 16 bytes, as a tiled TMA
+// copy requires; the origin may lie left of or above the image (the copy fills zeros there, and
+// such texels never decide a sample: a tap counts only when its pixel lies inside the image).
+constexpr int kSsaoHalo = 32;
+constexpr int kSsaoTileW = 64 + 2 * kSsaoHalo, kSsaoTileH = 32 + 2 * kSsaoHalo;
+constexpr unsigned kSsaoTileN = kSsaoTileW * kSsaoTileH;
+constexpr unsigned kSsaoTileBytes = kSsaoTileN * 4;
+constexpr unsigned long long kTmaWaitNs = 50ull * 1000 * 1000;  // a tile copy takes microseconds
+
+// Warps of k_ssao_raw<TILED> whose tile copy did not complete within kTmaWaitNs (their taps then
+// all read the depth plane, so the AO is unaffected); read and cleared by epbr_ssao_tile_timeouts.
+__device__ unsigned int g_ssao_tile_timeouts;
+
+__device__ __forceinline__ unsigned smem_addr(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ bool mbar_try_wait(unsigned bar, unsigned parity) {
+  unsigned done;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(done)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return done != 0;
+}
+
+// Waits for phase `parity` of the mbarrier for at most `limit_ns`; false when it ran out.
+__device__ __forceinline__ bool mbar_wait_bounded(unsigned bar, unsigned parity, unsigned long long limit_ns) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const unsigned long long t0 = global_ns();
+  while (!mbar_try_wait(bar, parity))
+    if (global_ns() - t0 > limit_ns) return false;
+  return true;
+}
+
+// One thread: arms the block's mbarrier for `bytes` and starts the 2-D tile copy of `map` at
+// element (x, y) into `dst` (the tensor map's box fixes the tile's shape).
+__device__ __forceinline__ void tma_load_tile_2d(const CUtensorMap* map, void* dst, unsigned bar, int x, int y,
+                                                 unsigned bytes) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::
+          "r"(smem_addr(dst)),
+      "l"(reinterpret_cast<unsigned long long>(map)), "r"(x), "r"(y), "r"(bar)
+      : "memory");
+}
+
+// floor(x) as an unsigned pixel index without the conversion unit: x + 1.5 * 2^23 rounded down
+// lies on the float grid of spacing 1, so for |x| < 2^22 it is exactly floor(x) + 1.5 * 2^23 and
+// its bit pattern minus that of 1.5 * 2^23 is floor(x) (two's complement for negative x).  Any
+// other x (|x| >= 2^22, inf, NaN) gives a value >= 2^22 as unsigned, which the on-screen test
+// (width and height <= 2^15) rejects, as it rejects the wrapped negative floors.
+__device__ __forceinline__ unsigned floor_px(float x) {
+  return (unsigned)__float_as_int(__fadd_rd(x, 12582912.0f)) - 0x4B400000u;
+}
+
+// Whether every sample of a texel projects inside the tile: each sample point lies within
+// Rb = radius * max_k |kernel[k]| of P, so in the pre-scaled coordinates (X, Y, eS) of
+// ssao_rows it lies in the box [X_P -+ sx Rb] x [Y_P -+ sy Rb] x [e -+ Rb]; with e - Rb > 0 the
+// pixel coordinates X / eS + W/2, Y / eS + H/2 take their extremes at the box's corners.  The
+// bounds are widened by 2 pixels, far beyond the FP32 rounding of either computation.
+__device__ __forceinline__ bool samples_in_tile(const SsaoRows& r, float e, float Rb, float sx, float sy, float hw,
+                                                float hh, int tx0, int ty0) {
+  const float dlo = e - Rb, dhi = e + Rb;
+  if (!(dlo > 0.0f)) return false;
+  const float ilo = 1.0f / dlo, ihi = 1.0f / dhi;
+  const float xa = r.x[3] - sx * Rb, xb = r.x[3] + sx * Rb;
+  const float ya = r.y[3] - sy * Rb, yb = r.y[3] + sy * Rb;
+  const float x0 = floorf(fminf(xa * ilo, xa * ihi) + hw) - 2.0f, x1 = floorf(fmaxf(xb * ilo, xb * ihi) + hw) + 2.0f;
+  const float y0 = floorf(fminf(ya * ilo, ya * ihi) + hh) - 2.0f, y1 = floorf(fmaxf(yb * ilo, yb * ihi) + hh) + 2.0f;
+  return x0 >= (float)tx0 && x1 < (float)(tx0 + kSsaoTileW) && y0 >= (float)ty0 && y1 < (float)(ty0 + kSsaoTileH);
+}
+
+// The sample loop for two texels (packed FP32x2).  FROM_TILE: every tap reads the shared-memory
+// tile (the caller has checked that every sample of the warp's texels projects inside it; the
+// index is clamped to the tile all the same); otherwise taps read the depth plane.  Branch-free
+// as in ssao_texel: an invalid sample (behind the camera or off-screen) reads some in-range texel
+// and is masked out.
+template <bool FROM_TILE>
+__device__ __forceinline__ float2 ssao_samples(const SsaoRows& a, const SsaoRows& b, float e0, float e1,
+                                               const float4* s_kernel, const SsaoDev& p, const CamDev& cam,
+                                               const GbufDev& g, const float* s_dep, unsigned tbase) {
+  const float2 tx = pk(a.x[0], b.x[0]), bx = pk(a.x[1], b.x[1]), nx = pk(a.x[2], b.x[2]), px = pk(a.x[3], b.x[3]);
+  const float2 ty = pk(a.y[0], b.y[0]), by = pk(a.y[1], b.y[1]), ny = pk(a.y[2], b.y[2]), py = pk(a.y[3], b.y[3]);
+  const float2 tz = pk(a.z[0], b.z[0]), bz = pk(a.z[1], b.z[1]), nz = pk(a.z[2], b.z[2]), pz = pk(a.z[3], b.z[3]);
+  const float2 hw = pk(0.5f * cam.W, 0.5f * cam.W), hh = pk(0.5f * cam.H, 0.5f * cam.H);
+  const float2 m2 = pk(-2.0f, -2.0f), c3 = pk(3.0f, 3.0f);
+  const float* dep = (const float*)g.rt[3];
+  const unsigned dp = (unsigned)(g.pitch[3] >> 2);
+  const unsigned W = (unsigned)cam.W, H = (unsigned)cam.H;
+  float2 occ = pk(0.0f, 0.0f);
+#pragma unroll(kSsaoUnroll)
+  for (int k = 0; k < p.K; ++k) {
+    const float4 ks = s_kernel[k];
+    const float2 KX = pk(ks.x, ks.x), KY = pk(ks.y, ks.y), KZ = pk(ks.z, ks.z);
+    const float2 X = __ffma2_rn(tx, KX, __ffma2_rn(bx, KY, __ffma2_rn(nx, KZ, px)));
+    const float2 Y = __ffma2_rn(ty, KX, __ffma2_rn(by, KY, __ffma2_rn(ny, KZ, py)));
+    const float2 Z = __ffma2_rn(tz, KX, __ffma2_rn(bz, KY, __ffma2_rn(nz, KZ, pz)));  // eS
+    const float2 inv = pk(rcp_ftz(Z.x), rcp_ftz(Z.y));
+    const float2 fx = __ffma2_rn(X, inv, hw), fy = __ffma2_rn(Y, inv, hh);
+    const unsigned ix0 = floor_px(fx.x), iy0 = floor_px(fy.x);
+    const unsigned ix1 = floor_px(fx.y), iy1 = floor_px(fy.y);
+    const bool v0 = Z.x > 0.0f && ix0 < W && iy0 < H;
+    const bool v1 = Z.y > 0.0f && ix1 < W && iy1 < H;
+    float eb0, eb1;
+    if (FROM_TILE) {
+      eb0 = s_dep[min(iy0 * (unsigned)kSsaoTileW + ix0 - tbase, kSsaoTileN - 1)];
+      eb1 = s_dep[min(iy1 * (unsigned)kSsaoTileW + ix1 - tbase, kSsaoTileN - 1)];
+    } else {
+      eb0 = __ldg(dep + (v0 ? iy0 * dp + ix0 : 0u));
+      eb1 = __ldg(dep + (v1 ? iy1 * dp + ix1 : 0u));
+    }
+    // eb <= eS - bias (finite) already excludes a background tap at +inf
+    const bool h0 = v0 && eb0 > 0.0f && eb0 <= Z.x - p.bias;
+    const bool h1 = v1 && eb1 > 0.0f && eb1 <= Z.y - p.bias;
+    const float2 x = pk(__saturatef(p.radius * rcp_ftz(fabsf(e0 - eb0))),
+                        __saturatef(p.radius * rcp_ftz(fabsf(e1 - eb1))));
+    const float2 sm = __fmul2_rn(__fmul2_rn(x, x), __ffma2_rn(m2, x, c3));  // smoothstep
+    occ = __fadd2_rn(occ, pk(h0 ? sm.x : 0.0f, h1 ? sm.y : 0.0f));
+  }
+  return occ;
+}
+
+template <int FMT, bool TILED>
+__global__ void __launch_bounds__(256, TILED ? EPBR_SSAO_TILED_MIN_BLOCKS : EPBR_SSAO_MIN_BLOCKS)
+    k_ssao_raw(const __grid_constant__ CUtensorMap depth_map, GbufDev g, CamDev cam, SsaoDev p,
+               float* __restrict__ ao, long long ao_pitch, int Wa, int Ha) {
   __shared__ float4 s_kernel[kMaxSsaoSamples];
+  __shared__ __align__(8) unsigned long long s_bar;
+  extern __shared__ __align__(128) float s_dep[];  // TILED: kSsaoTileH x kSsaoTileW depths
   const int tid = threadIdx.y * 32 + threadIdx.x;
+  // tile origin in pixels (a scale-2 block covers pixels [64 bx, 64 bx + 64) x [32 by, 32 by + 32))
+  const int tx0 = (int)blockIdx.x * 64 - kSsaoHalo, ty0 = (int)blockIdx.y * 32 - kSsaoHalo;
+  if (TILED && tid == 0) tma_load_tile_2d(&depth_map, s_dep, smem_addr(&s_bar), tx0, ty0, kSsaoTileBytes);
   for (int k = tid; k < p.K; k += 256) s_kernel[k] = __ldg(p.kernel + k);
   const int i = blockIdx.x * 32 + threadIdx.x, j0 = blockIdx.y * 16 + threadIdx.y, j1 = j0 + 8;
   const bool in0 = i < Wa && j0 < Ha, in1 = i < Wa && j1 < Ha;
   SsaoRows a, b;
   const float e0 = ssao_rows<FMT>(g, cam, p, i, j0, in0, a);
   const float e1 = ssao_rows<FMT>(g, cam, p, i, j1, in1, b);
-  __syncthreads();
+  __syncthreads();  // also orders the mbarrier's initialisation before every thread's wait
   const bool s0 = in0 && is_surface(e0), s1 = in1 && is_surface(e1);
-  if (s0 || s1) {
-    const float2 tx = pk(a.x[0], b.x[0]), bx = pk(a.x[1], b.x[1]), nx = pk(a.x[2], b.x[2]), px = pk(a.x[3], b.x[3]);
-    const float2 ty = pk(a.y[0], b.y[0]), by = pk(a.y[1], b.y[1]), ny = pk(a.y[2], b.y[2]), py = pk(a.y[3], b.y[3]);
-    const float2 tz = pk(a.z[0], b.z[0]), bz = pk(a.z[1], b.z[1]), nz = pk(a.z[2], b.z[2]), pz = pk(a.z[3], b.z[3]);
-    const float2 hw = pk(0.5f * cam.W, 0.5f * cam.W), hh = pk(0.5f * cam.H, 0.5f * cam.H);
-    const float2 m2 = pk(-2.0f, -2.0f), c3 = pk(3.0f, 3.0f);
-    const float* dep = (const float*)g.rt[3];
-    const unsigned dp = (unsigned)(g.pitch[3] >> 2);
-    const unsigned W = (unsigned)cam.W, H = (unsigned)cam.H;
-    float2 occ = pk(0.0f, 0.0f);
-    // branch-free as in ssao_texel: an invalid sample reads texel 0 and is masked out
-#pragma unroll(kSsaoUnroll)
-    for (int k = 0; k < p.K; ++k) {
+  bool tile_ok = false, from_tile = false;
+  if (TILED) {
+    tile_ok = mbar_wait_bounded(smem_addr(&s_bar), 0, kTmaWaitNs);
+    if (!tile_ok && threadIdx.x == 0) atomicAdd(&g_ssao_tile_timeouts, 1u);
+    // the longest kernel offset, over the warp's lanes
+    float k2 = 0.0f;
+    for (int k = threadIdx.x; k < p.K; k += 32) {
       const float4 ks = s_kernel[k];
-      const float2 KX = pk(ks.x, ks.x), KY = pk(ks.y, ks.y), KZ = pk(ks.z, ks.z);
-      const float2 X = __ffma2_rn(tx, KX, __ffma2_rn(bx, KY, __ffma2_rn(nx, KZ, px)));
-      const float2 Y = __ffma2_rn(ty, KX, __ffma2_rn(by, KY, __ffma2_rn(ny, KZ, py)));
-      const float2 Z = __ffma2_rn(tz, KX, __ffma2_rn(bz, KY, __ffma2_rn(nz, KZ, pz)));  // eS
-      const float2 inv = pk(rcp_ftz(Z.x), rcp_ftz(Z.y));
-      const float2 fx = __ffma2_rn(X, inv, hw), fy = __ffma2_rn(Y, inv, hh);
-      const int ix0 = __float2int_rd(fx.x), iy0 = __float2int_rd(fy.x);
-      const int ix1 = __float2int_rd(fx.y), iy1 = __float2int_rd(fy.y);
-      const bool v0 = Z.x > 0.0f && (unsigned)ix0 < W && (unsigned)iy0 < H;
-      const bool v1 = Z.y > 0.0f && (unsigned)ix1 < W && (unsigned)iy1 < H;
-      const float eb0 = __ldg(dep + (v0 ? (unsigned)iy0 * dp + (unsigned)ix0 : 0u));
-      const float eb1 = __ldg(dep + (v1 ? (unsigned)iy1 * dp + (unsigned)ix1 : 0u));
-      const bool h0 = v0 && eb0 > 0.0f && eb0 <= Z.x - p.bias;
-      const bool h1 = v1 && eb1 > 0.0f && eb1 <= Z.y - p.bias;
-      const float2 x = pk(__saturatef(p.radius * rcp_ftz(fabsf(e0 - eb0))),
-                          __saturatef(p.radius * rcp_ftz(fabsf(e1 - eb1))));
-      const float2 sm = __fmul2_rn(__fmul2_rn(x, x), __ffma2_rn(m2, x, c3));  // smoothstep
-      occ = __fadd2_rn(occ, pk(h0 ? sm.x : 0.0f, h1 ? sm.y : 0.0f));
+      k2 = fmaxf(k2, fmaf(ks.x, ks.x, fmaf(ks.y, ks.y, ks.z * ks.z)));
     }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) k2 = fmaxf(k2, __shfl_xor_sync(0xffffffffu, k2, o));
+    const float Rb = p.radius * sqrtf(k2) * 1.0001f;
+    const float sx = cam.ix_scale, sy = cam.iy_scale, hw = 0.5f * cam.W, hh = 0.5f * cam.H;
+    const bool fit = (!s0 || samples_in_tile(a, e0, Rb, sx, sy, hw, hh, tx0, ty0)) &&
+                     (!s1 || samples_in_tile(b, e1, Rb, sx, sy, hw, hh, tx0, ty0));
+    from_tile = __all_sync(0xffffffffu, tile_ok && fit);
+  }
+  if (s0 || s1) {
+    const unsigned tbase = (unsigned)ty0 * (unsigned)kSsaoTileW + (unsigned)tx0;
+    const float2 occ = from_tile ? ssao_samples<true>(a, b, e0, e1, s_kernel, p, cam, g, s_dep, tbase)
+                                 : ssao_samples<false>(a, b, e0, e1, s_kernel, p, cam, g, s_dep, tbase);
     if (s0) ((float*)((char*)ao + (size_t)j0 * ao_pitch))[i] = fmaf(-occ.x, p.inv_k, 1.0f);
     if (s1) ((float*)((char*)ao + (size_t)j1 * ao_pitch))[i] = fmaf(-occ.y, p.inv_k, 1.0f);
   }
   if (in0 && !s0) ((float*)((char*)ao + (size_t)j0 * ao_pitch))[i] = 1.0f;
   if (in1 && !s1) ((float*)((char*)ao + (size_t)j1 * ao_pitch))[i] = 1.0f;
+  // A copy that had not landed is waited for once more (bounded) so that it does not write into
+  // the shared memory of a block that starts on this SM after this one.
+  if (TILED && !tile_ok) mbar_wait_bounded(smem_addr(&s_bar), 0, kTmaWaitNs);
 }
 
 // Blur tile: 32x8 AO texels plus a halo of R <= 8 texels, AO values and the depths of their
@@ -228,6 +371,41 @@ static epbr_status check_ao_buffer(const void* ao, int64_t pitch, int Wa, const 
   return EPBR_OK;
 }
 
+
+// cuTensorMapEncodeTiled, fetched from the driver once per process (the library links only the
+// CUDA runtime); null when the driver does not provide it.
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static EncodeTiledFn encode_tiled() {
+  static const EncodeTiledFn fn = [] {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+      return (EncodeTiledFn) nullptr;
+    return (EncodeTiledFn)f;
+  }();
+  return fn;
+}
+
+// The TILED form applies at scale 2 when the depth plane meets the TMA rules (16-byte aligned
+// base, row pitch a multiple of 16 bytes below 2^40) and the tensor map encodes; `map` then
+// describes the depth plane with a kSsaoTileW x kSsaoTileH box.
+static bool depth_tile_map(const epbr_gbuffer* g, const epbr_ssao_params* p, CUtensorMap* map) {
+  if (p->scale != 2 || (uintptr_t)g->rt[3] % 16 || g->pitch[3] % 16 || g->pitch[3] >= (1ll << 40)) return false;
+  EncodeTiledFn enc = encode_tiled();
+  if (!enc) return false;
+  const cuuint64_t dims[2] = {(cuuint64_t)g->width, (cuuint64_t)g->height};
+  const cuuint64_t strides[1] = {(cuuint64_t)g->pitch[3]};
+  const cuuint32_t box[2] = {(cuuint32_t)kSsaoTileW, (cuuint32_t)kSsaoTileH};
+  const cuuint32_t estr[2] = {1, 1};
+  return enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, (void*)g->rt[3], dims, strides, box, estr,
+             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 }  // namespace epbr
 
 using namespace epbr;
@@ -266,11 +444,44 @@ extern "C" epbr_status epbr_ssao_raw(const epbr_gbuffer* g, const epbr_camera* c
   CamDev cd = make_cam(*cam);
   SsaoDev sd = make_ssao(*p);
   cudaStream_t s = (cudaStream_t)stream;
-  if (g->format == EPBR_GBUFFER_FP32)
-    k_ssao_raw<EPBR_GBUFFER_FP32><<<grd, blk, 0, s>>>(gd, cd, sd, ao, ao_pitch, Wa, Ha);
+  CUtensorMap map;
+  const bool tiled = depth_tile_map(g, p, &map);
+  if (!tiled) memset(&map, 0, sizeof(map));  // unused by the untiled form
+  const bool fp32 = g->format == EPBR_GBUFFER_FP32;
+  if (tiled) {
+    void (*k)(const CUtensorMap, GbufDev, CamDev, SsaoDev, float*, long long, int, int) =
+        fp32 ? k_ssao_raw<EPBR_GBUFFER_FP32, true> : k_ssao_raw<EPBR_GBUFFER_COMPACT, true>;
+    // the 48 KB tile is above the default dynamic shared-memory limit; the attribute is per
+    // function and device, and setting it again is harmless
+    if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSsaoTileBytes) != cudaSuccess)
+      return fail(EPBR_ERR_CUDA, "ssao_raw: shared-memory attribute: %s", cudaGetErrorString(cudaGetLastError()));
+    k<<<grd, blk, kSsaoTileBytes, s>>>(map, gd, cd, sd, ao, ao_pitch, Wa, Ha);
+  } else if (fp32)
+    k_ssao_raw<EPBR_GBUFFER_FP32, false><<<grd, blk, 0, s>>>(map, gd, cd, sd, ao, ao_pitch, Wa, Ha);
   else
-    k_ssao_raw<EPBR_GBUFFER_COMPACT><<<grd, blk, 0, s>>>(gd, cd, sd, ao, ao_pitch, Wa, Ha);
+    k_ssao_raw<EPBR_GBUFFER_COMPACT, false><<<grd, blk, 0, s>>>(map, gd, cd, sd, ao, ao_pitch, Wa, Ha);
   if ((st = check_launch("k_ssao_raw"))) return st;
+  return ok();
+}
+
+extern "C" epbr_status epbr_ssao_tiled(const epbr_gbuffer* g, const epbr_ssao_params* p, int32_t* tiled) {
+  int w, h;
+  epbr_status st = epbr_ssao_size(g, p, &w, &h);
+  if (st) return st;
+  if (!tiled) return fail(EPBR_ERR_INVALID_ARG, "tiled is NULL");
+  CUtensorMap map;
+  *tiled = depth_tile_map(g, p, &map) ? 1 : 0;
+  return ok();
+}
+
+extern "C" epbr_status epbr_ssao_tile_timeouts(uint32_t* count) {
+  if (!count) return fail(EPBR_ERR_INVALID_ARG, "count is NULL");
+  unsigned v = 0;
+  const unsigned zero = 0;
+  if (cudaMemcpyFromSymbol(&v, g_ssao_tile_timeouts, sizeof(v)) != cudaSuccess ||
+      cudaMemcpyToSymbol(g_ssao_tile_timeouts, &zero, sizeof(zero)) != cudaSuccess)
+    return fail(EPBR_ERR_CUDA, "ssao_tile_timeouts: %s", cudaGetErrorString(cudaGetLastError()));
+  *count = v;
   return ok();
 }
 
