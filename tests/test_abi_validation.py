@@ -77,6 +77,25 @@ def test_ssao_raw_rejects_a_depth_plane_over_2_32_texels(lib):
     assert st == UNSUPPORTED and "2^32" in last_error(lib)
 
 
+def test_ssao_tiled_query(lib):
+    """Which SSAO form a G-buffer takes is decided on the host; forms the TMA copy cannot describe
+    (scale 1, a depth pitch or base off a 16-byte boundary) are answered without the driver."""
+    g, p, t = gbuf(64, 32), ssao(), C.c_int32(-1)
+    assert lib.epbr_ssao_tiled(C.byref(g), C.byref(p), None) == INVALID
+    bad = gbuf(0, 32)
+    assert lib.epbr_ssao_tiled(C.byref(bad), C.byref(p), C.byref(t)) == INVALID
+    p1 = ssao(scale=1)
+    assert lib.epbr_ssao_tiled(C.byref(g), C.byref(p1), C.byref(t)) == F.EPBR_OK and t.value == 0
+    g.pitch[3] = 64 * 4 + 4  # a multiple of 4 bytes, not of 16
+    t.value = -1
+    assert lib.epbr_ssao_tiled(C.byref(g), C.byref(p), C.byref(t)) == F.EPBR_OK and t.value == 0
+    g2 = gbuf(64, 32)
+    g2.rt[3] = FAKE + 4  # 4-byte aligned depth plane, not 16
+    t.value = -1
+    assert lib.epbr_ssao_tiled(C.byref(g2), C.byref(p), C.byref(t)) == F.EPBR_OK and t.value == 0
+    assert lib.epbr_ssao_tile_timeouts(None) == INVALID
+
+
 @pytest.mark.parametrize("field,value", [("num_samples", 0), ("num_samples", 257), ("scale", 3), ("radius", 0.0),
                                          ("bias", -1.0), ("sigma_z", 0.0), ("blur_radius", 9), ("kernel", FAKE + 4),
                                          ("noise", 0)])
