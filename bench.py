@@ -653,7 +653,9 @@ def run_gpu(args):
     clock_mhz = clocks["sm_mhz"] if clocks else 2070.0
     peak_tflops = sms * 128 * 2 * clock_mhz * 1e6 / 1e12
     achieved = flops / (shade_ms * 1e-3) / 1e12
-    traffic = kernel_traffic("k_shade", SHADE_SOURCES) if not compact and not args.shadows else None
+    # the recorded traffic is the FP32 compose with the fused tone map (HDR and RGBA8 stores);
+    # with --bloom the compose stores HDR only, with --shadows another kernel runs
+    traffic = kernel_traffic("k_shade", SHADE_SOURCES) if not (compact or args.shadows or args.bloom) else None
     kname = "k_shade_shadow (compose with shadow maps + fused tone map)" if args.shadows else \
         "k_shade (compose + fused tone map)"
     roofline = {"bound": "alu", "kernel": kname, "achieved": achieved,
