@@ -52,23 +52,33 @@ __global__ void __launch_bounds__(kBloomTX* kBloomTY)
   const int tid = threadIdx.y * kBloomTX + threadIdx.x;
   {
     const BloomLevel& l1 = d.lev[1];
+    // two level-1 rows per batch: their eight HDR loads (coordinates clamped into the image, so
+    // every load is valid) are issued together, then reduced in the per-texel order
 #pragma unroll
-    for (int r = 0; r < 4; ++r) {
-      int li = threadIdx.x, lj = threadIdx.y + 8 * r;
-      int i = blockIdx.x * 32 + li, j = blockIdx.y * 32 + lj;
-      float3 sum = f3(0, 0, 0);
-      if (i < l1.W && j < l1.H) {
+    for (int r0 = 0; r0 < 4; r0 += 2) {
+      float3 c[2][4];
+#pragma unroll
+      for (int q = 0; q < 2; ++q) {
+        const int i = blockIdx.x * 32 + threadIdx.x, j = blockIdx.y * 32 + threadIdx.y + 8 * (r0 + q);
 #pragma unroll
         for (int b = 0; b < 2; ++b)
 #pragma unroll
-          for (int a = 0; a < 2; ++a) {
-            float3 c = load_hdr<HF>(hdr, pitch, min(2 * i + a, W - 1), min(2 * j + b, H - 1));
-            if (bloom_bright(c, threshold)) sum = sum + c;
-          }
-        sum = 0.25f * sum;
-        l1.pyr[(size_t)j * l1.W + i] = make_float4(sum.x, sum.y, sum.z, 0.0f);
+          for (int a = 0; a < 2; ++a) c[q][2 * b + a] = load_hdr<HF>(hdr, pitch, min(2 * i + a, W - 1), min(2 * j + b, H - 1));
       }
-      s_a[lj * 32 + li] = make_float4(sum.x, sum.y, sum.z, 0.0f);
+#pragma unroll
+      for (int q = 0; q < 2; ++q) {
+        int li = threadIdx.x, lj = threadIdx.y + 8 * (r0 + q);
+        int i = blockIdx.x * 32 + li, j = blockIdx.y * 32 + lj;
+        float3 sum = f3(0, 0, 0);
+        if (i < l1.W && j < l1.H) {
+#pragma unroll
+          for (int t = 0; t < 4; ++t)
+            if (bloom_bright(c[q][t], threshold)) sum = sum + c[q][t];
+          sum = 0.25f * sum;
+          l1.pyr[(size_t)j * l1.W + i] = make_float4(sum.x, sum.y, sum.z, 0.0f);
+        }
+        s_a[lj * 32 + li] = make_float4(sum.x, sum.y, sum.z, 0.0f);
+      }
     }
   }
 #pragma unroll
