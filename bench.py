@@ -19,6 +19,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 import numpy as np
@@ -57,6 +58,12 @@ def parse():
     ap.add_argument("--bloom", action="store_true",
                     help="add the bloom pass (Sec. 5.3) to the frame: shade to HDR, then bloom + tone map")
     return ap.parse_args()
+
+
+def bench_dir():
+    """Directory for the clock samples and the batch plan cache (EPBR_BENCH_DIR), or None."""
+    d = os.environ.get("EPBR_BENCH_DIR")
+    return d if d and os.path.isdir(d) else None
 
 
 def dist_env():
@@ -121,7 +128,7 @@ def config_dict(c, name, extra=None):
 
 
 # ------------------------------------------------------------------------------------------
-# algorithmic work of the compose kernel (per-unit figures; see DESIGN.md)
+# algorithmic work of the compose kernel (per-unit figures)
 # ------------------------------------------------------------------------------------------
 FLOP_LIGHT_TEST = 20     # L = p - P, |L|^2, normalisation, n.l test
 FLOP_LIGHT_LIT = 70      # the rest of Eq. 1 for a light with n.l > 0
@@ -182,8 +189,7 @@ class ClockSampler:
         self.idx = gpu_index
         self.proc = None
         self.t0 = self.t1 = None
-        out = os.path.join(ROOT, "gpurun_out")
-        self.path = os.path.join(out if os.path.isdir(out) else "/tmp", f"clocks_{os.getpid()}.csv")
+        self.path = os.path.join(bench_dir() or tempfile.gettempdir(), f"clocks_{os.getpid()}.csv")
 
     def __enter__(self):
         self.f = open(self.path, "w")
@@ -880,8 +886,7 @@ def run_batch(args):
                                   ep.EPBR_HDR_RGBA32F, tp, ldr, stream=stream)
 
     batch = ep.Batch(views, ibls, ep.batch_params(sp), keep=[per, keep])
-    cache = os.path.join(ROOT, "gpurun_out", "batch_plan.txt") if os.path.isdir(os.path.join(ROOT, "gpurun_out")) \
-        else None
+    cache = os.path.join(bench_dir(), "batch_plan.txt") if bench_dir() else None
     with torch.cuda.stream(stream):
         plan = batch.autotune(cache, stream=stream)
 
