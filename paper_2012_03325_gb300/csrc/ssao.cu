@@ -4,9 +4,9 @@
 //                kernel offsets sit in shared memory.  TILED: the block's depth footprint plus a
 //                kSsaoHalo-pixel halo is copied into shared memory by one TMA tile load
 //                (cp.async.bulk.tensor, completion on an mbarrier) while the texels' frames are
-//                set up, and the depth taps read that tile; taps outside it (about 0.1% at the
-//                1080p scene) and the untiled form read the depth plane through the read-only
-//                cache
+//                set up; a warp whose samples all project inside the tile reads its depth taps
+//                from it, any other warp (12% of the surface warps of the 1080p scene) and the
+//                untiled form read the depth plane through the read-only cache
 //   k_ssao_blur  one thread per AO texel; (2R+1)^2 depth-aware taps read from a shared-memory
 //                tile of AO values and depths with an R-texel halo
 //   k_ssao_blur2 the same for R = 3 with two vertically adjacent texels per thread sharing their
