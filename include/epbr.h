@@ -251,9 +251,9 @@ epbr_status epbr_ssao_raw(const epbr_gbuffer* gbuffer, const epbr_camera* camera
 /* Whether epbr_ssao_raw takes its tiled form for this G-buffer (*tiled = 1) or not (0).  The
  * tiled form (the same values bit for bit) copies each block's depth footprint plus a 32-pixel
  * halo into shared memory with one TMA tile load, and a warp whose samples all project inside
- * that tile reads its taps from it; it applies at scale 2 when the depth plane
- * rt[3] starts on a 16-byte boundary and its pitch is a multiple of 16 bytes (below 2^40) and
- * the driver provides cuTensorMapEncodeTiled.  Synchronous, enqueues nothing. */
+ * that tile reads its taps from it; it applies at scale 2 to views of at most 1536 rows when the
+ * depth plane rt[3] starts on a 16-byte boundary and its pitch is a multiple of 16 bytes (below
+ * 2^40) and the driver provides cuTensorMapEncodeTiled.  Synchronous, enqueues nothing. */
 epbr_status epbr_ssao_tiled(const epbr_gbuffer* gbuffer, const epbr_ssao_params* params,
                             int32_t* tiled);
 

@@ -390,11 +390,19 @@ static EncodeTiledFn encode_tiled() {
   return fn;
 }
 
-// The TILED form applies at scale 2 when the depth plane meets the TMA rules (16-byte aligned
-// base, row pitch a multiple of 16 bytes below 2^40) and the tensor map encodes; `map` then
-// describes the depth plane with a kSsaoTileW x kSsaoTileH box.
+// The TILED form applies at scale 2 to views of at most kSsaoTiledMaxRows rows when the depth
+// plane meets the TMA rules (16-byte aligned base, row pitch a multiple of 16 bytes below 2^40)
+// and the tensor map encodes; `map` then describes the depth plane with a kSsaoTileW x kSsaoTileH
+// box.  The row limit: the samples' spread in pixels grows with the view's focal length in pixels
+// (its height, at a given field of view) while the halo is fixed, so on taller views fewer warps
+// fit the tile (88% of the surface warps at 1080p, 35% at 2160p on the generator's scenes) and
+// the untiled form, at its higher occupancy, is used.
+constexpr int kSsaoTiledMaxRows = 1536;
+
 static bool depth_tile_map(const epbr_gbuffer* g, const epbr_ssao_params* p, CUtensorMap* map) {
-  if (p->scale != 2 || (uintptr_t)g->rt[3] % 16 || g->pitch[3] % 16 || g->pitch[3] >= (1ll << 40)) return false;
+  if (p->scale != 2 || g->height > kSsaoTiledMaxRows || (uintptr_t)g->rt[3] % 16 || g->pitch[3] % 16 ||
+      g->pitch[3] >= (1ll << 40))
+    return false;
   EncodeTiledFn enc = encode_tiled();
   if (!enc) return false;
   const cuuint64_t dims[2] = {(cuuint64_t)g->width, (cuuint64_t)g->height};

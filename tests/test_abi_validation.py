@@ -93,6 +93,9 @@ def test_ssao_tiled_query(lib):
     g2.rt[3] = FAKE + 4  # 4-byte aligned depth plane, not 16
     t.value = -1
     assert lib.epbr_ssao_tiled(C.byref(g2), C.byref(p), C.byref(t)) == F.EPBR_OK and t.value == 0
+    tall = gbuf(3840, 2160)  # aligned and dense, but taller than the tiled form's 1536 rows
+    t.value = -1
+    assert lib.epbr_ssao_tiled(C.byref(tall), C.byref(p), C.byref(t)) == F.EPBR_OK and t.value == 0
     assert lib.epbr_ssao_tile_timeouts(None) == INVALID
 
 
