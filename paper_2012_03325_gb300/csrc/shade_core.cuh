@@ -232,9 +232,9 @@ __device__ __forceinline__ Direct px_direct_begin(const Px& s) {
 }
 
 // Scalar light terms shared by both loops.  Guards are folded into existing FMAs: |L|^2 + 1e-30
-// (a light at P contributes 0), |n x s|^2 + 1e-18 (keeps the GGX denominator normal when
-// l = -v), and |l + v|^2 biased by 1e-6 (>= 0 under rounding); each changes a result by less
-// than 1e-12 relative.
+// (a light at P contributes 0) and |n x s|^2 + 1e-18 (keeps the GGX denominator normal when
+// l = -v) change a result by < 1e-12 relative; |l + v|^2 biased by 1e-6 (>= 0 under rounding)
+// changes the term of a light behind a grazing view (l ~ -v) by up to ~2e-6 / (n.v)^2 relative.
 struct LightTerms {
   float a, b, bf;
 };
