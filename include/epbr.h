@@ -259,7 +259,8 @@ epbr_status epbr_ssao_tiled(const epbr_gbuffer* gbuffer, const epbr_ssao_params*
 
 /* Number of tiled-form warps whose wait for their depth tile ran out (50 ms) since the last call,
  * then reset to 0.  Such warps read every tap from the depth plane instead, so their AO is
- * unaffected; a nonzero count means a copy stalled.  Synchronous (device-wide copy). */
+ * unaffected; a nonzero count means a copy stalled.  Synchronous copies on the current device;
+ * the launches it should cover must have completed (synchronise their stream first). */
 epbr_status epbr_ssao_tile_timeouts(uint32_t* count);
 
 /* Depth-aware blur of an AO image: out_p = sum_q w_q ao_q / sum_q w_q over the
