@@ -723,6 +723,11 @@ def run_gpu(args):
                                                 surfels=srec if args.surfels else None)
         line["cpu_baseline"] = {"value": rate, "unit": "Mpixels/s", "cores": cores, "kind": "oracle",
                                 "sample": sample}
+        if not (args.bloom or args.shadows or args.mesh or args.surfels):
+            # the same per-frame path on one host thread (a few bands)
+            r1, _, s1 = oracle_frame_rate(dict(c, name=name), sc, g, env, k, nz, min(3.0, args.cpu_seconds),
+                                          threads=1)
+            line["cpu_baseline"]["one_core"] = {"value": r1, "unit": "Mpixels/s", "cores": 1, "sample": s1}
     print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
