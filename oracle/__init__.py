@@ -84,6 +84,7 @@ def lib():
                                   dp, dp, dp, C.c_int]
             L.or_shade.argtypes = [dp, C.POINTER(Camera), dp, C.c_int, C.POINTER(Ibl), dp, C.c_int,
                                    C.c_int, lp, C.c_long, dp, C.c_int]
+            L.or_ssao_blur_image.argtypes = [dp, C.POINTER(Camera), C.POINTER(SsaoParams), dp, dp]
             L.or_tonemap.argtypes = [dp, C.c_long, C.c_double, C.c_int, C.c_void_p, dp]
             L.or_brdf.argtypes = [dp, dp, dp, dp, C.c_double, C.c_double, dp]
             L.or_brdf.restype = None
@@ -218,6 +219,20 @@ def ssao(gb, cam: Camera, K: int, scale: int, radius: float, bias: float, blur_r
     if t is None:
         return ao.reshape(Ha, Wa), lo.reshape(Ha, Wa), hi.reshape(Ha, Wa)
     return ao, lo, hi
+
+
+def ssao_blur_image(gb, cam: Camera, raw, scale: int = 2, blur_radius: int = 3, sigma_s: float = 2.0,
+                    sigma_z: float = 0.1) -> np.ndarray:
+    """The bilateral blur of `ssao(..., blurred=True)` applied to a given raw AO image (Ha, Wa),
+    with the G-buffer's depths; returns the blurred (Ha, Wa) image."""
+    Wa, Ha = (cam.W + scale - 1) // scale, (cam.H + scale - 1) // scale
+    r = _f64(raw)
+    assert r.shape == (Ha, Wa)
+    sp = SsaoParams(1, scale, blur_radius, 0.5, 0.0, sigma_s, sigma_z, None, None)
+    g = _f64(gb)
+    out = np.zeros((Ha, Wa))
+    assert lib().or_ssao_blur_image(_dp(g), C.byref(cam), C.byref(sp), _dp(r), _dp(out)) == 0
+    return out
 
 
 class IblSet:

@@ -551,6 +551,47 @@ typedef struct {
   double *ao, *lo, *hi;
 } ssao_ctx;
 
+/* Bilateral blur weight of AO texel q seen from texel p (Sec. 5.2): a Gaussian of the texel
+ * offset (sigma_s in AO texels) times a range term that falls with the relative depth step,
+ * exp(-|e_q - e_p| / (sigma_z e_p)). */
+static double blur_weight(const or_ssao_params* sp, int dx, int dy, double ep, double eq) {
+  return exp(-(dx * dx + dy * dy) / (2.0 * sp->sigma_s * sp->sigma_s)) * exp(-fabs(eq - ep) / (sp->sigma_z * ep));
+}
+
+/* Blurred AO of texel (i, j).  raw == NULL: the raw AO of each tap (and its tie bounds) comes
+ * from ssao_raw_texel; otherwise from the given Ha*Wa raw AO image (no ties).  Background taps
+ * (no surface at the tap's pixel) carry no weight; a background texel is 1. */
+static void ssao_blur_texel(const double* gb, const or_camera* cam, const or_ssao_params* sp, int Wa, int Ha,
+                            const double* raw, int i, int j, double* ao, double* lo, double* hi) {
+  double ep = gb[(((long)sp->scale * j) * cam->W + (long)sp->scale * i) * 9 + 8];
+  if (!is_surface(ep)) {
+    *ao = *lo = *hi = 1.0;
+    return;
+  }
+  double num = 0.0, nlo = 0.0, nhi = 0.0, den = 0.0;
+  for (int dy = -sp->blur_radius; dy <= sp->blur_radius; ++dy)
+    for (int dx = -sp->blur_radius; dx <= sp->blur_radius; ++dx) {
+      int qi = i + dx, qj = j + dy;
+      if (qi < 0 || qj < 0 || qi >= Wa || qj >= Ha) continue;
+      double eq = gb[(((long)sp->scale * qj) * cam->W + (long)sp->scale * qi) * 9 + 8];
+      if (!is_surface(eq)) continue;
+      double w = blur_weight(sp, dx, dy, ep, eq);
+      double a, l, h;
+      if (raw) {
+        a = l = h = raw[(long)qj * Wa + qi];
+      } else {
+        ssao_raw_texel(gb, cam, sp, qi, qj, &a, &l, &h);
+      }
+      num += w * a;
+      nlo += w * l;
+      nhi += w * h;
+      den += w;
+    }
+  *ao = num / den;
+  *lo = nlo / den;
+  *hi = nhi / den;
+}
+
 static void ssao_body(void* p, long i0, long i1) {
   ssao_ctx* c = (ssao_ctx*)p;
   const or_ssao_params* sp = c->sp;
@@ -561,31 +602,7 @@ static void ssao_body(void* p, long i0, long i1) {
       ssao_raw_texel(c->gb, c->cam, sp, i, j, &c->ao[t], &c->lo[t], &c->hi[t]);
       continue;
     }
-    /* Bilateral blur of the raw AO: Gaussian in AO texels times exp(-|e_q - e_p| / (sz e_p)). */
-    double ep = c->gb[(((long)sp->scale * j) * c->cam->W + (long)sp->scale * i) * 9 + 8];
-    if (!is_surface(ep)) {
-      c->ao[t] = c->lo[t] = c->hi[t] = 1.0;
-      continue;
-    }
-    double num = 0.0, nlo = 0.0, nhi = 0.0, den = 0.0;
-    for (int dy = -sp->blur_radius; dy <= sp->blur_radius; ++dy)
-      for (int dx = -sp->blur_radius; dx <= sp->blur_radius; ++dx) {
-        int qi = i + dx, qj = j + dy;
-        if (qi < 0 || qj < 0 || qi >= c->Wa || qj >= c->Ha) continue;
-        double eq = c->gb[(((long)sp->scale * qj) * c->cam->W + (long)sp->scale * qi) * 9 + 8];
-        if (!is_surface(eq)) continue;
-        double w = exp(-(dx * dx + dy * dy) / (2.0 * sp->sigma_s * sp->sigma_s)) *
-                   exp(-fabs(eq - ep) / (sp->sigma_z * ep));
-        double a, l, h;
-        ssao_raw_texel(c->gb, c->cam, sp, qi, qj, &a, &l, &h);
-        num += w * a;
-        nlo += w * l;
-        nhi += w * h;
-        den += w;
-      }
-    c->ao[t] = num / den;
-    c->lo[t] = nlo / den;
-    c->hi[t] = nhi / den;
+    ssao_blur_texel(c->gb, c->cam, sp, c->Wa, c->Ha, NULL, i, j, &c->ao[t], &c->lo[t], &c->hi[t]);
   }
 }
 
@@ -598,6 +615,20 @@ int or_ssao(const double* gb, const or_camera* cam, const or_ssao_params* sp, in
   ssao_ctx c = {gb, cam, sp, mode, Wa, Ha, texels, ao, lo, hi};
   long cnt = texels ? n : (long)Wa * Ha;
   or_parallel_for(cnt, threads, ssao_body, &c);
+  return 0;
+}
+
+/* The bilateral blur alone, applied to a given raw AO image (Ha*Wa doubles, the AO layout of
+ * or_ssao) with the depths of the G-buffer: the same blur as or_ssao mode 1.  out: Ha*Wa. */
+int or_ssao_blur_image(const double* gb, const or_camera* cam, const or_ssao_params* sp, const double* raw,
+                       double* out) {
+  if (!gb || !cam || !sp || !raw || !out || (sp->scale != 1 && sp->scale != 2) || sp->blur_radius < 0) return 1;
+  int Wa = (cam->W + sp->scale - 1) / sp->scale, Ha = (cam->H + sp->scale - 1) / sp->scale;
+  for (int j = 0; j < Ha; ++j)
+    for (int i = 0; i < Wa; ++i) {
+      double lo, hi;
+      ssao_blur_texel(gb, cam, sp, Wa, Ha, raw, i, j, &out[(long)j * Wa + i], &lo, &hi);
+    }
   return 0;
 }
 
