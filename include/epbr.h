@@ -197,6 +197,10 @@ epbr_status epbr_irradiance(const epbr_env* env, int32_t irr_width, int32_t irr_
  *    2048x1024 environment needs 4.75 MiB.
  *  - Set-up: the first call on each device looks up the array's device address with that
  *    device current (cudaGetSymbolAddress); make that first call before any stream capture.
+ *    The address belongs to the context current at the call (the primary context, or a
+ *    caller's own driver context): it is cached per device together with that context's
+ *    unique id and looked up again when a call finds another context current, e.g. after
+ *    cudaDeviceReset or from a caller's own context.
  *  - Sharing: every call on a device uses the same array, which keeps the previous call's
  *    contents (each call writes every partial it reads, so nothing needs clearing).  Calls
  *    whose work overlaps on the GPU (other streams, other threads) race on the array: order
@@ -257,11 +261,23 @@ epbr_status epbr_ssao_raw(const epbr_gbuffer* gbuffer, const epbr_camera* camera
 epbr_status epbr_ssao_tiled(const epbr_gbuffer* gbuffer, const epbr_ssao_params* params,
                             int32_t* tiled);
 
-/* Number of tiled-form warps whose wait for their depth tile ran out (50 ms) since the last call,
- * then reset to 0.  Such warps read every tap from the depth plane instead, so their AO is
- * unaffected; a nonzero count means a copy stalled.  Synchronous copies on the current device;
- * the launches it should cover must have completed (synchronise their stream first). */
+/* Number of tiled-form warps whose first wait for their depth tile ran out (50 ms by default)
+ * since the last call, then reset to 0.  Such warps read every tap from the depth plane instead,
+ * so their AO is unaffected; a nonzero count means a copy stalled.  Such a block waits once more
+ * (50 ms) before it exits; if that wait runs out too, its copy may still land in shared memory
+ * that a later block uses, and this call returns EPBR_ERR_DEVICE_STATUS (with *count set, the
+ * flag cleared): treat the AO of the launches since the previous call as suspect.  Synchronous
+ * copies on the current device; the launches it should cover must have completed (synchronise
+ * their stream first). */
 epbr_status epbr_ssao_tile_timeouts(uint32_t* count);
+
+/* Test hook for the tiled form's fallback path: sets the limit of the first wait for the depth
+ * tile (nanoseconds, at most the default 50 ms) used by later epbr_ssao_raw launches and returns
+ * the previous limit in *previous_ns (nullable).  0 makes every tiled warp give up at once, read
+ * its taps from the depth plane (the same AO) and count itself in epbr_ssao_tile_timeouts; the
+ * second wait before a block exits keeps its 50 ms bound.  Process-wide; not for production use.
+ * EPBR_ERR_INVALID_ARG above the default. */
+epbr_status epbr_ssao_set_tile_wait(uint64_t first_wait_ns, uint64_t* previous_ns);
 
 /* Depth-aware blur of an AO image: out_p = sum_q w_q ao_q / sum_q w_q over the
  * (2R+1)^2 window (clipped to the image) with w_q = exp(-(dx^2+dy^2)/(2 sigma_s^2)) *

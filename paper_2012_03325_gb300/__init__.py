@@ -48,6 +48,30 @@ def _dev(t: torch.Tensor, dtype=None, name="tensor") -> int:
     return t.data_ptr()
 
 
+def _flat(t: torch.Tensor, n: int, dtype, name: str) -> int:
+    """Pointer of a dense output that the library fills with n elements of `dtype`."""
+    _dev(t, dtype, name)
+    if not t.is_contiguous() or t.numel() < n:
+        raise ValueError(f"{name} must be contiguous with at least {n} elements, got {tuple(t.shape)}")
+    return t.data_ptr()
+
+
+def _image(t: torch.Tensor, H: int, W: int, channels: int | None, name: str, dtype=None) -> int:
+    """Pointer of an (H, W[, channels]) image read or written through its row pitch: at least H
+    rows of at least W texels, rows dense."""
+    _dev(t, dtype, name)
+    want = 2 if channels is None else 3
+    if t.dim() != want or t.shape[0] < H or t.shape[1] < W or (channels is not None and t.shape[2] != channels):
+        shape = (H, W) if channels is None else (H, W, channels)
+        raise ValueError(f"{name} must cover {shape}, got {tuple(t.shape)}")
+    _pitch(t, 1)
+    return t.data_ptr()
+
+
+def _hdr_dtype(fmt: int):
+    return torch.float16 if fmt == EPBR_HDR_RGBA16F else torch.float32
+
+
 def _pitch(t: torch.Tensor, texel_elems: int) -> int:
     """Row pitch in bytes of an (H, W[, C]) tensor whose rows are dense."""
     if t.dim() >= 2:
@@ -74,17 +98,18 @@ class GBuffer:
     @classmethod
     def fp32(cls, rt0: torch.Tensor, rt1: torch.Tensor, depth: torch.Tensor) -> "GBuffer":
         H, W = depth.shape
-        for t, n in ((rt0, "rt0"), (rt1, "rt1"), (depth, "depth")):
-            _dev(t, torch.float32, n)
+        _image(rt0, H, W, 4, "rt0", torch.float32)
+        _image(rt1, H, W, 4, "rt1", torch.float32)
+        _image(depth, H, W, None, "depth", torch.float32)
         return cls(F.EPBR_GBUFFER_FP32, [rt0, rt1, None, depth], W, H)
 
     @classmethod
     def compact(cls, rt0: torch.Tensor, rt1: torch.Tensor, rt2: torch.Tensor, depth: torch.Tensor) -> "GBuffer":
         H, W = depth.shape
-        _dev(rt0, torch.uint8, "rt0")
-        _dev(rt1, torch.float16, "rt1")
-        _dev(rt2, torch.uint8, "rt2")
-        _dev(depth, torch.float32, "depth")
+        _image(rt0, H, W, 4, "rt0", torch.uint8)
+        _image(rt1, H, W, 2, "rt1", torch.float16)
+        _image(rt2, H, W, 2, "rt2", torch.uint8)
+        _image(depth, H, W, None, "depth", torch.float32)
         return cls(F.EPBR_GBUFFER_COMPACT, [rt0, rt1, rt2, depth], W, H)
 
 
@@ -168,18 +193,17 @@ def epbr_precompute_ibl(env: torch.Tensor, ibl: Ibl, workspace: torch.Tensor | N
 
 
 def epbr_brdf_lut(S: int, N: int, out: torch.Tensor, stream=None):
-    _dev(out, torch.float32, "lut")
-    _check(lib().epbr_brdf_lut(S, N, out.data_ptr(), _stream(stream)))
+    _check(lib().epbr_brdf_lut(S, N, _flat(out, S * S * 2, torch.float32, "lut"), _stream(stream)))
 
 
 def epbr_irradiance(env: torch.Tensor, Wi: int, Hi: int, out: torch.Tensor, workspace=None, stream=None):
     e = env_struct(env)
-    _dev(out, torch.float32, "out")
+    op = _flat(out, Wi * Hi * 4, torch.float32, "out")
     n = C.c_size_t()
     p = ibl_params(1, 1, 1, 1, Wi, Hi)
     _check(lib().epbr_precompute_ibl_workspace_size(C.byref(p), e.width, e.height, C.byref(n)))
     ws = workspace if workspace is not None else _workspace(n.value, env.device)
-    _check(lib().epbr_irradiance(C.byref(e), Wi, Hi, out.data_ptr(), _aligned(ws),
+    _check(lib().epbr_irradiance(C.byref(e), Wi, Hi, op, _aligned(ws),
                                  ws.numel() - (_aligned(ws) - ws.data_ptr()), _stream(stream)))
 
 
@@ -187,8 +211,8 @@ def epbr_irradiance_noalloc(env: torch.Tensor, Wi: int, Hi: int, out: torch.Tens
     """epbr_irradiance without a workspace: for callers that may not allocate device memory
     (the library's fixed 8 MiB scratch array is used instead)."""
     e = env_struct(env)
-    _dev(out, torch.float32, "out")
-    _check(lib().epbr_irradiance_noalloc(C.byref(e), Wi, Hi, out.data_ptr(), _stream(stream)))
+    op = _flat(out, Wi * Hi * 4, torch.float32, "out")
+    _check(lib().epbr_irradiance_noalloc(C.byref(e), Wi, Hi, op, _stream(stream)))
 
 
 def epbr_prefilter(env: torch.Tensor, N: int, ibl: Ibl, stream=None):
@@ -213,9 +237,13 @@ class SsaoParams:
         return ((H + s - 1) // s, (W + s - 1) // s)
 
 
+def _ao(g: GBuffer, p: SsaoParams, t: torch.Tensor, name: str) -> int:
+    Ha, Wa = p.ao_shape(g.struct.width, g.struct.height)
+    return _image(t, Ha, Wa, None, name, torch.float32)
+
+
 def epbr_ssao_raw(g: GBuffer, cam: F.epbr_camera, p: SsaoParams, ao: torch.Tensor, stream=None):
-    _dev(ao, torch.float32, "ao")
-    _check(lib().epbr_ssao_raw(C.byref(g.struct), C.byref(cam), C.byref(p.struct), ao.data_ptr(),
+    _check(lib().epbr_ssao_raw(C.byref(g.struct), C.byref(cam), C.byref(p.struct), _ao(g, p, ao, "ao"),
                                _pitch(ao, 1), _stream(stream)))
 
 
@@ -233,15 +261,21 @@ def epbr_ssao_tile_timeouts() -> int:
     return n.value
 
 
+def epbr_ssao_set_tile_wait(first_wait_ns: int) -> int:
+    """Test hook: limit of the tiled form's first depth-tile wait (0 = give up at once); returns
+    the previous limit."""
+    prev = C.c_uint64()
+    _check(lib().epbr_ssao_set_tile_wait(int(first_wait_ns), C.byref(prev)))
+    return prev.value
+
+
 def epbr_ssao_blur(g: GBuffer, p: SsaoParams, ao_in: torch.Tensor, ao_out: torch.Tensor, stream=None):
-    _dev(ao_in, torch.float32, "ao_in")
-    _dev(ao_out, torch.float32, "ao_out")
-    _check(lib().epbr_ssao_blur(C.byref(g.struct), C.byref(p.struct), ao_in.data_ptr(), _pitch(ao_in, 1),
-                                ao_out.data_ptr(), _pitch(ao_out, 1), _stream(stream)))
+    _check(lib().epbr_ssao_blur(C.byref(g.struct), C.byref(p.struct), _ao(g, p, ao_in, "ao_in"), _pitch(ao_in, 1),
+                                _ao(g, p, ao_out, "ao_out"), _pitch(ao_out, 1), _stream(stream)))
 
 
 def epbr_ssao(g: GBuffer, cam: F.epbr_camera, p: SsaoParams, ao: torch.Tensor, workspace=None, stream=None):
-    _dev(ao, torch.float32, "ao")
+    _ao(g, p, ao, "ao")
     n = C.c_size_t()
     _check(lib().epbr_ssao_workspace_size(C.byref(g.struct), C.byref(p.struct), C.byref(n)))
     ws = workspace if workspace is not None else _workspace(n.value, ao.device)
@@ -269,9 +303,9 @@ def _lights(lights: torch.Tensor | None):
 def epbr_shade(g: GBuffer, cam: F.epbr_camera, lights: torch.Tensor | None, ibl: Ibl | None,
                params: F.epbr_shade_params, hdr: torch.Tensor, hdr_format: int = EPBR_HDR_RGBA32F, stream=None):
     lp, nl = _lights(lights)
-    _dev(hdr, name="hdr")
+    hp = _image(hdr, g.struct.height, g.struct.width, 4, "hdr", _hdr_dtype(hdr_format))
     _check(lib().epbr_shade(C.byref(g.struct), C.byref(cam), lp, nl, C.byref(ibl.struct) if ibl else None,
-                            C.byref(params), hdr.data_ptr(), hdr_format, _pitch(hdr, 1), _stream(stream)))
+                            C.byref(params), hp, hdr_format, _pitch(hdr, 1), _stream(stream)))
 
 
 def tonemap_params(exposure: float = 1.0, op: int = EPBR_TONEMAP_ACES) -> F.epbr_tonemap_params:
@@ -282,18 +316,19 @@ def epbr_shade_tonemap(g: GBuffer, cam: F.epbr_camera, lights, ibl: Ibl | None, 
                        hdr: torch.Tensor | None, hdr_format: int, tp: F.epbr_tonemap_params, ldr: torch.Tensor,
                        stream=None):
     lp, nl = _lights(lights)
-    _dev(ldr, torch.uint8, "ldr")
-    hp, hpitch = (None, 0) if hdr is None else (_dev(hdr, name="hdr"), _pitch(hdr, 1))
+    H, W = g.struct.height, g.struct.width
+    dp = _image(ldr, H, W, 4, "ldr", torch.uint8)
+    hp, hpitch = (None, 0) if hdr is None else (_image(hdr, H, W, 4, "hdr", _hdr_dtype(hdr_format)), _pitch(hdr, 1))
     _check(lib().epbr_shade_tonemap(C.byref(g.struct), C.byref(cam), lp, nl, C.byref(ibl.struct) if ibl else None,
-                                    C.byref(params), hp, hdr_format, hpitch, C.byref(tp), ldr.data_ptr(),
+                                    C.byref(params), hp, hdr_format, hpitch, C.byref(tp), dp,
                                     _pitch(ldr, 1), _stream(stream)))
 
 
 def epbr_tonemap(hdr: torch.Tensor, hdr_format: int, tp: F.epbr_tonemap_params, out: torch.Tensor, stream=None):
-    _dev(hdr, name="hdr")
-    _dev(out, torch.uint8, "out")
     H, W = hdr.shape[0], hdr.shape[1]
-    _check(lib().epbr_tonemap(hdr.data_ptr(), hdr_format, W, H, _pitch(hdr, 1), C.byref(tp), out.data_ptr(),
+    hp = _image(hdr, H, W, 4, "hdr", _hdr_dtype(hdr_format))
+    op = _image(out, H, W, 4, "out", torch.uint8)
+    _check(lib().epbr_tonemap(hp, hdr_format, W, H, _pitch(hdr, 1), C.byref(tp), op,
                               _pitch(out, 1), _stream(stream)))
 
 
@@ -325,7 +360,7 @@ def epbr_raster_gbuffer(mesh: Mesh, cam: F.epbr_camera, near: float, out: GBuffe
     W, H = out.struct.width, out.struct.height
     need = epbr_raster_workspace_size(mesh.struct.num_triangles, W, H)
     ws = workspace if workspace is not None else _workspace(need, mesh.tensors[0].device)
-    ip = _dev(ids, torch.int32, "ids") if ids is not None else None
+    ip = _image(ids, H, W, None, "ids", torch.int32) if ids is not None else None
     _check(lib().epbr_raster_gbuffer(C.byref(mesh.struct), C.byref(cam), near, C.byref(out.struct), ip,
                                      _pitch(ids, 1) if ids is not None else 0, _aligned(ws),
                                      ws.numel() - (_aligned(ws) - ws.data_ptr()), _stream(stream)))
@@ -353,7 +388,7 @@ def epbr_surfel_gbuffer(surfels: Surfels, cam: F.epbr_camera, near: float, toler
     W, H = out.struct.width, out.struct.height
     need = epbr_surfel_workspace_size(surfels.struct.num_surfels, W, H)
     ws = workspace if workspace is not None else _workspace(need, surfels.tensors[0].device)
-    wp = _dev(weight, torch.float32, "weight") if weight is not None else None
+    wp = _image(weight, H, W, None, "weight", torch.float32) if weight is not None else None
     _check(lib().epbr_surfel_gbuffer(C.byref(surfels.struct), C.byref(cam), near, tolerance, C.byref(out.struct), wp,
                                      _pitch(weight, 1) if weight is not None else 0, _aligned(ws),
                                      ws.numel() - (_aligned(ws) - ws.data_ptr()), _stream(stream)))
@@ -369,9 +404,11 @@ def edl_params(strength: float = 8.0, radius: int = 1, directions: int = 8) -> F
 def epbr_edl(g: GBuffer, params: F.epbr_edl_params, hdr: torch.Tensor | None, hdr_format: int = EPBR_HDR_RGBA32F,
              ao: torch.Tensor | None = None, ao_scale: int = 2, tp: F.epbr_tonemap_params | None = None,
              ldr: torch.Tensor | None = None, stream=None):
-    ap = _dev(ao, torch.float32, "ao") if ao is not None else None
-    hp = _dev(hdr, name="hdr") if hdr is not None else None
-    dp = _dev(ldr, torch.uint8, "ldr") if ldr is not None else None
+    H, W = g.struct.height, g.struct.width
+    ap = _image(ao, (H + ao_scale - 1) // ao_scale, (W + ao_scale - 1) // ao_scale, None, "ao",
+                torch.float32) if ao is not None else None
+    hp = _image(hdr, H, W, 4, "hdr", _hdr_dtype(hdr_format)) if hdr is not None else None
+    dp = _image(ldr, H, W, 4, "ldr", torch.uint8) if ldr is not None else None
     _check(lib().epbr_edl(C.byref(g.struct), C.byref(params), ap, _pitch(ao, 1) if ao is not None else 0, ao_scale,
                           hp, hdr_format, _pitch(hdr, 1) if hdr is not None else 0,
                           C.byref(tp) if tp is not None else None, dp, _pitch(ldr, 1) if ldr is not None else 0,
@@ -401,8 +438,9 @@ def epbr_shade_shadows(g: GBuffer, cam: F.epbr_camera, lights, ibl: Ibl | None, 
                        shadows: Shadows, hdr: torch.Tensor | None, hdr_format: int,
                        tp: F.epbr_tonemap_params | None = None, ldr: torch.Tensor | None = None, stream=None):
     lp, nl = _lights(lights)
-    hp = _dev(hdr, name="hdr") if hdr is not None else None
-    dp = _dev(ldr, torch.uint8, "ldr") if ldr is not None else None
+    H, W = g.struct.height, g.struct.width
+    hp = _image(hdr, H, W, 4, "hdr", _hdr_dtype(hdr_format)) if hdr is not None else None
+    dp = _image(ldr, H, W, 4, "ldr", torch.uint8) if ldr is not None else None
     _check(lib().epbr_shade_shadows(C.byref(g.struct), C.byref(cam), lp, nl, C.byref(ibl.struct) if ibl else None,
                                     C.byref(params), C.byref(shadows.struct), hp, hdr_format,
                                     _pitch(hdr, 1) if hdr is not None else 0, C.byref(tp) if tp is not None else None,
@@ -426,12 +464,12 @@ def epbr_bloom_workspace_size(W: int, H: int, bp: F.epbr_bloom_params) -> int:
 def epbr_bloom(hdr: torch.Tensor, hdr_format: int, bp: F.epbr_bloom_params, out_hdr: torch.Tensor | None = None,
                out_format: int = EPBR_HDR_RGBA32F, tp: F.epbr_tonemap_params | None = None,
                ldr: torch.Tensor | None = None, workspace: torch.Tensor | None = None, stream=None):
-    _dev(hdr, name="hdr")
     H, W = hdr.shape[0], hdr.shape[1]
+    _image(hdr, H, W, 4, "hdr", _hdr_dtype(hdr_format))
     need = epbr_bloom_workspace_size(W, H, bp)
     ws = workspace if workspace is not None else _workspace(need, hdr.device)
-    op = _dev(out_hdr, name="out_hdr") if out_hdr is not None else None
-    lp = _dev(ldr, torch.uint8, "ldr") if ldr is not None else None
+    op = _image(out_hdr, H, W, 4, "out_hdr", _hdr_dtype(out_format)) if out_hdr is not None else None
+    lp = _image(ldr, H, W, 4, "ldr", torch.uint8) if ldr is not None else None
     _check(lib().epbr_bloom(hdr.data_ptr(), hdr_format, _pitch(hdr, 1), W, H, C.byref(bp), _aligned(ws),
                             ws.numel() - (_aligned(ws) - ws.data_ptr()), op, out_format,
                             _pitch(out_hdr, 1) if out_hdr is not None else 0, C.byref(tp) if tp is not None else None,
@@ -446,9 +484,10 @@ def view(g: GBuffer, cam: F.epbr_camera, lights: torch.Tensor | None, ibl_index:
     lp, nl = _lights(lights)
     v = F.epbr_view()
     v.gbuffer, v.camera, v.lights, v.num_lights, v.ibl_index = g.struct, cam, lp, nl, ibl_index
-    v.ldr, v.ldr_pitch = _dev(ldr, torch.uint8, "ldr"), _pitch(ldr, 1)
+    H, W = g.struct.height, g.struct.width
+    v.ldr, v.ldr_pitch = _image(ldr, H, W, 4, "ldr", torch.uint8), _pitch(ldr, 1)
     if hdr is not None:
-        v.hdr, v.hdr_pitch = _dev(hdr, name="hdr"), _pitch(hdr, 1)
+        v.hdr, v.hdr_pitch = _image(hdr, H, W, 4, "hdr"), _pitch(hdr, 1)
     return v
 
 

@@ -159,6 +159,7 @@ PROTOTYPES = {
     "epbr_ssao_raw": [P(epbr_gbuffer), P(epbr_camera), P(epbr_ssao_params), vp, i64, vp],
     "epbr_ssao_tiled": [P(epbr_gbuffer), P(epbr_ssao_params), P(i32)],
     "epbr_ssao_tile_timeouts": [P(C.c_uint32)],
+    "epbr_ssao_set_tile_wait": [C.c_uint64, P(C.c_uint64)],
     "epbr_ssao_blur": [P(epbr_gbuffer), P(epbr_ssao_params), vp, i64, vp, i64, vp],
     "epbr_ssao": [P(epbr_gbuffer), P(epbr_camera), P(epbr_ssao_params), vp, i64, vp, sz, vp],
     "epbr_shade": [P(epbr_gbuffer), P(epbr_camera), vp, i32, P(epbr_ibl), P(epbr_shade_params), vp, i32,

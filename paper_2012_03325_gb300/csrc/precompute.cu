@@ -5,6 +5,8 @@
 //   k_irradiance_final  sums the partials in a fixed order (deterministic) and normalises
 //   k_prefilter         GGX-prefiltered levels 1..M-1, one thread per output texel, the level's
 //                       sample set tabulated once per block in shared memory
+#include <cuda.h>  // CUcontext and CUresult for the context queries (fetched at run time)
+
 #include <algorithm>
 #include <mutex>
 
@@ -331,26 +333,64 @@ constexpr size_t kStaticScratchBytes = (size_t)8 << 20;  // 8 MiB: 32x16 outputs
 static __device__ __align__(256) float4 g_irr_scratch[kStaticScratchBytes / sizeof(float4)];
 
 constexpr int kMaxDevices = 64;
-static std::mutex g_scratch_mutex;
-static void* g_scratch_addr[kMaxDevices];  // device address of g_irr_scratch, per device
 
-// Device address of g_irr_scratch on the current device.  In host code the name g_irr_scratch
-// is only a host-side handle, so the address is asked from the runtime once per device (with
-// that device current) and cached.
+// The array's device address is per context: a caller may run its own driver context on a
+// device instead of the primary one, and a device reset gives the device a new primary context
+// (with the array loaded afresh).  The cache therefore keeps, per device, the unique id of the
+// context the address was looked up in (cuCtxGetId, never reused within a process) and looks
+// the address up again when the current context is another one.
+struct ScratchSlot {
+  unsigned long long ctx_id;
+  void* addr;
+};
+static std::mutex g_scratch_mutex;
+static ScratchSlot g_scratch_slot[kMaxDevices];
+
+typedef CUresult (*CtxGetCurrentFn)(CUcontext*);
+typedef CUresult (*CtxGetIdFn)(CUcontext, unsigned long long*);
+
+template <typename Fn>
+static Fn driver_fn(const char* name) {
+  void* f = nullptr;
+  cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+  if (cudaGetDriverEntryPointByVersion(name, &f, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+      q != cudaDriverEntryPointSuccess)
+    return nullptr;
+  return (Fn)f;
+}
+
+// Unique id of the calling thread's current context (0 and false when there is none).
+static bool current_ctx_id(unsigned long long* id) {
+  static const CtxGetCurrentFn get_cur = driver_fn<CtxGetCurrentFn>("cuCtxGetCurrent");
+  static const CtxGetIdFn get_id = driver_fn<CtxGetIdFn>("cuCtxGetId");
+  CUcontext ctx = nullptr;
+  if (!get_cur || !get_id || get_cur(&ctx) != CUDA_SUCCESS || !ctx) return false;
+  return get_id(ctx, id) == CUDA_SUCCESS;
+}
+
+// Device address of g_irr_scratch in the current context.  In host code the name g_irr_scratch
+// is only a host-side handle, so the address is asked from the runtime (with the device current)
+// once per device and context and cached.
 static epbr_status static_scratch(void** out) {
   int dev = -1;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return fail(EPBR_ERR_CUDA, "irradiance_noalloc: cudaGetDevice: %s", cudaGetErrorString(e));
   if (dev < 0 || dev >= kMaxDevices) return fail(EPBR_ERR_UNSUPPORTED, "irradiance_noalloc: device %d", dev);
   std::lock_guard<std::mutex> lock(g_scratch_mutex);
-  if (!g_scratch_addr[dev]) {
+  unsigned long long id = 0;
+  bool have_id = current_ctx_id(&id);
+  ScratchSlot& slot = g_scratch_slot[dev];
+  if (!have_id || !slot.addr || slot.ctx_id != id) {
     void* p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_irr_scratch);
+    e = cudaGetSymbolAddress(&p, g_irr_scratch);  // also makes the primary context current if none is
     if (e != cudaSuccess || !p)
       return fail(EPBR_ERR_CUDA, "irradiance_noalloc: cudaGetSymbolAddress: %s", cudaGetErrorString(e));
-    g_scratch_addr[dev] = p;
+    if (!have_id && !current_ctx_id(&id))
+      return fail(EPBR_ERR_CUDA, "irradiance_noalloc: no current context after the symbol lookup");
+    slot.ctx_id = id;
+    slot.addr = p;
   }
-  *out = g_scratch_addr[dev];
+  *out = slot.addr;
   return EPBR_OK;
 }
 

@@ -214,7 +214,6 @@ __device__ __forceinline__ bool stage_lights(float4* s_lights, const float4* __r
 // monochrome lights (Ic_r = Ic_g = Ic_b) the three channels share one sum each.
 struct Direct {
   float3 sa, sb, sbf;  // sums of Ic w (1 - fc), Ic w spec', Ic w spec' fc
-  float3 nxv;          // n x v: n x (l + v) = (n x L) / |L| + n x v
   float a2vv, alpha, nva, k, omk;  // nva = alpha n.v: alpha (n.l + n.v) = fma(n.l, alpha, nva)
 };
 
@@ -227,14 +226,14 @@ __device__ __forceinline__ Direct px_direct_begin(const Px& s) {
   d.k = (s.rough + 1.0f) * (s.rough + 1.0f) * 0.125f;
   d.omk = 1.0f - d.k;
   d.a2vv = alpha * alpha * rcp_ftz(4.0f * kPi * fmaf(s.nv, d.omk, d.k));  // alpha^2 G1(v) / (4 pi n.v)
-  d.nxv = cross3(s.n, s.v);
   return d;
 }
 
 // Scalar light terms shared by both loops.  Guards are folded into existing FMAs: |L|^2 + 1e-30
 // (a light at P contributes 0) and |n x s|^2 + 1e-18 (keeps the GGX denominator normal when
-// l = -v) change a result by < 1e-12 relative; |l + v|^2 biased by 1e-6 (>= 0 under rounding)
-// changes the term of a light behind a grazing view (l ~ -v) by up to ~2e-6 / (n.v)^2 relative.
+// l = -v) change a result by < 1e-12 relative.  The half vector s = l + v is formed explicitly,
+// so |s|^2 is a sum of squares (never negative) and needs no bias, also for a light behind a
+// grazing view (l ~ -v, where 2 + 2 l.v would cancel).
 struct LightTerms {
   float a, b, bf;
 };
@@ -246,13 +245,11 @@ __device__ __forceinline__ LightTerms light_terms(const Px& s, const Direct& d, 
   float3 l = L * rs;
   float nl = dot3(s.n, l);
   float nlc = fmaxf(nl, 0.0f);
-  float lv = dot3(s.v, l);
-  // n x (l + v) = n x l + n x v, accumulated onto the per-pixel n x v
-  float3 c = f3(fmaf(s.n.y, l.z, fmaf(-s.n.z, l.y, d.nxv.x)), fmaf(s.n.z, l.x, fmaf(-s.n.x, l.z, d.nxv.y)),
-                fmaf(s.n.x, l.y, fmaf(-s.n.y, l.x, d.nxv.z)));
+  float3 h = f3(fmaf(L.x, rs, s.v.x), fmaf(L.y, rs, s.v.y), fmaf(L.z, rs, s.v.z));  // s = l + v
+  float3 c = cross3(s.n, h);                                                        // n x s
   float c2 = fmaf(c.x, c.x, fmaf(c.y, c.y, fmaf(c.z, c.z, 1e-18f)));
   float nsa = fmaf(nl, d.alpha, d.nva);  // alpha n.(l + v)
-  float hh = fmaf(2.0f, lv, 2.000001f);  // |l + v|^2
+  float hh = fmaf(h.x, h.x, fmaf(h.y, h.y, h.z * h.z));  // |s|^2
   float den = fmaf(nsa, nsa, c2);
   float xx = fmaf(-0.5f, sqrt_ftz(hh), 1.0f);  // 1 - v.h, v.h = |l + v| / 2
 #ifdef EPBR_FC_POW5

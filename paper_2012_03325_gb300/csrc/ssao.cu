@@ -14,6 +14,8 @@
 #include <cuda.h>  // CUtensorMap and its encoder's enums (the encoder is fetched at run time)
 #include <string.h>
 
+#include <atomic>
+
 #include "ssao_core.cuh"
 
 namespace epbr {
@@ -78,9 +80,13 @@ constexpr unsigned kSsaoTileN = kSsaoTileW * kSsaoTileH;
 constexpr unsigned kSsaoTileBytes = kSsaoTileN * 4;
 constexpr unsigned long long kTmaWaitNs = 50ull * 1000 * 1000;  // a tile copy takes microseconds
 
-// Warps of k_ssao_raw<TILED> whose tile copy did not complete within kTmaWaitNs (their taps then
-// all read the depth plane, so the AO is unaffected); read and cleared by epbr_ssao_tile_timeouts.
+// Warps of k_ssao_raw<TILED> whose first wait for their tile copy ran out (their taps then all
+// read the depth plane, so the AO is unaffected); read and cleared by epbr_ssao_tile_timeouts.
 __device__ unsigned int g_ssao_tile_timeouts;
+// Set when a block's second (drain) wait ran out too, so that it exited with its copy possibly
+// still in flight towards shared memory another block may reuse: the AO of such a launch is
+// suspect.  Read and cleared by epbr_ssao_tile_timeouts, which then reports an error.
+__device__ unsigned int g_ssao_tile_lost;
 
 __device__ __forceinline__ unsigned smem_addr(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
 
@@ -205,7 +211,7 @@ __device__ __forceinline__ float2 ssao_samples(const SsaoRows& a, const SsaoRows
 template <int FMT, bool TILED>
 __global__ void __launch_bounds__(256, TILED ? EPBR_SSAO_TILED_MIN_BLOCKS : EPBR_SSAO_MIN_BLOCKS)
     k_ssao_raw(const __grid_constant__ CUtensorMap depth_map, GbufDev g, CamDev cam, SsaoDev p,
-               float* __restrict__ ao, long long ao_pitch, int Wa, int Ha) {
+               float* __restrict__ ao, long long ao_pitch, int Wa, int Ha, unsigned long long wait_ns) {
   __shared__ float4 s_kernel[kMaxSsaoSamples];
   __shared__ __align__(8) unsigned long long s_bar;
   extern __shared__ __align__(128) float s_dep[];  // TILED: kSsaoTileH x kSsaoTileW depths
@@ -223,7 +229,8 @@ __global__ void __launch_bounds__(256, TILED ? EPBR_SSAO_TILED_MIN_BLOCKS : EPBR
   const bool s0 = in0 && is_surface(e0), s1 = in1 && is_surface(e1);
   bool tile_ok = false, from_tile = false;
   if (TILED) {
-    tile_ok = mbar_wait_bounded(smem_addr(&s_bar), 0, kTmaWaitNs);
+    // wait_ns = 0 gives up at once (the fallback path, exercised by a test)
+    tile_ok = wait_ns != 0 && mbar_wait_bounded(smem_addr(&s_bar), 0, wait_ns);
     if (!tile_ok && threadIdx.x == 0) atomicAdd(&g_ssao_tile_timeouts, 1u);
     // the longest kernel offset, over the warp's lanes
     float k2 = 0.0f;
@@ -249,8 +256,10 @@ __global__ void __launch_bounds__(256, TILED ? EPBR_SSAO_TILED_MIN_BLOCKS : EPBR
   if (in0 && !s0) ((float*)((char*)ao + (size_t)j0 * ao_pitch))[i] = 1.0f;
   if (in1 && !s1) ((float*)((char*)ao + (size_t)j1 * ao_pitch))[i] = 1.0f;
   // A copy that had not landed is waited for once more (bounded) so that it does not write into
-  // the shared memory of a block that starts on this SM after this one.
-  if (TILED && !tile_ok) mbar_wait_bounded(smem_addr(&s_bar), 0, kTmaWaitNs);
+  // the shared memory of a block that starts on this SM after this one; if that wait runs out
+  // too, the launch is flagged.
+  if (TILED && !tile_ok && !mbar_wait_bounded(smem_addr(&s_bar), 0, kTmaWaitNs) && threadIdx.x == 0)
+    atomicOr(&g_ssao_tile_lost, 1u);
 }
 
 // Blur tile: 32x8 AO texels plus a halo of R <= 8 texels, AO values and the depths of their
@@ -399,6 +408,10 @@ static EncodeTiledFn encode_tiled() {
 // the untiled form, at its higher occupancy, is used.
 constexpr int kSsaoTiledMaxRows = 1536;
 
+// Limit of the tiled form's first wait for its depth tile, passed to every launch; changed only
+// by epbr_ssao_set_tile_wait (a test of the fallback path sets 0).
+static std::atomic<unsigned long long> g_tile_wait_ns{kTmaWaitNs};
+
 static bool depth_tile_map(const epbr_gbuffer* g, const epbr_ssao_params* p, CUtensorMap* map) {
   if (p->scale != 2 || g->height > kSsaoTiledMaxRows || (uintptr_t)g->rt[3] % 16 || g->pitch[3] % 16 ||
       g->pitch[3] >= (1ll << 40))
@@ -457,17 +470,17 @@ extern "C" epbr_status epbr_ssao_raw(const epbr_gbuffer* g, const epbr_camera* c
   if (!tiled) memset(&map, 0, sizeof(map));  // unused by the untiled form
   const bool fp32 = g->format == EPBR_GBUFFER_FP32;
   if (tiled) {
-    void (*k)(const CUtensorMap, GbufDev, CamDev, SsaoDev, float*, long long, int, int) =
+    void (*k)(const CUtensorMap, GbufDev, CamDev, SsaoDev, float*, long long, int, int, unsigned long long) =
         fp32 ? k_ssao_raw<EPBR_GBUFFER_FP32, true> : k_ssao_raw<EPBR_GBUFFER_COMPACT, true>;
     // the 48 KB tile is above the default dynamic shared-memory limit; the attribute is per
     // function and device, and setting it again is harmless
     if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSsaoTileBytes) != cudaSuccess)
       return fail(EPBR_ERR_CUDA, "ssao_raw: shared-memory attribute: %s", cudaGetErrorString(cudaGetLastError()));
-    k<<<grd, blk, kSsaoTileBytes, s>>>(map, gd, cd, sd, ao, ao_pitch, Wa, Ha);
+    k<<<grd, blk, kSsaoTileBytes, s>>>(map, gd, cd, sd, ao, ao_pitch, Wa, Ha, g_tile_wait_ns.load());
   } else if (fp32)
-    k_ssao_raw<EPBR_GBUFFER_FP32, false><<<grd, blk, 0, s>>>(map, gd, cd, sd, ao, ao_pitch, Wa, Ha);
+    k_ssao_raw<EPBR_GBUFFER_FP32, false><<<grd, blk, 0, s>>>(map, gd, cd, sd, ao, ao_pitch, Wa, Ha, 0ull);
   else
-    k_ssao_raw<EPBR_GBUFFER_COMPACT, false><<<grd, blk, 0, s>>>(map, gd, cd, sd, ao, ao_pitch, Wa, Ha);
+    k_ssao_raw<EPBR_GBUFFER_COMPACT, false><<<grd, blk, 0, s>>>(map, gd, cd, sd, ao, ao_pitch, Wa, Ha, 0ull);
   if ((st = check_launch("k_ssao_raw"))) return st;
   return ok();
 }
@@ -484,12 +497,28 @@ extern "C" epbr_status epbr_ssao_tiled(const epbr_gbuffer* g, const epbr_ssao_pa
 
 extern "C" epbr_status epbr_ssao_tile_timeouts(uint32_t* count) {
   if (!count) return fail(EPBR_ERR_INVALID_ARG, "count is NULL");
-  unsigned v = 0;
+  unsigned v = 0, lost = 0;
   const unsigned zero = 0;
   if (cudaMemcpyFromSymbol(&v, g_ssao_tile_timeouts, sizeof(v)) != cudaSuccess ||
-      cudaMemcpyToSymbol(g_ssao_tile_timeouts, &zero, sizeof(zero)) != cudaSuccess)
+      cudaMemcpyToSymbol(g_ssao_tile_timeouts, &zero, sizeof(zero)) != cudaSuccess ||
+      cudaMemcpyFromSymbol(&lost, g_ssao_tile_lost, sizeof(lost)) != cudaSuccess ||
+      cudaMemcpyToSymbol(g_ssao_tile_lost, &zero, sizeof(zero)) != cudaSuccess)
     return fail(EPBR_ERR_CUDA, "ssao_tile_timeouts: %s", cudaGetErrorString(cudaGetLastError()));
   *count = v;
+  if (lost)
+    return fail(EPBR_ERR_DEVICE_STATUS,
+                "ssao_tile_timeouts: a block's depth-tile copy did not complete within two waits of %llu ms; "
+                "the AO of launches since the last call is suspect",
+                (unsigned long long)(kTmaWaitNs / 1000000));
+  return ok();
+}
+
+extern "C" epbr_status epbr_ssao_set_tile_wait(uint64_t first_wait_ns, uint64_t* previous_ns) {
+  if (first_wait_ns > kTmaWaitNs)
+    return fail(EPBR_ERR_INVALID_ARG, "ssao_set_tile_wait: %llu ns above the default %llu ns",
+                (unsigned long long)first_wait_ns, (unsigned long long)kTmaWaitNs);
+  const unsigned long long prev = g_tile_wait_ns.exchange(first_wait_ns);
+  if (previous_ns) *previous_ns = prev;
   return ok();
 }
 

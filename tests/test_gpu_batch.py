@@ -137,3 +137,62 @@ def test_batch_colored_lights_equal_per_view():
             g, r = hdr.cpu().numpy()[..., :3], rh.cpu().numpy()[..., :3]
             assert (np.abs(g - r) / np.maximum(np.abs(r), 1e-6)).max() <= 1e-6
     b.close()
+
+
+@pytest.mark.parametrize("compact,hdr16", [(False, False), (True, True)])
+def test_batch_hdr_against_oracle(compact, hdr16):
+    """Linear HDR of batched views against the oracle (blurred SSAO, compose) for both modes:
+    a view with 256 lights and one with 300 (two light chunks), FP32 G-buffers with RGBA32F output
+    (1e-4) and compact G-buffers with RGBA16F output (2e-3 after the oracle's value is rounded to
+    FP16); pixels whose AO texel has a tied decision are left out."""
+    from _common import REL_TOL_REDUCED, check_hdr, fp16_round
+    specs = [(200, 120, 256, 1), (96, 64, 300, 0), (33, 17, 5, 1)]
+    envs = [synth.make_env(s, 128, 64) for s in (0, 5)]
+    base = make_inputs("small")
+    ibls, oibls = [], []
+    for e in envs:
+        inp = make_inputs("small")
+        inp.env = e
+        ibls.append(gpu_ibl(inp, torch.from_numpy(e).cuda()))
+        oibls.append(oracle.precompute_ibl(e, 6, 256, 32, 256, 32, 16))
+    hdt = torch.float16 if hdr16 else torch.float32
+    views, keep, per = [], [], []
+    for W, H, NL, ei in specs:
+        inp = make_inputs("small", W=W, H=H, lights=NL)
+        d = gpu_inputs(inp, compact=compact)
+        ldr = torch.zeros(H, W, 4, dtype=torch.uint8, device="cuda")
+        hdr = torch.zeros(H, W, 4, dtype=hdt, device="cuda")
+        views.append(ep.view(d["gb"], d["cam"], d["lights"], ei, ldr, hdr))
+        keep += [d, ldr, hdr]
+        per.append((inp, hdr, ei))
+    kernel, noise = torch.from_numpy(base.kernel).cuda(), torch.from_numpy(base.noise).cuda()
+    sp = ep.SsaoParams(kernel, noise, radius=0.5, scale=2, blur_radius=3)
+    keep += [kernel, noise, sp]
+    fmt = ep.EPBR_HDR_RGBA16F if hdr16 else ep.EPBR_HDR_RGBA32F
+    b = ep.Batch(views, ibls, ep.batch_params(sp, hdr_format=fmt), keep=keep)
+    refs = []
+    for inp, _, ei in per:
+        gb = decoded(inp, compact)
+        cam = oracle_camera(inp)
+        a, lo, hi = oracle.ssao(gb, cam, K=16, scale=2, radius=0.5, bias=0.025, blur_radius=3, sigma_s=2.0,
+                                sigma_z=0.1, kernel=inp.kernel, noise=inp.noise, blurred=True)
+        ref = oracle.shade(gb, cam, inp.lights, oibls[ei], ep.EPBR_SHADE_ALL, ao=a, ao_scale=2)
+        tied = np.repeat(np.repeat(lo != hi, 2, 0), 2, 1)[:inp.H, :inp.W].reshape(-1)
+        refs.append((gb, cam, a, ref, tied))
+    try:
+        for md in (ep.F.EPBR_BATCH_FUSED, ep.F.EPBR_BATCH_STAGED):
+            b.set_plan(md, 64, 32, 128)
+            b.launch()
+            torch.cuda.synchronize()
+            for (inp, hdr, ei), (gb, cam, a, ref, tied) in zip(per, refs):
+                g = hdr.float().cpu().numpy()[..., :3].reshape(-1, 3)
+                r = ref.reshape(-1, 3)
+                keep_px = np.nonzero(~tied)[0]
+                assert len(keep_px) > 0.8 * len(tied)
+                if hdr16:
+                    check_hdr(g[keep_px], fp16_round(r[keep_px]), REL_TOL_REDUCED)
+                else:
+                    check_hdr(g[keep_px], r[keep_px], REL_TOL_FP32, gb=gb, cam=cam, lights=inp.lights, ibl=oibls[ei],
+                              flags=ep.EPBR_SHADE_ALL, ao=a, ao_scale=2, pixels=keep_px)
+    finally:
+        b.close()

@@ -4,6 +4,8 @@ Inputs are generated (synth.make_bloom_field / make_hdr_field), never taken from
 HDR rule: 1e-4 relative (FP32 output), 2e-3 with an FP16 image on either side; 8-bit rule: 1 LSB,
 99.9% identical.  The bright-map decision is the same FP32 expression on both sides, so the
 bright maps are identical."""
+import ctypes
+
 import numpy as np
 import pytest
 
@@ -137,7 +139,13 @@ def test_bloom_invalid_arguments():
         ep.epbr_bloom(x, ep.EPBR_HDR_RGBA32F, bp, out, ep.EPBR_HDR_RGBA32F,
                       workspace=torch.empty(64, dtype=torch.uint8, device="cuda"))
     h16 = torch.zeros(8, 8, 4, dtype=torch.float16, device="cuda")
-    with pytest.raises(ep.EpbrError):  # in place with another format
+    with pytest.raises(ValueError):  # the binding checks the output's dtype against its format
         ep.epbr_bloom(x, ep.EPBR_HDR_RGBA32F, bp, x, ep.EPBR_HDR_RGBA16F)
+    ws = torch.empty(ep.epbr_bloom_workspace_size(8, 8, bp) + 256, dtype=torch.uint8, device="cuda")
+    wsp = (ws.data_ptr() + 255) & ~255
+    st = ep.lib().epbr_bloom(x.data_ptr(), ep.EPBR_HDR_RGBA32F, 128, 8, 8, ctypes.byref(bp), wsp, ws.numel() - 256,
+                             x.data_ptr(), ep.EPBR_HDR_RGBA16F, 128, None, None, 0,
+                             torch.cuda.current_stream().cuda_stream)
+    assert st == 1  # in place with another format: refused by the library itself
     with pytest.raises(ep.EpbrError):  # ldr without tone-map parameters
         ep.epbr_bloom(h16, ep.EPBR_HDR_RGBA16F, bp, None, 0, None, torch.zeros(8, 8, 4, dtype=torch.uint8, device="cuda"))

@@ -321,3 +321,45 @@ def test_padded_row_pitches():
         outs.append((ao.cpu(), hdr.cpu(), ldr.cpu()))
     for a, b in zip(*outs):
         assert torch.equal(a, b)
+
+
+@pytest.mark.parametrize("nv", [0.1, 0.03])
+@pytest.mark.parametrize("el", [0.005, 0.02])
+def test_shade_colored_light_behind_a_grazing_view(nv, el):
+    """One coloured light just above the horizon behind a grazing view (n.v = 0.1, 0.03): there
+    l is close to -v, so |l + v|^2 is small and a form that cancels (2 + 2 l.v) loses it.  The
+    colour loop forms s = l + v explicitly; its direct term must match the oracle at 1e-4."""
+    rng = np.random.default_rng(int(nv * 1000 + el * 1e5))
+    eye = np.eye(4)
+    cam_t = ep.camera(eye.T.reshape(-1), np.radians(60.0), 1, 1)
+    cam_o = oracle.camera(eye.T.reshape(-1), np.radians(60.0), 1, 1)
+    P = np.array([0.0, 0.0, -3.0])
+    v = np.array([0.0, 0.0, 1.0])
+    for metal, rough in ((1.0, 1.0), (0.0, 0.6), (1.0, 0.3), (0.0, 0.15)):
+        for _ in range(3):
+            phi = rng.uniform(0, 2 * np.pi)
+            n = np.array([np.sqrt(1 - nv * nv) * np.cos(phi), np.sqrt(1 - nv * nv) * np.sin(phi), nv])
+            n = n.astype(np.float32).astype(np.float64)
+            tv = v - (v @ n) * n
+            tv /= np.linalg.norm(tv)
+            l = -np.cos(el) * tv + np.sin(el) * n
+            albedo = rng.uniform(0.2, 1.0, 3)
+            light = np.zeros((1, 8), np.float32)
+            light[0, :3] = P + 5.0 * l
+            light[0, 3] = 20.0
+            light[0, 4:7] = rng.uniform(0.1, 1.0, 3)
+            rt0 = np.zeros((1, 1, 4), np.float32)
+            rt0[0, 0, :3], rt0[0, 0, 3] = albedo, metal
+            rt1 = np.zeros((1, 1, 4), np.float32)
+            rt1[0, 0, :3], rt1[0, 0, 3] = n, rough
+            depth = np.full((1, 1), 3.0, np.float32)
+            t = lambda a: torch.from_numpy(a).cuda()
+            g = ep.GBuffer.fp32(t(rt0), t(rt1), t(depth))
+            hdr = torch.zeros(1, 1, 4, device="cuda")
+            ep.epbr_shade(g, cam_t, t(light), None, ep.shade_params(ep.EPBR_SHADE_DIRECT), hdr)
+            gb = oracle.decode_fp32(rt0, rt1, depth)
+            ref = oracle.shade(gb, cam_o, light, None, ep.EPBR_SHADE_DIRECT)
+            got = np_(hdr)[..., :3]
+            assert ref.max() > 0
+            rel = np.abs(got - ref) / np.abs(ref).max()
+            assert rel.max() <= REL_TOL_FP32, (metal, rough, phi, rel.max())

@@ -5,7 +5,8 @@ deadline passes."""
 import numpy as np
 import pytest
 
-from _common import gpu_ibl, gpu_inputs, make_inputs
+import oracle
+from _common import check_ldr, decoded, gpu_ibl, gpu_inputs, make_inputs, oracle_camera, sample_pixels
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -132,3 +133,76 @@ def test_destroy_cancels_queued_requests(env):
         r, _, keep = _request(srv, inp, ei)
         srv.submit(r, keep)
     srv.close()  # must return: admitted work completes, queued work is cancelled
+
+
+# every resolution class of the serving workload, FP32 and compact G-buffers, two lighting sets
+ORACLE_MIX = [(256, 256, 3, 0, False), (512, 512, 37, 1, True), (1920, 1080, 256, 0, True),
+              (3840, 2160, 1, 1, False), (512, 512, 9, 0, False), (256, 256, 120, 1, True)]
+
+
+def _oracle_ldr_sampled(inp, ei, compact, sp_args, envs, pixels):
+    """Oracle RGBA8 of the sampled pixels (blurred AO of the texels they read, compose, tone map)
+    and which of them read an AO texel with a tied decision."""
+    gb = decoded(inp, compact)
+    cam = oracle_camera(inp)
+    Wa, Ha = (inp.W + 1) // 2, (inp.H + 1) // 2
+    px, py = pixels % inp.W, pixels // inp.W
+    tex = np.unique((py // 2) * Wa + px // 2)
+    a, lo, hi = oracle.ssao(gb, cam, blurred=True, texels=tex, kernel=inp.kernel, noise=inp.noise, **sp_args)
+    ao = np.ones(Ha * Wa)
+    ao[tex] = a
+    tied = np.zeros(Ha * Wa, bool)
+    tied[tex] = lo != hi
+    ref = oracle.shade(gb, cam, inp.lights, envs[ei], ep.EPBR_SHADE_ALL, ao=ao.reshape(Ha, Wa), ao_scale=2,
+                       pixels=pixels)
+    out, scaled = oracle.tonemap(ref)
+    return out, scaled, tied[(py // 2) * Wa + px // 2]
+
+
+def test_served_mix_against_oracle():
+    """A mix of requests (every resolution class of the serving workload, FP32 and compact
+    G-buffers, 1-256 lights, two resident lighting sets) submitted together: every result is
+    checked on sampled pixels against the oracle's blurred SSAO, compose and tone map with the
+    8-bit rule (pixels whose AO texel has a tied decision are left out, as in the batch test)."""
+    base = make_inputs("small")
+    env_seeds = (0, 5)
+    ibls, oibls = [], []
+    for seed in env_seeds:
+        inp = make_inputs("small")
+        inp.env = synth.make_env(seed, 128, 64)
+        ibls.append(gpu_ibl(inp, torch.from_numpy(inp.env).cuda()))
+        c = inp.cfg
+        oibls.append(oracle.precompute_ibl(inp.env, c["levels"], c["prefilter_samples"], c["lut"], c["lut_samples"],
+                                           *c["irr"]))
+    k, nz = torch.from_numpy(base.kernel).cuda(), torch.from_numpy(base.noise).cuda()
+    sp = ep.SsaoParams(k, nz, radius=0.5, scale=2, blur_radius=3)
+    sp_args = dict(K=base.cfg["ssao_k"], scale=2, radius=0.5, bias=0.025, blur_radius=3, sigma_s=2.0, sigma_z=0.1)
+    srv = ep.Server(ibls, sp, memory_budget=2 << 30, max_in_flight=8, num_streams=4)
+    try:
+        jobs = []
+        for W, H, NL, ei, compact in ORACLE_MIX:
+            inp = make_inputs("small", W=W, H=H, lights=NL)
+            if compact:
+                c = inp.compact()
+                rts = [c.rt0, c.rt1, c.rt2, c.depth]
+                fmt = ep.EPBR_GBUFFER_COMPACT
+            else:
+                rts = [inp.g.rt0, inp.g.rt1, None, inp.g.depth]
+                fmt = ep.EPBR_GBUFFER_FP32
+            rts = [None if a is None else np.ascontiguousarray(a) for a in rts]
+            cam = ep.camera(inp.scene.camera_array(), inp.scene.fov_y, W, H)
+            out = np.zeros((H, W, 4), np.uint8)
+            lights = np.ascontiguousarray(inp.lights)
+            r = srv.request(fmt, rts, cam, lights, ei, out)
+            jobs.append((srv.submit(r, (rts, lights, out)), inp, ei, compact, out))
+        for t, inp, ei, compact, out in jobs:
+            res = srv.wait(t)
+            assert res.status == 0, res.message
+            pixels = sample_pixels(inp.W, inp.H, 1500, seed=inp.W + inp.H)
+            ref8, scaled, tied = _oracle_ldr_sampled(inp, ei, compact, sp_args, oibls, pixels)
+            g = out.reshape(-1, 4)[pixels]
+            assert (~tied).mean() > 0.8
+            check_ldr(g[~tied], ref8[~tied], scaled[~tied])
+        assert srv.stats().failed == 0
+    finally:
+        srv.close()

@@ -78,3 +78,36 @@ def test_ssao_scale1_untiled():
     d = gpu_inputs(inp)
     p = ep.SsaoParams(d["kernel"], d["noise"], radius=0.5, scale=1, blur_radius=3)
     assert not ep.epbr_ssao_tiled(d["gb"], p)
+
+
+@pytest.mark.parametrize("W,H", [(300, 170), (64, 32)])
+def test_ssao_tiled_wait_runs_out(W, H):
+    """The bounded wait's fallback path: with the first-wait limit at 0 every tiled warp gives up
+    on its depth tile at once, reads its taps from the depth plane and counts itself.  The AO is
+    the untiled form's bit for bit, the count is the number of warps launched (8 per block), and
+    the drain wait before a block exits still sees its copy land (no lost-copy error)."""
+    inp = make_inputs("small", W=W, H=H)
+    d = gpu_inputs(inp)
+    p = ep.SsaoParams(d["kernel"], d["noise"], radius=inp.cfg["radius"], scale=2, blur_radius=3)
+    twin, _keep = _untiled_twin(d["gb"], W, H)
+    assert ep.epbr_ssao_tiled(d["gb"], p) and not ep.epbr_ssao_tiled(twin, p)
+    Ha, Wa = p.ao_shape(W, H)
+    plain = torch.full((Ha, Wa), -2.0, device="cuda")
+    ep.epbr_ssao_raw(twin, d["cam"], p, plain)
+    torch.cuda.synchronize()
+    assert ep.epbr_ssao_tile_timeouts() == 0
+    tiled = torch.full((Ha, Wa), -1.0, device="cuda")
+    prev = ep.epbr_ssao_set_tile_wait(0)
+    try:
+        ep.epbr_ssao_raw(d["gb"], d["cam"], p, tiled)
+        torch.cuda.synchronize()
+    finally:
+        assert ep.epbr_ssao_set_tile_wait(prev) == 0
+    blocks = ((Wa + 31) // 32) * ((Ha + 15) // 16)
+    assert ep.epbr_ssao_tile_timeouts() == 8 * blocks
+    assert torch.equal(tiled, plain)
+    # with the default limit restored nothing times out
+    ep.epbr_ssao_raw(d["gb"], d["cam"], p, tiled)
+    torch.cuda.synchronize()
+    assert ep.epbr_ssao_tile_timeouts() == 0
+    assert torch.equal(tiled, plain)

@@ -41,6 +41,37 @@ def test_noalloc_matches_workspace_version_on_two_calls_in_a_row():
         assert (np.abs(g - r) / np.maximum(np.abs(r), 1e-30)).max() <= REL_TOL_FP32
 
 
+def test_noalloc_call_allocates_no_device_memory():
+    """The reason the entry point exists: after a first call (which loads the library's module,
+    and with it the static scratch array, and looks the array's address up), further calls take
+    no device memory.  Measured with cudaMemGetInfo around a second call, every tensor allocated
+    beforehand; device allocations come in pages of at least 2 MiB, so any allocation by the call
+    would lower the free bytes by at least that much."""
+    env_t = torch.from_numpy(synth.make_env(1000, 2048, 1024)).cuda()
+    out = torch.zeros(16, 32, 4, device="cuda")
+    ep.epbr_irradiance_noalloc(env_t, 32, 16, out)
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    ep.epbr_irradiance_noalloc(env_t, 32, 16, out)
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free0 - free1 < (2 << 20), (free0, free1)
+
+
+def test_noalloc_binding_rejects_an_undersized_output():
+    """The binding refuses an output that cannot hold irr_h x irr_w float4 (or is not dense)
+    before any call into the library, so no kernel writes past its end."""
+    env_t = torch.from_numpy(synth.make_env(7, 128, 64)).cuda()
+    small = torch.full((10, 20, 3), 7.0, device="cuda")  # 600 floats < 10 x 20 x 4
+    with pytest.raises(ValueError):
+        ep.epbr_irradiance_noalloc(env_t, 20, 10, small)
+    strided = torch.full((10, 40, 4), 7.0, device="cuda")[:, ::2]  # enough elements, not dense
+    with pytest.raises(ValueError):
+        ep.epbr_irradiance_noalloc(env_t, 20, 10, strided)
+    torch.cuda.synchronize()
+    assert (small == 7.0).all() and (strided == 7.0).all()
+
+
 def test_noalloc_rejects_requests_beyond_the_static_scratch():
     env_t = torch.from_numpy(synth.make_env(3, 2048, 1024)).cuda()
     out = torch.zeros(32, 64, 4, device="cuda")  # 2048 outputs x 608 blocks x 16 B > 8 MiB
