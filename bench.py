@@ -46,6 +46,8 @@ def parse():
     ap.add_argument("--serve-streams", type=int, default=8, help="server streams (serve workload)")
     ap.add_argument("--serve-inflight", type=int, default=16, help="server requests in flight (serve workload)")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="CPU-baseline time budget")
+    ap.add_argument("--no-system-forms", action="store_true",
+                    help="default workload only: skip the batched and served measurements added to the line")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--mesh", action="store_true",
                     help="produce the G-buffer on the device every frame by rasterising the scene's triangle mesh "
@@ -279,7 +281,7 @@ def sources_sha(files=SHADE_SOURCES):
 # CPU oracle baseline
 # ------------------------------------------------------------------------------------------
 def oracle_frame_rate(c, sc, g, env, k, nz, seconds: float, oracle_ibl=None, threads: int = 0, bloom=False,
-                      shadow_maps=None, mesh=None, surfels=None):
+                      shadow_maps=None, mesh=None, surfels=None, stats=None):
     """The FP64 oracle's per-frame path (blurred SSAO, compose, tone map) on horizontal bands of
     the frame until `seconds` elapse; returns (Mpixels/s, cores, sample description).  With
     `bloom`, the oracle's bloom of one whole frame (it needs the whole image) is timed as well and
@@ -321,6 +323,8 @@ def oracle_frame_rate(c, sc, g, env, k, nz, seconds: float, oracle_ibl=None, thr
         px_done += pixels.size
         y0 = (y0 + band) % H
     dt = time.perf_counter() - t0
+    if stats is not None:
+        stats.update(px=px_done, seconds=dt)
     if mesh is not None:  # the oracle's G-buffer pass of one whole frame, one thread
         tr = time.perf_counter()
         oracle.raster(mesh[0], mesh[1], oracle.camera(sc.camera_array(), float(np.float32(sc.fov_y)), W, H),
@@ -358,18 +362,26 @@ def run_reference(args):
     # warm-up: a short oracle pass
     for _ in range(args.warmup):
         oracle_frame_rate(c, sc, g, env, k, nz, 0.2)
-    per_step = []
+    px, secs = 0, 0.0
     samples = []
     for _ in range(args.steps):
-        rate, cores, sample = oracle_frame_rate(c, sc, g, env, k, nz, max(0.5, args.cpu_seconds / max(args.steps, 1)))
-        per_step.append(rate)
+        st = {}
+        rate, cores, sample = oracle_frame_rate(c, sc, g, env, k, nz, max(0.5, args.cpu_seconds / max(args.steps, 1)),
+                                                stats=st)
+        px += st["px"]
+        secs += st["seconds"]
         samples.append(sample)
-    value = statistics.mean(per_step)
-    ms = c["width"] * c["height"] / (value * 1e6) * 1e3
+    value = px / secs / 1e6
+    # a step is one bounded band sample of the frame (not a whole frame): ms_per_step is its measured
+    # wall time; the time a whole frame would take at the same rate is reported separately
     line = {"metric": METRIC, "value": value, "unit": "Mpixels/s", "n_gpus": args.gpus, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
-            "config": config_dict(c, name, {"note": "oracle on host cores, bounded band sample per step"}),
+            "warmup": args.warmup, "ms_per_step": secs / args.steps * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": config_dict(c, name, {"note": "oracle on host cores; each step shades a bounded band sample "
+                                                    "of the frame (full-width rows), timed on the wall clock",
+                                            "pixels_per_step": px // args.steps,
+                                            "full_frame_ms_extrapolated": c["width"] * c["height"] / (value * 1e6)
+                                            * 1e3}),
             "cpu_baseline": {"value": value, "unit": "Mpixels/s", "cores": cores, "kind": "oracle",
                              "sample": samples[0]},
             "e2e": {"value": value, "unit": "Mpixels/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -728,6 +740,23 @@ def run_gpu(args):
             r1, _, s1 = oracle_frame_rate(dict(c, name=name), sc, g, env, k, nz, min(3.0, args.cpu_seconds),
                                           threads=1)
             line["cpu_baseline"]["one_core"] = {"value": r1, "unit": "Mpixels/s", "cores": 1, "sample": s1}
+    if (world == 1 and name == WORKLOAD and not args.no_system_forms
+            and not (args.bloom or args.shadows or args.mesh or args.surfels)):
+        # the other two parts of the metric, each measured on its own workload after this one:
+        # batched vs the plain per-view loop, served vs one request at a time with p50/p99
+        del gb, hdr, ldr, ao, ao_raw, flush
+        torch.cuda.empty_cache()
+        mb = measure_batch(args, max_steps=10)
+        line["batch"] = {k: mb[k] for k in ("value", "unit", "speedup_vs_plain", "plain_per_view", "ms_per_step",
+                                            "steps", "plan", "workload", "clocks", "l2")}
+        ms = measure_serve(args, rates=SERVE_DEFAULT_RATES)
+        line["serve"] = {"value": ms["value"], "unit": "Mpixels/s", "speedup_vs_fifo": ms["speedup_vs_fifo"],
+                         "fifo_mpx_s": ms["fifo_one_at_a_time"]["mpx_s"],
+                         "latency_ms": [{"offered_req_s": r["offered_req_s"], "p50": r["p50_ms"], "p99": r["p99_ms"],
+                                         "achieved_req_s": r["achieved_req_s"], "mpx_s": r["mpx_s"],
+                                         "requests": r["requests"], "failed": r["failed"]} for r in ms["rates"]],
+                         "saturation_p50_ms": ms["saturation"]["p50_ms"], "saturation_p99_ms": ms["saturation"]["p99_ms"],
+                         "workload": ms["workload"], "server": ms["server"], "clocks": ms["clocks"]}
     print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
@@ -840,7 +869,9 @@ def _gen_view(spec):
     return g.rt0, g.rt1, g.depth, sc.lights, sc.camera_array(), sc.fov_y
 
 
-def run_batch(args):
+def measure_batch(args, max_steps: int = 20) -> dict:
+    """The multi-view workload: 64 views in one persistent launch replayed from a CUDA graph
+    against the plain per-view loop (3 launches per view) on the same views and stream."""
     import multiprocessing as mp
 
     specs = synth.batch_views()
@@ -850,8 +881,7 @@ def run_batch(args):
     import torch
 
     import paper_2012_03325_gb300 as ep
-    dev = torch.device("cuda", 0)
-    torch.cuda.set_device(dev)
+    dev = torch.device("cuda", torch.cuda.current_device())
     stream = torch.cuda.Stream(device=dev)
     c1 = synth.CONFIGS["full"]
     params = ep.ibl_params(c1["levels"], c1["prefilter_samples"], c1["lut"], c1["lut_samples"], *c1["irr"])
@@ -910,34 +940,46 @@ def run_batch(args):
         stream.synchronize()
         return [a.elapsed_time(b) for a, b in ms]
 
-    steps = max(3, min(args.steps, 20))
-    with ClockSampler(0) as clk:
+    steps = max(3, min(args.steps, max_steps))
+    with ClockSampler(torch.cuda.current_device()) as clk:
         clk.mark_start()
         plain_ms = timed(plain_step, steps)
         batch_ms = timed(lambda: batch.launch(stream=stream), steps)
         clk.mark_end()
+    batch.close()
     plain = total_px * steps / (sum(plain_ms) * 1e-3) / 1e6
     batched = total_px * steps / (sum(batch_ms) * 1e-3) / 1e6
-    line = {"metric": METRIC, "value": batched, "unit": "Mpixels/s", "n_gpus": 1, "steps": steps,
-            "warmup": args.warmup, "ms_per_step": sum(batch_ms) / steps, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": f"batch: {len(specs)} views, {total_px / 1e6:.1f} Mpx, resolutions "
-                                   "{512^2, 1280x720, 1920x1080, 3840x2160}, 16-256 lights (log-uniform), "
-                                   "8 environments 1024x512 (M=8, N_s=1024, LUT 64^2), SSAO 32 + 7x7",
-                       "plan": {"mode": ["fused", "staged"][plan[0]], "tile_w": plan[1], "tile_h": plan[2],
-                                "light_chunk": plan[3]},
-                       "l2": "flushed between timed steps (256 MB write)"},
+    return {"value": batched, "unit": "Mpixels/s", "steps": steps, "ms_per_step": sum(batch_ms) / steps,
+            "views": len(specs), "pixels_per_step": total_px,
+            "workload": f"batch: {len(specs)} views, {total_px / 1e6:.1f} Mpx, resolutions "
+                        "{512^2, 1280x720, 1920x1080, 3840x2160}, 16-256 lights (log-uniform), "
+                        "8 environments 1024x512 (M=8, N_s=1024, LUT 64^2), SSAO 32 + 7x7",
+            "plan": {"mode": ["fused", "staged"][plan[0]], "tile_w": plan[1], "tile_h": plan[2],
+                     "light_chunk": plan[3]},
             "plain_per_view": {"value": plain, "unit": "Mpixels/s", "ms_per_step": sum(plain_ms) / steps,
                                "launches_per_step": 3 * len(specs)},
-            "speedup_vs_plain": batched / plain, "gpu_launches": 1, "clocks": clk.summary()}
+            "speedup_vs_plain": batched / plain, "clocks": clk.summary(),
+            "l2": "flushed between timed steps (256 MB write)"}
+
+
+def run_batch(args):
+    import torch
+    torch.cuda.set_device(0)
+    m = measure_batch(args)
+    line = {"metric": METRIC, "value": m["value"], "unit": "Mpixels/s", "n_gpus": 1, "steps": m["steps"],
+            "warmup": args.warmup, "ms_per_step": m["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": m["workload"], "plan": m["plan"], "l2": m["l2"]},
+            "plain_per_view": m["plain_per_view"], "speedup_vs_plain": m["speedup_vs_plain"], "gpu_launches": 1,
+            "clocks": m["clocks"]}
     print(json.dumps(line), flush=True)
-    batch.close()
 
 
 # ------------------------------------------------------------------------------------------
 # serving workload: Poisson arrivals against the continuous-batching server
 # ------------------------------------------------------------------------------------------
 SERVE_CLASSES = [(256, 256, 0.4), (512, 512, 0.3), (1920, 1080, 0.2), (3840, 2160, 0.1)]
+SERVE_DEFAULT_RATES = (10, 100, 1000, 2000)  # arrival rates measured for the default line
 
 
 def _gen_serve_gbuffer(spec):
@@ -948,7 +990,9 @@ def _gen_serve_gbuffer(spec):
     return g.rt0, g.rt1, g.depth, sc.camera_array(), sc.fov_y, sc.F
 
 
-def run_serve(args):
+def measure_serve(args, rates=(10, 30, 100, 300, 1000, 2000)) -> dict:
+    """The serving workload: Poisson arrivals against the continuous-batching server at each rate,
+    then every request at once (saturation) against a server that runs one request at a time."""
     import multiprocessing as mp
     import threading
 
@@ -960,8 +1004,7 @@ def run_serve(args):
     import torch
 
     import paper_2012_03325_gb300 as ep
-    dev = torch.device("cuda", 0)
-    torch.cuda.set_device(dev)
+    dev = torch.device("cuda", torch.cuda.current_device())
     c1 = synth.CONFIGS["full"]
     params = ep.ibl_params(c1["levels"], c1["prefilter_samples"], c1["lut"], c1["lut_samples"], *c1["irr"])
     ibls, keep = [], []
@@ -1065,31 +1108,40 @@ def run_serve(args):
     run(served, make_requests(20, 1), None)  # warm-up
     run(fifo, make_requests(10, 2), None)
     n_req = max(20, args.serve_requests)
-    rates = []
-    with ClockSampler(0) as clk:
+    per_rate = []
+    with ClockSampler(torch.cuda.current_device()) as clk:
         clk.mark_start()
-        for rate in (10, 30, 100, 300, 1000, 2000):
+        for rate in rates:
             n = int(min(n_req, max(20, rate * args.serve_seconds)))
-            rates.append(run(served, make_requests(n, 100 + rate), rate))
+            per_rate.append(run(served, make_requests(n, 100 + rate), rate))
         burst = run(served, make_requests(n_req, 9), None)
         burst_fifo = run(fifo, make_requests(n_req, 9), None)
         clk.mark_end()
     st = served.stats()
     served.close()
     fifo.close()
-    line = {"metric": METRIC, "value": burst["mpx_s"], "unit": "Mpixels/s", "n_gpus": 1, "steps": len(rates),
-            "warmup": 1, "ms_per_step": None, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f32", "data": "synthetic",
-            "config": {"workload": "serve: Poisson arrivals, resolution {256^2, 512^2, 1920x1080, 3840x2160} with "
-                                   "weights .4/.3/.2/.1, 1-256 lights (log-uniform), 16 resident 1024x512 "
-                                   "lighting sets, FP32 G-buffer from pinned host memory, RGBA8 back to host",
-                       "server": {"memory_budget": budget, "max_in_flight": args.serve_inflight,
-                                  "streams": args.serve_streams},
-                       "value": "saturation throughput: all requests submitted at once"},
-            "rates": rates, "saturation": burst, "fifo_one_at_a_time": burst_fifo,
+    return {"value": burst["mpx_s"], "unit": "Mpixels/s",
+            "workload": "serve: Poisson arrivals, resolution {256^2, 512^2, 1920x1080, 3840x2160} with weights "
+                        ".4/.3/.2/.1, 1-256 lights (log-uniform), 16 resident 1024x512 lighting sets, FP32 "
+                        "G-buffer from pinned host memory, RGBA8 back to host",
+            "server": {"memory_budget": budget, "max_in_flight": args.serve_inflight, "streams": args.serve_streams},
+            "rates": per_rate, "saturation": burst, "fifo_one_at_a_time": burst_fifo,
             "speedup_vs_fifo": burst["mpx_s"] / burst_fifo["mpx_s"],
             "server_stats": {"admitted": st.admitted, "deferred": st.deferred, "peak_bytes": st.peak_bytes},
             "clocks": clk.summary()}
+
+
+def run_serve(args):
+    import torch
+    torch.cuda.set_device(0)
+    m = measure_serve(args)
+    line = {"metric": METRIC, "value": m["value"], "unit": "Mpixels/s", "n_gpus": 1, "steps": len(m["rates"]),
+            "warmup": 1, "ms_per_step": None, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic",
+            "config": {"workload": m["workload"], "server": m["server"],
+                       "value": "saturation throughput: all requests submitted at once"},
+            "rates": m["rates"], "saturation": m["saturation"], "fifo_one_at_a_time": m["fifo_one_at_a_time"],
+            "speedup_vs_fifo": m["speedup_vs_fifo"], "server_stats": m["server_stats"], "clocks": m["clocks"]}
     print(json.dumps(line), flush=True)
 
 

@@ -1,7 +1,8 @@
 // Image-based lighting precompute (paper Sec. 3.1; split sum of Karis 2013):
 //   k_brdf_lut          BRDF integration table (A, B), one warp per texel, Kahan + shuffles
 //   k_irradiance_part   exact-quadrature irradiance, per-block partial sums over a slice of
-//                       source texels staged in shared memory
+//                       source texels staged in shared memory (packed FP32x2 over output pairs,
+//                       plain sums per staged tile, Kahan across tiles)
 //   k_irradiance_final  sums the partials in a fixed order (deterministic) and normalises
 //   k_prefilter         GGX-prefiltered levels 1..M-1, one thread per output texel, the level's
 //                       sample set tabulated once per block in shared memory
@@ -74,9 +75,9 @@ __global__ void k_brdf_lut(int S, int N, float2* __restrict__ lut) {
 // ------------------------------------------------------------------------------------------
 // Irradiance: sum_t L_t max(n.d_t, 0) Omega_t / sum_t max(n.d_t, 0) Omega_t
 // ------------------------------------------------------------------------------------------
-constexpr int kIrrThreads = 256;
-constexpr int kIrrOutPerThread = 4;  // outputs per thread and pass: 1024 per pass
-constexpr int kIrrTile = 512;        // source texels staged per step
+constexpr int kIrrThreads = 128;
+constexpr int kIrrOutPerThread = 4;  // outputs per thread and pass (two packed pairs): 512 per pass
+constexpr int kIrrTile = 256;        // source texels staged per step
 constexpr int kIrrTexelsPerBlock = 1024;
 constexpr int kIrrMaxBlocks = 608;
 
@@ -98,11 +99,16 @@ __device__ __forceinline__ float3 texel_dir(int i, int j, int W, int H) {
   return f3(st * sp, ct, -st * cp);
 }
 
+// Each block sums over its slice of source texels for every output texel; a thread owns
+// kIrrOutPerThread outputs as two pairs whose arithmetic runs in packed FP32x2 instructions.
+// A source texel is staged once per tile as d Omega (max(n.d, 0) Omega = max(n.(d Omega), 0) since
+// Omega > 0) and L, every value duplicated into both halves of a pair: (dx, dx, dy, dy),
+// (dz, dz, Lr, Lr), (Lg, Lg, Lb, Lb).  Per tile the four sums of each output (L w and w) are
+// plain FP32; the tile's sums are then added to the slice totals with Kahan compensation.
 __global__ void __launch_bounds__(kIrrThreads) k_irradiance_part(const float4* __restrict__ env, int We,
                                                                  int He, int Wi, int Hi,
                                                                  float4* __restrict__ part) {
-  __shared__ float4 s_dir[kIrrTile];  // d.xyz, Omega
-  __shared__ float4 s_rad[kIrrTile];  // L.rgb
+  __shared__ float4 s_src[kIrrTile][3];
   long long ntex = (long long)We * He;
   long long per = (ntex + gridDim.x - 1) / gridDim.x;
   long long t0 = per * blockIdx.x;
@@ -112,36 +118,54 @@ __global__ void __launch_bounds__(kIrrThreads) k_irradiance_part(const float4* _
   //               = (4 pi / W) sin(pi (y + 0.5) / H) sin(pi / (2 H))   (product form)
   float row_k = 4.0f * kPi / We * sinpif(0.5f / He);
   for (int og = 0; og < nout; og += kIrrThreads * kIrrOutPerThread) {
-    float3 n[kIrrOutPerThread];
-    Kahan acc[kIrrOutPerThread][4];
+    // pair p holds outputs og + (2p + h) * kIrrThreads + tid, h = 0, 1; an absent output has n = 0
+    float2 nx[2], ny[2], nz[2];
 #pragma unroll
-    for (int r = 0; r < kIrrOutPerThread; ++r) {
-      int o = og + r * kIrrThreads + threadIdx.x;
-      n[r] = o < nout ? texel_dir(o % Wi, o / Wi, Wi, Hi) : f3(0, 0, 0);
+    for (int p = 0; p < 2; ++p) {
+      float3 a, b;
+      int oa = og + (2 * p) * kIrrThreads + threadIdx.x, ob = oa + kIrrThreads;
+      a = oa < nout ? texel_dir(oa % Wi, oa / Wi, Wi, Hi) : f3(0, 0, 0);
+      b = ob < nout ? texel_dir(ob % Wi, ob / Wi, Wi, Hi) : f3(0, 0, 0);
+      nx[p] = make_float2(a.x, b.x), ny[p] = make_float2(a.y, b.y), nz[p] = make_float2(a.z, b.z);
     }
+    Kahan acc[kIrrOutPerThread][4];
     for (long long base = t0; base < t1; base += kIrrTile) {
       int cnt = (int)(t1 - base < kIrrTile ? t1 - base : kIrrTile);
       __syncthreads();
       for (int q = threadIdx.x; q < cnt; q += kIrrThreads) {
         long long t = base + q;
         int x = (int)(t % We), y = (int)(t / We);
-        float3 d = texel_dir(x, y, We, He);
-        float om = row_k * sinpif((y + 0.5f) / He);
-        s_dir[q] = make_float4(d.x, d.y, d.z, om);
-        s_rad[q] = __ldg(env + t);
+        float3 d = texel_dir(x, y, We, He) * (row_k * sinpif((y + 0.5f) / He));
+        float4 L = __ldg(env + t);
+        s_src[q][0] = make_float4(d.x, d.x, d.y, d.y);
+        s_src[q][1] = make_float4(d.z, d.z, L.x, L.x);
+        s_src[q][2] = make_float4(L.y, L.y, L.z, L.z);
       }
       __syncthreads();
-      for (int q = 0; q < cnt; ++q) {
-        float4 dd = s_dir[q];
-        float4 L = s_rad[q];
+      float2 sr[2], sg[2], sb[2], sw[2];
 #pragma unroll
-        for (int r = 0; r < kIrrOutPerThread; ++r) {
-          float w = fmaxf(fmaf(n[r].x, dd.x, fmaf(n[r].y, dd.y, n[r].z * dd.z)), 0.0f) * dd.w;
-          acc[r][0].add(L.x * w);
-          acc[r][1].add(L.y * w);
-          acc[r][2].add(L.z * w);
-          acc[r][3].add(w);
+      for (int p = 0; p < 2; ++p) sr[p] = sg[p] = sb[p] = sw[p] = make_float2(0.0f, 0.0f);
+#pragma unroll 4
+      for (int q = 0; q < cnt; ++q) {
+        const float4 u = s_src[q][0], v = s_src[q][1], z = s_src[q][2];
+        const float2 dx = make_float2(u.x, u.y), dy = make_float2(u.z, u.w), dz = make_float2(v.x, v.y);
+        const float2 Lr = make_float2(v.z, v.w), Lg = make_float2(z.x, z.y), Lb = make_float2(z.z, z.w);
+#pragma unroll
+        for (int p = 0; p < 2; ++p) {
+          float2 w = __ffma2_rn(nx[p], dx, __ffma2_rn(ny[p], dy, __fmul2_rn(nz[p], dz)));
+          w = make_float2(fmaxf(w.x, 0.0f), fmaxf(w.y, 0.0f));
+          sr[p] = __ffma2_rn(Lr, w, sr[p]);
+          sg[p] = __ffma2_rn(Lg, w, sg[p]);
+          sb[p] = __ffma2_rn(Lb, w, sb[p]);
+          sw[p] = __fadd2_rn(sw[p], w);
         }
+      }
+#pragma unroll
+      for (int p = 0; p < 2; ++p) {
+        acc[2 * p][0].add(sr[p].x), acc[2 * p][1].add(sg[p].x), acc[2 * p][2].add(sb[p].x);
+        acc[2 * p][3].add(sw[p].x);
+        acc[2 * p + 1][0].add(sr[p].y), acc[2 * p + 1][1].add(sg[p].y), acc[2 * p + 1][2].add(sb[p].y);
+        acc[2 * p + 1][3].add(sw[p].y);
       }
     }
 #pragma unroll
