@@ -164,9 +164,27 @@ static double radical_inverse2(uint32_t i) {
   }
   return r;
 }
+/* Tangent frame of the sampling around unit n, built from the environment's pole axis y as
+ * Karis 2013's reference code builds it from its up vector: t = normalize(y x n), b = n x t.  It
+ * turns with n about the pole axis (rotating n about y rotates t and b alike).  For n on the
+ * axis itself (y x n = 0; no texel centre of an equirect map lies there) the Duff et al. basis
+ * is used. */
+static void onb_pole(const double* n, double* t, double* b) {
+  double len2 = n[2] * n[2] + n[0] * n[0];
+  if (!(len2 > 0.0)) {
+    onb_duff(n, t, b);
+    return;
+  }
+  double inv = 1.0 / sqrt(len2);
+  t[0] = n[2] * inv; /* y x n = (n.z, 0, -n.x) */
+  t[1] = 0.0;
+  t[2] = -n[0] * inv;
+  cross3(n, t, b);
+}
+
 /* Half vector for Hammersley point (xi1, xi2) = (k/N, radical_inverse(k)) around n:
  * phi = 2 pi xi1, cos(theta) = sqrt((1 - xi2) / (1 + (alpha^2 - 1) xi2)), i.e. the inverse CDF
- * of the GGX distribution of normals D(h)(n.h). */
+ * of the GGX distribution of normals D(h)(n.h), in the frame of onb_pole. */
 static void ggx_half_vector(double xi1, double xi2, double alpha, const double* n, double* h) {
   double a2 = alpha * alpha;
   double phi = 2.0 * OR_PI * xi1;
@@ -174,7 +192,7 @@ static void ggx_half_vector(double xi1, double xi2, double alpha, const double* 
   double st = sqrt(1.0 - ct * ct);
   double hx = st * cos(phi), hy = st * sin(phi), hz = ct;
   double t[3], b[3];
-  onb_duff(n, t, b);
+  onb_pole(n, t, b);
   for (int c = 0; c < 3; ++c) h[c] = t[c] * hx + b[c] * hy + n[c] * hz;
 }
 

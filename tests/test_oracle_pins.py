@@ -64,6 +64,46 @@ def test_ggx_half_vectors_form_a_rotating_orthonormal_frame():
         assert abs(d) < 1e-9
 
 
+def _rot_y(a):
+    c, s_ = math.cos(a), math.sin(a)
+    # turns the azimuth phi = atan2(x, -z) by +a
+    return np.array([[c, 0.0, -s_], [0.0, 1.0, 0.0], [s_, 0.0, c]])
+
+
+def test_sampling_frame_turns_with_the_normal_about_the_pole_axis():
+    """The sampling frame is built from the pole axis y (t = y x n normalised, b = n x t): the
+    half vectors of a normal turned about y are the turned half vectors, for any sample; t lies
+    in the horizontal plane.  A frame built otherwise (e.g. the Duff et al. basis) fails."""
+    for _ in range(200):
+        n = rand_unit()
+        a = rng.uniform(-math.pi, math.pi)
+        R = _rot_y(a)
+        xi1, xi2, alpha = rng.uniform(0, 1), rng.uniform(0.02, 0.98), rng.uniform(0.05, 1.0)
+        h = oracle.ggx_half_vector(xi1, xi2, alpha, n)
+        hr = oracle.ggx_half_vector(xi1, xi2, alpha, R @ n)
+        assert np.allclose(hr, R @ h, atol=1e-12)
+    n = np.array([0.3, 0.5, -0.8]) / np.linalg.norm([0.3, 0.5, -0.8])
+    t = oracle.ggx_half_vector(0.0, 1.0 - 1e-15, 1.0, n)  # xi2 -> 1 with alpha 1: h -> t (phi = 0)
+    assert abs(t[1]) < 1e-6 and abs(t @ n) < 1e-6
+    # at n = z the frame is (x, y, z): phi = 0 tilts h towards +x
+    h = oracle.ggx_half_vector(0.0, 0.5, 1.0, np.array([0.0, 0.0, 1.0]))
+    assert h[0] > 0 and abs(h[1]) < 1e-15
+
+
+def test_prefilter_commutes_with_turning_the_environment():
+    """Turning the environment about the pole axis by k * 2^m source columns turns prefiltered
+    level m by k columns, texel for texel (the sampling frame turns with the texel direction)."""
+    W, H, M, N = 64, 32, 4, 64
+    env, _ = _smooth_env(W, H)
+    env = env.astype(np.float64)
+    for m in (1, 2):
+        ref = oracle.prefilter_level(env, M, N, m)
+        for k in (1, 3):
+            turned = np.roll(env, k * (1 << m), axis=1)
+            got = oracle.prefilter_level(turned, M, N, m)
+            np.testing.assert_allclose(got, np.roll(ref, k, axis=1), rtol=1e-11, atol=1e-12)
+
+
 # ------------------------------------------------------------------------------------------
 # Equirect mapping
 # ------------------------------------------------------------------------------------------
