@@ -57,6 +57,10 @@ def parse():
                          "(Sec. 4.3) instead of uploading it; the surfels stay resident")
     ap.add_argument("--shadows", action="store_true",
                     help="shade with per-light shadow maps and 3x3 PCF (Sec. 5.1); maps stay resident")
+    ap.add_argument("--shadow-maps", default="static", choices=["static", "device"],
+                    help="with --shadows: 'static' keeps resident maps (the scene does not move); 'device' "
+                         "re-renders every light's map from the scene's triangle mesh on the device every frame "
+                         "(the scene or a light moved)")
     ap.add_argument("--bloom", action="store_true",
                     help="add the bloom pass (Sec. 5.3) to the frame: shade to HDR, then bloom + tone map")
     return ap.parse_args()
@@ -143,6 +147,7 @@ FLOP_SHADOW = 40         # lit pair with shadows: light-view transform (18), 1/z
 SHADOW = {"size": 512, "fov_deg": 90.0, "bias_const": 0.02, "bias_slope": 0.01}
 MESH = {"n_lat": 16, "n_lon": 32, "ground_cells": 64, "near": 0.05}
 RASTER_LAUNCHES = 7  # key reset, set-up, three scan kernels, coverage, resolve
+SHADOW_MAP_LAUNCHES = 6  # per light: set-up, three scan kernels, coverage, depth resolve (the key reset is a memset)
 SURFELS = {"per_sphere": 4000, "ground": 400000, "overlap": 1.2, "seed": 11, "near": 0.05, "tolerance": 0.01}
 SURFEL_LAUNCHES = 10  # depth and sum resets, pixel rays, set-up, three scan kernels, two coverage passes, resolve
 
@@ -281,7 +286,7 @@ def sources_sha(files=SHADE_SOURCES):
 # CPU oracle baseline
 # ------------------------------------------------------------------------------------------
 def oracle_frame_rate(c, sc, g, env, k, nz, seconds: float, oracle_ibl=None, threads: int = 0, bloom=False,
-                      shadow_maps=None, mesh=None, surfels=None, stats=None):
+                      shadow_maps=None, mesh=None, surfels=None, stats=None, shadow_mesh=None):
     """The FP64 oracle's per-frame path (blurred SSAO, compose, tone map) on horizontal bands of
     the frame until `seconds` elapse; returns (Mpixels/s, cores, sample description).  With
     `bloom`, the oracle's bloom of one whole frame (it needs the whole image) is timed as well and
@@ -300,6 +305,17 @@ def oracle_frame_rate(c, sc, g, env, k, nz, seconds: float, oracle_ibl=None, thr
         gb = oracle.decode_fp32(g.rt0, g.rt1, g.depth)
     cam = oracle.camera(sc.camera_array(), sc.fov_y, W, H)
     cores = oracle.num_threads(threads)
+    t_maps = 0.0
+    if shadow_mesh is not None:  # the oracle renders the first light's map (one thread) and shades with it
+        smv, smt, v2ws, scams = shadow_mesh
+        S = SHADOW["size"]
+        tm = time.perf_counter()
+        ogb, _ = oracle.raster(smv, smt, oracle.camera(np.asarray(v2ws[0], np.float32).T.reshape(-1),
+                                                       float(np.float32(math.radians(SHADOW["fov_deg"]))), S, S),
+                               MESH["near"])
+        t_maps = (time.perf_counter() - tm) * len(v2ws)  # every light's map takes about as long
+        m1 = ogb[..., 8].astype(np.float32)
+        shadow_maps = (np.broadcast_to(m1, (len(v2ws), S, S)).copy(), scams)
     band = 16
     px_done, t0 = 0, time.perf_counter()
     y0 = H // 3
@@ -325,6 +341,11 @@ def oracle_frame_rate(c, sc, g, env, k, nz, seconds: float, oracle_ibl=None, thr
     dt = time.perf_counter() - t0
     if stats is not None:
         stats.update(px=px_done, seconds=dt)
+    if shadow_mesh is not None:
+        rate = 1.0 / (dt / px_done + t_maps / (W * H)) / 1e6
+        return rate, cores, (f"{px_done} px in {px_done // W} full-width rows ({dt:.1f} s wall) + the shadow maps of "
+                             f"one frame ({len(shadow_mesh[2])} lights x the first light's map rendered from "
+                             f"{len(shadow_mesh[1])} triangles: {t_maps:.2f} s, one thread)")
     if mesh is not None:  # the oracle's G-buffer pass of one whole frame, one thread
         tr = time.perf_counter()
         oracle.raster(mesh[0], mesh[1], oracle.camera(sc.camera_array(), float(np.float32(sc.fov_y)), W, H),
@@ -466,9 +487,35 @@ def run_gpu(args):
         if args.bloom else None
 
     shadows = None
-    if args.shadows:
+    smesh = maps_t = ws_smaps = None
+    smaps_dev = args.shadows and args.shadow_maps == "device"
+    if smaps_dev:  # maps rendered on the device every frame from the scene's triangle mesh
+        smv, smt = (mv, mt) if args.mesh else synth.make_mesh_scene(sc, MESH["n_lat"], MESH["n_lon"],
+                                                                    MESH["ground_cells"])
+        smesh = ep.Mesh(t(smv), t(smt))
+        v2ws, cams = synth.shadow_cameras(sc, SHADOW["fov_deg"])
+        S = SHADOW["size"]
+        scams = [ep.camera(np.asarray(v, np.float32).T.reshape(-1), math.radians(SHADOW["fov_deg"]), S, S)
+                 for v in v2ws]
+        maps_t = torch.empty(len(v2ws), S, S, device=dev)
+        ws_smaps = torch.empty(ep.epbr_shadow_maps_workspace_size(len(smt), S) + 256, dtype=torch.uint8, device=dev)
+        ep.epbr_shadow_maps(smesh, scams, MESH["near"], maps_t, ws_smaps)
+        torch.cuda.synchronize()
+        maps = None  # the oracle baseline renders its own (or_raster)
+        shadows = ep.Shadows(maps_t, t(cams), SHADOW["bias_const"], SHADOW["bias_slope"])
+    elif args.shadows:
         maps, cams = synth.make_shadow_maps(sc, SHADOW["size"], SHADOW["fov_deg"])
         shadows = ep.Shadows(t(maps), t(cams), SHADOW["bias_const"], SHADOW["bias_slope"])
+    ev_smaps = []
+
+    def render_shadow_maps(record=False):
+        if record:
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+        ep.epbr_shadow_maps(smesh, scams, MESH["near"], maps_t, ws_smaps, stream=stream)
+        if record:
+            b.record(stream)
+            ev_smaps.append((a, b))
 
     def compose(g_, shp_, hdr_, ldr_, lights_, record=False):
         """Compose (+ bloom): with bloom the compose writes HDR only and the bloom pass tone-maps."""
@@ -513,6 +560,8 @@ def run_gpu(args):
     def step(record=False, ssao_events=False):
         if produced:
             raster(gb, record)
+        if smaps_dev:
+            render_shadow_maps(record)
         if ssao_events:
             e3 = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
             e3[0].record(stream)
@@ -526,7 +575,7 @@ def run_gpu(args):
         compose(gb, shp, hdr, ldr, lights, record)
 
     launches_per_step = 3 + (BLOOM_LAUNCHES if args.bloom else 0) + (RASTER_LAUNCHES if args.mesh else 0) + \
-        (SURFEL_LAUNCHES if args.surfels else 0)
+        (SURFEL_LAUNCHES if args.surfels else 0) + (SHADOW_MAP_LAUNCHES * len(scams) if smaps_dev else 0)
     with torch.cuda.stream(stream):
         for _ in range(max(3, args.warmup)):
             step()
@@ -617,6 +666,8 @@ def run_gpu(args):
             flush.zero_()  # L2 flush inside the timed window
             if produced:
                 raster(b["gb"])
+            if smaps_dev:
+                render_shadow_maps()
             ep.epbr_ssao_raw(b["gb"], cam, sp, b["ao_raw"], stream=stream)
             ep.epbr_ssao_blur(b["gb"], sp, b["ao_raw"], b["ao"], stream=stream)
             compose(b["gb"], b["shp"], b["hdr"], b["ldr"], b["lights"])
@@ -694,7 +745,11 @@ def run_gpu(args):
                                                 "bloom": BLOOM} if args.bloom else {}),
                                             **({"shadows": dict(SHADOW, maps="one per light, resident (static "
                                                                 "scene), generated by the ray caster")}
-                                               if args.shadows else {}),
+                                               if args.shadows and not smaps_dev else {}),
+                                            **({"shadows": dict(SHADOW, maps="one per light, rendered on the device "
+                                                                "every frame from the scene's triangle mesh "
+                                                                "(the scene or a light moved)", **MESH)}
+                                               if smaps_dev else {}),
                                             **({"gbuffer": "fp32 36 B/px, rasterised on the device every frame from "
                                                            "the resident triangle mesh"} if args.mesh else {}),
                                             **({"gbuffer": "fp32 36 B/px, splatted on the device every frame from "
@@ -712,6 +767,10 @@ def run_gpu(args):
                           "launches": RASTER_LAUNCHES, **MESH}
         line["e2e"]["how"] = ("mesh resident; lights uploaded and RGBA8 downloaded every step; frames pipelined "
                               "over upload, compute (raster + SSAO + compose) and download streams")
+    if smaps_dev:
+        line["shadow_maps"] = {"ms": statistics.mean(a.elapsed_time(b) for a, b in ev_smaps), "maps": len(scams),
+                               "size": SHADOW["size"], "triangles": smesh.struct.num_triangles,
+                               "launches": SHADOW_MAP_LAUNCHES * len(scams)}
     if args.surfels:
         line["surfels"] = {"ms": statistics.mean(a.elapsed_time(b) for a, b in ev_raster), "surfels": len(srec),
                            "launches": SURFEL_LAUNCHES, **SURFELS}
@@ -730,7 +789,8 @@ def run_gpu(args):
     if not args.no_cpu_baseline and world == 1:
         rate, cores, sample = oracle_frame_rate(dict(c, name=name), sc, g, env, k, nz, args.cpu_seconds,
                                                 bloom=args.bloom,
-                                                shadow_maps=(maps, cams) if args.shadows else None,
+                                                shadow_maps=(maps, cams) if args.shadows and not smaps_dev else None,
+                                                shadow_mesh=(smv, smt, v2ws, cams) if smaps_dev else None,
                                                 mesh=(mv, mt) if args.mesh else None,
                                                 surfels=srec if args.surfels else None)
         line["cpu_baseline"] = {"value": rate, "unit": "Mpixels/s", "cores": cores, "kind": "oracle",

@@ -382,6 +382,22 @@ epbr_status epbr_raster_gbuffer(const epbr_mesh* mesh, const epbr_camera* camera
                                 const epbr_gbuffer* out, int32_t* ids, int64_t ids_pitch, void* workspace,
                                 size_t workspace_bytes, void* stream);
 
+/* Device workspace epbr_shadow_maps needs for maps of size x size texels (one light's key image
+ * and triangle set-up, reused light after light). */
+epbr_status epbr_shadow_maps_workspace_size(int32_t num_triangles, int32_t size, size_t* bytes);
+
+/* Shadow maps by rendering the mesh "only as a depth map" from each light as from a normal
+ * camera (Sec. 5.1): map i is the eye depth of the mesh seen by cameras[i] (square, every camera
+ * of the same size S, field of view in (0, 3.1) rad), exactly the depth plane epbr_raster_gbuffer
+ * writes for that camera (same coverage, depth and tie rules; +inf where nothing is drawn).
+ * `maps` is DEVICE float[num_maps][S][S] (dense rows), the layout epbr_shadows.maps takes; the
+ * cameras are host structs (the world -> light-view rows epbr_shadows.cameras holds for shading
+ * are the inverse of each camera's view_to_world).  The lights are rendered one after the other
+ * through `workspace` (DEVICE, 256-byte aligned, epbr_shadow_maps_workspace_size bytes), stream-
+ * ordered; no allocation.  Re-render when the scene or a light moves. */
+epbr_status epbr_shadow_maps(const epbr_mesh* mesh, const epbr_camera* cameras, int32_t num_maps,
+                             float near_depth, float* maps, void* workspace, size_t workspace_bytes, void* stream);
+
 /* ---------------------------------------------------------------------------------------- */
 /* The G-buffer pass of surfel rendering (Sec. 4.3): elliptical disks splatted and blended   */
 /* ---------------------------------------------------------------------------------------- */

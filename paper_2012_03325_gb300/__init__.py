@@ -394,6 +394,27 @@ def epbr_surfel_gbuffer(surfels: Surfels, cam: F.epbr_camera, near: float, toler
                                      ws.numel() - (_aligned(ws) - ws.data_ptr()), _stream(stream)))
 
 
+def epbr_shadow_maps_workspace_size(num_triangles: int, size: int) -> int:
+    n = C.c_size_t()
+    _check(lib().epbr_shadow_maps_workspace_size(num_triangles, size, C.byref(n)))
+    return n.value
+
+
+def epbr_shadow_maps(mesh: Mesh, cameras, near: float, maps: torch.Tensor, workspace: torch.Tensor | None = None,
+                     stream=None):
+    """Renders one depth map per camera (list of epbr_camera, square, same size) into maps (NL, S, S)."""
+    cams = list(cameras)
+    if not cams:
+        return
+    S = cams[0].width
+    mp = _flat(maps, len(cams) * S * S, torch.float32, "maps")
+    need = epbr_shadow_maps_workspace_size(mesh.struct.num_triangles, S)
+    ws = workspace if workspace is not None else _workspace(need, maps.device)
+    arr = (F.epbr_camera * len(cams))(*cams)
+    _check(lib().epbr_shadow_maps(C.byref(mesh.struct), arr, len(cams), near, mp, _aligned(ws),
+                                  ws.numel() - (_aligned(ws) - ws.data_ptr()), _stream(stream)))
+
+
 # ------------------------------------------------------------------------------------------
 # eye-dome lighting for point clouds (Sec. 4.2)
 # ------------------------------------------------------------------------------------------

@@ -169,6 +169,8 @@ PROTOTYPES = {
     "epbr_tonemap": [vp, i32, i32, i32, i64, P(epbr_tonemap_params), vp, i64, vp],
     "epbr_raster_workspace_size": [i32, i32, i32, P(sz)],
     "epbr_raster_gbuffer": [P(epbr_mesh), P(epbr_camera), C.c_float, P(epbr_gbuffer), vp, i64, vp, sz, vp],
+    "epbr_shadow_maps_workspace_size": [i32, i32, P(sz)],
+    "epbr_shadow_maps": [P(epbr_mesh), P(epbr_camera), i32, C.c_float, vp, vp, sz, vp],
     "epbr_surfel_workspace_size": [i32, i32, i32, P(sz)],
     "epbr_surfel_gbuffer": [P(epbr_surfels), P(epbr_camera), C.c_float, C.c_float, P(epbr_gbuffer), vp, i64, vp, sz,
                             vp],

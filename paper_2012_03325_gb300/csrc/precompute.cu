@@ -4,8 +4,9 @@
 //                       source texels staged in shared memory (packed FP32x2 over output pairs,
 //                       plain sums per staged tile, Kahan across tiles)
 //   k_irradiance_final  sums the partials in a fixed order (deterministic) and normalises
-//   k_prefilter         GGX-prefiltered levels 1..M-1, one thread per output texel, the level's
-//                       sample set tabulated once per block in shared memory
+//   k_prefilter         GGX-prefiltered levels 1..M-1, one block per row of a level: the row's
+//                       sample geometry computed once (the sampling frame turns with the texel
+//                       about the pole axis), each texel sums its samples at shifted columns
 #include <cuda.h>  // CUcontext and CUresult for the context queries (fetched at run time)
 
 #include <algorithm>
@@ -207,13 +208,21 @@ struct ChainDev {
   float4* dst[EPBR_MAX_LEVELS];
 };
 
-// One grid row per level (blockIdx.y = m - 1).  With n = v, a GGX half vector h with
-// tangent-space components (sin t cos p, sin t sin p, cos t) gives
-//   l = 2 (n.h) h - n = T (2 h_z h_x) + B (2 h_z h_y) + n (2 h_z^2 - 1),   n.l = 2 h_z^2 - 1,
-// both functions of the sample and the level only.  Each block therefore tabulates its level's
-// samples once, keeping those with n.l > 0 in sample order (a deterministic compaction), and the
-// per-texel loop is the rotation into the texel's frame plus the environment lookup.
+// With n = v, a GGX half vector h with tangent-space components (sin t cos p, sin t sin p, cos t)
+// gives l = 2 (n.h) h - n = T (2 h_z h_x) + B (2 h_z h_y) + n (2 h_z^2 - 1), n.l = 2 h_z^2 - 1:
+// functions of the sample and the level only.  The frame (T, B, n) is built from the map's pole
+// axis (T = y x n normalised, B = n x T), so it turns with n about that axis: the texels of one
+// row of a level share every sample's polar angle, and their sample directions differ only by
+// the row's azimuth step.  In the source map (level 0, W0 columns) texel i of a level-m row
+// therefore reads each sample at the source coordinate of texel 0 moved right by i * W0 / Wm
+// columns.  One block per (level, row): the block computes, once, every kept sample's source
+// coordinate for texel 0 (the only equirect mapping in the kernel) and its bilinear weights,
+// then every texel of the row sums its samples from the shifted coordinates.  Rows wider than
+// kPrefilterSeg texels are split into segments, one block each.
 constexpr int kPrefilterMaxSamples = 2048;
+constexpr int kPrefilterThreads = 256;
+constexpr int kPrefilterTexels = 2;  // texels per thread: a block shades a segment of up to 512 texels of a row
+constexpr int kPrefilterSeg = kPrefilterThreads * kPrefilterTexels;
 
 // Sample `sidx` of N for alpha^2 = a2 as (2 h_z h_x, 2 h_z h_y, n.l, -); kept iff n.l > 0.  Both
 // compaction passes call this, so they agree on every decision.
@@ -226,28 +235,50 @@ __device__ __forceinline__ float4 prefilter_sample(int sidx, float a2, float inv
   return make_float4(2.0f * ct * st * cp, 2.0f * ct * st * sp, fmaf(2.0f * ct, ct, -1.0f), 0.0f);
 }
 
-__global__ void __launch_bounds__(256) k_prefilter(MapDev src, ChainDev ch, int N) {
-  __shared__ float4 s_smp[kPrefilterMaxSamples];  // kept samples, in sample order
+// Source coordinate of a sample direction l in the level-0 map: x = u W0 - 0.5, y = v H0 - 0.5.
+__device__ __forceinline__ float2 prefilter_src_xy(float3 l, int W0, int H0) {
+  float u, v;
+  dir_to_uv(l, u, v);
+  return make_float2(fmaf(u, (float)W0, -0.5f), fmaf(v, (float)H0, -0.5f));
+}
+
+// Per kept sample, for texel 0 of the row, in order of source row: INT_SHIFT (W0 a multiple of
+// Wm) stores the four bilinear weights times n.l and (column, row); otherwise the two row weights
+// times n.l and the source x coordinate (the column fraction then varies along the row), and the
+// row.  Samples are visited in order of their source row so that consecutive samples read the
+// same two rows, which stay in L1 (a deterministic bitonic sort of (row, sample) keys).
+template <bool INT_SHIFT>
+__global__ void __launch_bounds__(kPrefilterThreads) k_prefilter(MapDev src, ChainDev ch, int N) {
+  // dynamic shared memory: N float4 weights, N int2 (column, row), N ushort sorted positions; the
+  // sort keys ((source row << 16) | kept-sample index, N unsigned) occupy the weights' space
+  // until the records are written
+  extern __shared__ __align__(16) float4 s_pf[];
   __shared__ int s_base[kPrefilterMaxSamples / 32 + 1];
+  __shared__ float s_wsum[kPrefilterThreads / 32];
+  float4* s_w = s_pf;
+  int2* s_xy = (int2*)(s_pf + N);
+  unsigned short* s_pos = (unsigned short*)(s_xy + N);
+  unsigned* s_key = (unsigned*)s_pf;
   const int m = blockIdx.y + 1;
   const int W = ch.W[m], H = ch.H[m];
-  const long long ntex = (long long)W * H;
-  const long long t0 = (long long)blockIdx.x * blockDim.x;
-  if (t0 >= ntex) return;  // block-uniform
+  const int segs = (W + kPrefilterSeg - 1) / kPrefilterSeg;
+  const int j = blockIdx.x / segs, i0 = (blockIdx.x - j * segs) * kPrefilterSeg;
+  if (j >= H) return;  // block-uniform
+  const int W0 = src.W, H0 = src.H;
   const float r = (float)m / (float)(ch.M - 1);
   const float a2 = r * r * r * r;
   const float invN = 1.0f / N;
   const int groups = (N + 31) / 32;
-  const int lane = threadIdx.x & 31;
-  // pass 1: kept samples per group of 32
-  for (int gi = threadIdx.x / 32; gi < groups; gi += blockDim.x / 32) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  // kept samples per group of 32, then an exclusive prefix over the groups (sample order)
+  for (int gi = warp; gi < groups; gi += kPrefilterThreads / 32) {
     int sidx = gi * 32 + lane;
     bool keep = sidx < N && prefilter_sample(sidx, a2, invN).z > 0.0f;
     unsigned bal = __ballot_sync(0xffffffffu, keep);
     if (lane == 0) s_base[gi] = __popc(bal);
   }
   __syncthreads();
-  if (threadIdx.x == 0) {  // exclusive prefix over the groups, in sample order
+  if (tid == 0) {
     int acc = 0;
     for (int gi = 0; gi < groups; ++gi) {
       int c = s_base[gi];
@@ -257,35 +288,181 @@ __global__ void __launch_bounds__(256) k_prefilter(MapDev src, ChainDev ch, int 
     s_base[groups] = acc;
   }
   __syncthreads();
-  // pass 2: the kept samples at their compacted positions
-  for (int gi = threadIdx.x / 32; gi < groups; gi += blockDim.x / 32) {
+  const int ns = s_base[groups];
+  // the frame of texel 0 of the row: n, T = y x n / |y x n| = (-cos phi0, 0, -sin phi0), B = n x T
+  const float3 n = texel_dir(0, j, W, H);
+  float sp0, cp0;
+  sincospif(2.0f * (0.5f / W) - 1.0f, &sp0, &cp0);
+  const float3 T = f3(-cp0, 0.0f, -sp0);
+  const float3 B = cross3(n, T);
+  // pass A: each kept sample's source row, as a sort key
+  for (int gi = warp; gi < groups; gi += kPrefilterThreads / 32) {
     int sidx = gi * 32 + lane;
     float4 e = sidx < N ? prefilter_sample(sidx, a2, invN) : make_float4(0, 0, 0, 0);
     bool keep = sidx < N && e.z > 0.0f;
     unsigned bal = __ballot_sync(0xffffffffu, keep);
-    if (keep) s_smp[s_base[gi] + __popc(bal & ((1u << lane) - 1u))] = e;
+    if (keep) {
+      const int q = s_base[gi] + __popc(bal & ((1u << lane) - 1u));
+      const float2 xy = prefilter_src_xy(T * e.x + B * e.y + n * e.z, W0, H0);
+      const int iy = min(max((int)floorf(xy.y), 0), H0 - 1);
+      s_key[q] = ((unsigned)iy << 16) | (unsigned)q;
+    }
   }
+  int P = 1;
+  while (P < ns) P <<= 1;
+  for (int q = ns + tid; q < P; q += kPrefilterThreads) s_key[q] = 0xffffffffu;
   __syncthreads();
-  const int ns = s_base[groups];
-  const long long t = t0 + threadIdx.x;
-  if (t >= ntex) return;
-  int i = (int)(t % W), j = (int)(t / W);
-  float3 n = texel_dir(i, j, W, H);
-  float3 tt, bb;
-  onb(n, tt, bb);
-  Kahan acc[4];
-  for (int q = 0; q < ns; ++q) {
-    float4 e = s_smp[q];
-    float3 l = tt * e.x + bb * e.y + n * e.z;
-    float3 L = equirect_lookup(src, l);
-    acc[0].add(L.x * e.z);
-    acc[1].add(L.y * e.z);
-    acc[2].add(L.z * e.z);
-    acc[3].add(e.z);
+  for (int k = 2; k <= P; k <<= 1) {
+    for (int jj = k >> 1; jj > 0; jj >>= 1) {
+      for (int q = tid; q < P; q += kPrefilterThreads) {
+        const int o = q ^ jj;
+        if (o > q) {
+          const unsigned a = s_key[q], b = s_key[o];
+          if ((a > b) == ((q & k) == 0)) {
+            s_key[q] = b;
+            s_key[o] = a;
+          }
+        }
+      }
+      __syncthreads();
+    }
   }
-  float inv = 1.0f / (acc[3].s - acc[3].c);
-  ch.dst[m][t] = make_float4((acc[0].s - acc[0].c) * inv, (acc[1].s - acc[1].c) * inv,
-                             (acc[2].s - acc[2].c) * inv, 1.0f);
+  for (int q = tid; q < ns; q += kPrefilterThreads) s_pos[s_key[q] & 0xffffu] = (unsigned short)q;
+  __syncthreads();  // the keys are dead from here: their space takes the records
+  // pass B: the records at their sorted positions; the weight sum sum_k n.l_k (the same for every
+  // texel of the level), summed in sample order
+  float wpart = 0.0f;
+  for (int gi = warp; gi < groups; gi += kPrefilterThreads / 32) {
+    int sidx = gi * 32 + lane;
+    float4 e = sidx < N ? prefilter_sample(sidx, a2, invN) : make_float4(0, 0, 0, 0);
+    bool keep = sidx < N && e.z > 0.0f;
+    unsigned bal = __ballot_sync(0xffffffffu, keep);
+    if (keep) {
+      const int q = s_base[gi] + __popc(bal & ((1u << lane) - 1u));
+      const float2 xy = prefilter_src_xy(T * e.x + B * e.y + n * e.z, W0, H0);
+      const float xf = floorf(xy.x), yf = floorf(xy.y);
+      const float fx = xy.x - xf, fy = xy.y - yf;
+      const float wt = e.z * (1.0f - fy), wb = e.z * fy;
+      const int p = s_pos[q];
+      if (INT_SHIFT)
+        s_w[p] = make_float4(wt * (1.0f - fx), wt * fx, wb * (1.0f - fx), wb * fx);
+      else
+        s_w[p] = make_float4(wt, wb, xy.x, 0.0f);
+      s_xy[p] = make_int2((int)xf, (int)yf);
+      wpart += e.z;
+    }
+  }
+  wpart = warp_sum(wpart);
+  if (lane == 0) s_wsum[warp] = wpart;
+  __syncthreads();
+  float wsum = 0.0f;
+#pragma unroll
+  for (int w = 0; w < kPrefilterThreads / 32; ++w) wsum += s_wsum[w];
+  const float inv = 1.0f / wsum;
+  const int step_i = W0 / W;  // INT_SHIFT: whole source columns per texel
+  const float step_f = (float)W0 / (float)W;
+  if (INT_SHIFT) {
+    // Lanes by tap column: lane l of warp w serves output texels i = i0 + 64 w + 16 g + (l >> 1),
+    // g = 0..3, with the tap column d = l & 1 (columns x0 + s i + d), so a warp's loads of one
+    // row and group are 32 consecutive texels at level 1 (s = 2); the two lanes of a texel add
+    // their sums at the end.
+    const int t = lane >> 1, dl = lane & 1;
+    const int wbase = i0 + warp * 64;
+    if (wbase >= W) return;  // warp-uniform, after the last barrier
+    int col[4];
+    bool ong[4];
+    float3 acc[4], part[4];
+#pragma unroll
+    for (int g = 0; g < 4; ++g) {
+      const int i = wbase + 16 * g + t;
+      ong[g] = wbase + 16 * g < W;  // warp-uniform: whether group g has texels
+      col[g] = min(i, W - 1) * step_i + dl;
+      acc[g] = part[g] = f3(0, 0, 0);
+    }
+#pragma unroll 2
+    for (int q = 0; q < ns; ++q) {
+      const float4 w = s_w[q];
+      const int2 xy = s_xy[q];
+      const int r0 = max(xy.y, 0) * W0, r1 = min(xy.y + 1, H0 - 1) * W0;
+      const float wa = dl ? w.y : w.x, wb = dl ? w.w : w.z;  // this column's weights in rows r0, r1
+#pragma unroll
+      for (int g = 0; g < 4; ++g) {
+        if (!ong[g]) continue;
+        int c = xy.x + col[g];  // in [-1, 2 W0 - 1)
+        c = c < 0 ? c + W0 : (c >= W0 ? c - W0 : c);
+        const float4 a = __ldg(src.texels + (r0 + c)), p = __ldg(src.texels + (r1 + c));
+        part[g].x = fmaf(wa, a.x, fmaf(wb, p.x, part[g].x));
+        part[g].y = fmaf(wa, a.y, fmaf(wb, p.y, part[g].y));
+        part[g].z = fmaf(wa, a.z, fmaf(wb, p.z, part[g].z));
+      }
+      if ((q & 63) == 63) {  // fold every 64 samples' plain sums into the running sums
+#pragma unroll
+        for (int g = 0; g < 4; ++g) {
+          acc[g] = acc[g] + part[g];
+          part[g] = f3(0, 0, 0);
+        }
+      }
+    }
+#pragma unroll
+    for (int g = 0; g < 4; ++g) {
+      if (!ong[g]) continue;
+      float3 v = acc[g] + part[g];
+      v.x += __shfl_xor_sync(0xffffffffu, v.x, 1);
+      v.y += __shfl_xor_sync(0xffffffffu, v.y, 1);
+      v.z += __shfl_xor_sync(0xffffffffu, v.z, 1);
+      const int i = wbase + 16 * g + t;
+      if (dl == 0 && i < W) {
+        const float3 o = v * inv;
+        ch.dst[m][(long long)j * W + i] = make_float4(o.x, o.y, o.z, 1.0f);
+      }
+    }
+    return;
+  }
+  int ii[kPrefilterTexels];
+  bool on[kPrefilterTexels];  // block-uniform: whether the segment has a texel group c
+  float3 acc[kPrefilterTexels], part[kPrefilterTexels];
+#pragma unroll
+  for (int c = 0; c < kPrefilterTexels; ++c) {
+    on[c] = i0 + c * kPrefilterThreads < W;
+    ii[c] = min(i0 + c * kPrefilterThreads + tid, W - 1);  // duplicates of the last texel are not stored
+    acc[c] = part[c] = f3(0, 0, 0);
+  }
+#pragma unroll 2
+  for (int q = 0; q < ns; ++q) {
+    const float4 w = s_w[q];
+    const int2 xy = s_xy[q];
+    const int r0 = max(xy.y, 0) * W0, r1 = min(xy.y + 1, H0 - 1) * W0;
+#pragma unroll
+    for (int c = 0; c < kPrefilterTexels; ++c) {
+      if (!on[c]) continue;
+      const float x = fmaf((float)ii[c], step_f, w.z);
+      const float xf = floorf(x), fx = x - xf;
+      int x0 = (int)xf;
+      const float4 wq = make_float4(w.x * (1.0f - fx), w.x * fx, w.y * (1.0f - fx), w.y * fx);
+      x0 = x0 < 0 ? x0 + W0 : (x0 >= W0 ? x0 - W0 : x0);
+      const int x1 = x0 + 1 == W0 ? 0 : x0 + 1;
+      const float4 a = __ldg(src.texels + (r0 + x0)), b = __ldg(src.texels + (r0 + x1));
+      const float4 p = __ldg(src.texels + (r1 + x0)), d = __ldg(src.texels + (r1 + x1));
+      part[c].x = fmaf(wq.x, a.x, fmaf(wq.y, b.x, fmaf(wq.z, p.x, fmaf(wq.w, d.x, part[c].x))));
+      part[c].y = fmaf(wq.x, a.y, fmaf(wq.y, b.y, fmaf(wq.z, p.y, fmaf(wq.w, d.y, part[c].y))));
+      part[c].z = fmaf(wq.x, a.z, fmaf(wq.y, b.z, fmaf(wq.z, p.z, fmaf(wq.w, d.z, part[c].z))));
+    }
+    if ((q & 63) == 63) {  // fold every 64 samples' plain sums into the running sums
+#pragma unroll
+      for (int c = 0; c < kPrefilterTexels; ++c) {
+        acc[c] = acc[c] + part[c];
+        part[c] = f3(0, 0, 0);
+      }
+    }
+  }
+#pragma unroll
+  for (int c = 0; c < kPrefilterTexels; ++c) {
+    const int i = i0 + c * kPrefilterThreads + tid;
+    if (on[c] && i < W) {
+      const float3 o = (acc[c] + part[c]) * inv;
+      ch.dst[m][(long long)j * W + i] = make_float4(o.x, o.y, o.z, 1.0f);
+    }
+  }
 }
 
 static epbr_status validate_ibl_for(const epbr_ibl* ibl, int We, int He) {
@@ -470,9 +647,23 @@ extern "C" epbr_status epbr_prefilter(const epbr_env* env, int32_t N, const epbr
   }
   for (int li = 0; li < ch.nlev; ++li) ch.off[li + 1] = ch.off[li] + (long long)ch.W[li + 1] * ch.H[li + 1];
   MapDev src{(const float4*)env->texels, env->width, env->height};
-  long long most = (long long)ch.W[1] * ch.H[1];  // level 1 has the most texels
-  dim3 grid((unsigned)((most + 255) / 256), (unsigned)ch.nlev);
-  k_prefilter<<<grid, 256, 0, s>>>(src, ch, N);
+  // one block per row of every level (level 1 has the most rows); whole-column shifts when every
+  // level's width divides the source width
+  bool int_shift = true;
+  for (int m = 1; m < ibl->num_levels; ++m) int_shift = int_shift && env->width % ch.W[m] == 0;
+  unsigned most = 0;
+  for (int m = 1; m < ibl->num_levels; ++m)
+    most = std::max(most, (unsigned)(ch.H[m] * ((ch.W[m] + kPrefilterSeg - 1) / kPrefilterSeg)));
+  dim3 grid(most, (unsigned)ch.nlev);
+  const size_t smem = (size_t)N * (sizeof(float4) + sizeof(int2) + sizeof(unsigned short));
+  void (*k)(MapDev, ChainDev, int) = int_shift ? k_prefilter<true> : k_prefilter<false>;
+  if (smem > 48 * 1024 &&
+      cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+    return fail(EPBR_ERR_CUDA, "prefilter: shared-memory attribute: %s", cudaGetErrorString(cudaGetLastError()));
+  // a small shared-memory carve-out leaves most of the SM's 256 KB to L1, which holds the source
+  // rows the resident blocks read (two rows of up to 16 KB per block)
+  cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, 50);  // a hint; failure is harmless
+  k<<<grid, kPrefilterThreads, smem, s>>>(src, ch, N);
   if ((st = check_launch("k_prefilter"))) return st;
   return ok();
 }

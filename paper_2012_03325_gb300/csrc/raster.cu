@@ -4,13 +4,16 @@
 //                      bounding box; the triangle's work item count is its box area (0: culled)
 //   k_scan_*           exclusive int64 prefix sum of the item counts (block scan, scan of the
 //                      block totals, add)
-//   k_raster_cover     one work item per (triangle, box pixel): threads take runs of 8 items (one
-//                      binary search per run, then a walk along the box rows), test the pixel
+//   k_raster_cover     one work item per (triangle, box pixel): threads take runs of 8 items (a
+//                      binary search for the run's first triangle and for each later one, so runs
+//                      of culled triangles cost nothing, and a walk along the box rows), test the pixel
 //                      centre with 64-bit integer edge
 //                      functions and a top-left rule, and keep the nearest (depth bits, index)
 //                      with a 64-bit atomicMin per pixel
 //   k_raster_resolve   one thread per pixel: the winning triangle's perspective-correct weights
 //                      and interpolated attributes, written as the FP32 G-buffer
+//   k_raster_depth     depth-only resolve: the shadow map of a light (Sec. 5.1 renders the scene
+//                      "as a depth map" from each point light as from a normal camera)
 // The coverage and depth decisions evaluate exactly the expressions of the oracle (integer edge
 // functions; FP32 products, sums and quotients each rounded), so the covering triangle of every
 // pixel is reproducible bit for bit.
@@ -206,8 +209,9 @@ void launch_exclusive_scan(long long* data, long long n, long long* sums, cudaSt
 // ---- coverage --------------------------------------------------------------------------------
 constexpr int kCoverThreads = 256;
 
-// Threads take runs of 8 consecutive items: one binary search per run for the first item's
-// triangle, then a walk along the box rows (and on to the next triangles).
+// Threads take runs of 8 consecutive items: a binary search for the first item's triangle, then a
+// walk along the box rows and on to the next triangles (each found by a binary search as well:
+// a view that culls most triangles leaves long stretches of empty ones between two with items).
 __global__ void __launch_bounds__(kCoverThreads) k_raster_cover(const TriSetup* __restrict__ setup,
                                                                 const long long* __restrict__ offsets, int T,
                                                                 const long long* __restrict__ total_p, int W,
@@ -233,10 +237,21 @@ __global__ void __launch_bounds__(kCoverThreads) k_raster_cover(const TriSetup* 
     long long wc = 0, wa = 0, wb = 0;     // edge functions at the current pixel centre
     long long dc = 0, da = 0, db = 0;     // their change per pixel along a row
     for (; item < stop; ++item) {
-      while (item >= t_end) {  // next triangle with items
+      if (item >= t_end) {  // the next triangle with items
         ++t;
         t_begin = t_end;
         t_end = t + 1 < T ? __ldg(offsets + t + 1) : total;
+        if (item >= t_end) {  // t has no items either: a binary search skips the stretch of empty ones
+          int a = t + 1, b = T - 1;  // the last t' with offsets[t'] <= item
+          while (a < b) {
+            int mid = (a + b + 1) >> 1;
+            if (__ldg(offsets + mid) <= item) a = mid;
+            else b = mid - 1;
+          }
+          t = a;
+          t_begin = __ldg(offsets + t);
+          t_end = t + 1 < T ? __ldg(offsets + t + 1) : total;
+        }
         s = setup[t];
         fresh = true;
       }
@@ -332,6 +347,17 @@ __global__ void __launch_bounds__(256) k_raster_resolve(const float* __restrict_
   if (idp) *idp = t;
 }
 
+// Depth-only resolve (shadow maps, Sec. 5.1): the winning triangle's eye depth, +inf where no
+// triangle covers the texel.
+__global__ void __launch_bounds__(256) k_raster_depth(const unsigned long long* __restrict__ keys, int W, int H,
+                                                      float* __restrict__ out, long long pitch) {
+  int x = blockIdx.x * 32 + threadIdx.x, y = blockIdx.y * 8 + threadIdx.y;
+  if (x >= W || y >= H) return;
+  const unsigned long long key = keys[(size_t)y * W + x];
+  ((float*)((char*)out + (size_t)y * pitch))[x] =
+      key == ~0ULL ? __int_as_float(0x7f800000) : __uint_as_float((unsigned)(key >> 32));
+}
+
 static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 struct RasterLayout {
@@ -365,6 +391,57 @@ extern "C" epbr_status epbr_raster_workspace_size(int32_t num_triangles, int32_t
   return ok();
 }
 
+namespace epbr {
+
+static epbr_status validate_mesh(const epbr_mesh* mesh, float near_depth) {
+  if (mesh->num_vertices < 0 || mesh->num_triangles < 0 || mesh->num_vertices > (1 << 28) ||
+      (mesh->num_triangles > 0 && (!mesh->vertices || !mesh->triangles)) || (uintptr_t)mesh->vertices % 16 ||
+      (uintptr_t)mesh->triangles % 4)
+    return fail(EPBR_ERR_INVALID_ARG, "raster: vertices / triangles NULL, misaligned or counts out of range");
+  if (!(near_depth > 0.0f) || !std::isfinite(near_depth)) return fail(EPBR_ERR_INVALID_ARG, "raster: near must be > 0");
+  return EPBR_OK;
+}
+
+static RasterCam make_raster_cam(const epbr_camera& camera, float near_depth) {
+  RasterCam rc;
+  CamDev cd = make_cam(camera);
+  for (int i = 0; i < 9; ++i) rc.r[i] = cd.r[i];
+  for (int i = 0; i < 3; ++i) rc.eye[i] = cd.eye[i];
+  const int W = camera.width, H = camera.height;
+  double t = std::tan(0.5 * (double)camera.fov_y);
+  rc.ky = (float)(1.0 / t);
+  rc.kx = (float)((double)H / ((double)W * t));
+  rc.hw = (float)(0.5 * W);
+  rc.hh = (float)(0.5 * H);
+  rc.near = near_depth;
+  rc.W = W;
+  rc.H = H;
+  return rc;
+}
+
+// Set-up, scan and coverage of the mesh seen by `rc`: the nearest (depth, triangle) key of
+// every pixel in the workspace's key image.
+static epbr_status raster_keys(const epbr_mesh* mesh, const RasterCam& rc, const RasterLayout& l, char* ws,
+                               cudaStream_t s) {
+  const int T = mesh->num_triangles;
+  unsigned long long* keys = (unsigned long long*)(ws + l.keys);
+  TriSetup* setup = (TriSetup*)(ws + l.setup);
+  long long* offsets = (long long*)(ws + l.offsets);
+  long long* sums = (long long*)(ws + l.sums);
+  if (cudaMemsetAsync(keys, 0xff, sizeof(unsigned long long) * (size_t)rc.W * rc.H, s) != cudaSuccess)
+    return fail(EPBR_ERR_CUDA, "raster: memset failed");
+  if (T > 0) {
+    k_raster_setup<<<(T + 255) / 256, 256, 0, s>>>(mesh->vertices, mesh->num_vertices, mesh->triangles, T, rc, setup,
+                                                   offsets);
+    const long long nb = scan_num_blocks(T);
+    launch_exclusive_scan(offsets, T, sums, s);
+    k_raster_cover<<<num_sms() * 8, kCoverThreads, 0, s>>>(setup, offsets, T, sums + nb, rc.W, keys);
+  }
+  return EPBR_OK;
+}
+
+}  // namespace epbr
+
 extern "C" epbr_status epbr_raster_gbuffer(const epbr_mesh* mesh, const epbr_camera* camera, float near_depth,
                                            const epbr_gbuffer* out, int32_t* ids, int64_t ids_pitch, void* workspace,
                                            size_t workspace_bytes, void* stream) {
@@ -373,11 +450,7 @@ extern "C" epbr_status epbr_raster_gbuffer(const epbr_mesh* mesh, const epbr_cam
   if (st) return st;
   if (out->format != EPBR_GBUFFER_FP32) return fail(EPBR_ERR_INVALID_ARG, "raster: the output G-buffer must be FP32");
   if ((st = validate_gbuffer(out, true))) return st;
-  if (mesh->num_vertices < 0 || mesh->num_triangles < 0 || mesh->num_vertices > (1 << 28) ||
-      (mesh->num_triangles > 0 && (!mesh->vertices || !mesh->triangles)) || (uintptr_t)mesh->vertices % 16 ||
-      (uintptr_t)mesh->triangles % 4)
-    return fail(EPBR_ERR_INVALID_ARG, "raster: vertices / triangles NULL, misaligned or counts out of range");
-  if (!(near_depth > 0.0f) || !std::isfinite(near_depth)) return fail(EPBR_ERR_INVALID_ARG, "raster: near must be > 0");
+  if ((st = validate_mesh(mesh, near_depth))) return st;
   if (ids && (ids_pitch < 4LL * out->width || ids_pitch % 4 || (uintptr_t)ids % 4))
     return fail(EPBR_ERR_INVALID_ARG, "raster: ids misaligned or pitch too small");
   const int W = out->width, H = out->height, T = mesh->num_triangles;
@@ -385,35 +458,48 @@ extern "C" epbr_status epbr_raster_gbuffer(const epbr_mesh* mesh, const epbr_cam
   if (!workspace || (uintptr_t)workspace % 256 || workspace_bytes < l.bytes)
     return fail(EPBR_ERR_INVALID_ARG, "raster: workspace NULL, not 256-byte aligned or below %zu bytes", l.bytes);
   char* ws = (char*)workspace;
-  unsigned long long* keys = (unsigned long long*)(ws + l.keys);
-  TriSetup* setup = (TriSetup*)(ws + l.setup);
-  long long* offsets = (long long*)(ws + l.offsets);
-  long long* sums = (long long*)(ws + l.sums);
-  RasterCam rc;
-  CamDev cd = make_cam(*camera);
-  for (int i = 0; i < 9; ++i) rc.r[i] = cd.r[i];
-  for (int i = 0; i < 3; ++i) rc.eye[i] = cd.eye[i];
-  double t = std::tan(0.5 * (double)camera->fov_y);
-  rc.ky = (float)(1.0 / t);
-  rc.kx = (float)((double)H / ((double)W * t));
-  rc.hw = (float)(0.5 * W);
-  rc.hh = (float)(0.5 * H);
-  rc.near = near_depth;
-  rc.W = W;
-  rc.H = H;
   cudaStream_t s = (cudaStream_t)stream;
-  if (cudaMemsetAsync(keys, 0xff, sizeof(unsigned long long) * (size_t)W * H, s) != cudaSuccess)
-    return fail(EPBR_ERR_CUDA, "raster: memset failed");
+  if ((st = raster_keys(mesh, make_raster_cam(*camera, near_depth), l, ws, s))) return st;
   GbufDev gd = make_gbuf(*out);
-  if (T > 0) {
-    k_raster_setup<<<(T + 255) / 256, 256, 0, s>>>(mesh->vertices, mesh->num_vertices, mesh->triangles, T, rc, setup,
-                                                   offsets);
-    const long long nb = scan_num_blocks(T);
-    launch_exclusive_scan(offsets, T, sums, s);
-    k_raster_cover<<<num_sms() * 8, kCoverThreads, 0, s>>>(setup, offsets, T, sums + nb, W, keys);
-  }
   dim3 blk(32, 8), grd((W + 31) / 32, (H + 7) / 8);
-  k_raster_resolve<<<grd, blk, 0, s>>>(mesh->vertices, setup, keys, W, H, gd, ids, ids_pitch);
+  k_raster_resolve<<<grd, blk, 0, s>>>(mesh->vertices, (const TriSetup*)(ws + l.setup),
+                                       (const unsigned long long*)(ws + l.keys), W, H, gd, ids, ids_pitch);
   if ((st = check_launch("raster"))) return st;
+  return ok();
+}
+
+extern "C" epbr_status epbr_shadow_maps_workspace_size(int32_t num_triangles, int32_t size, size_t* bytes) {
+  return epbr_raster_workspace_size(num_triangles, size, size, bytes);
+}
+
+extern "C" epbr_status epbr_shadow_maps(const epbr_mesh* mesh, const epbr_camera* cameras, int32_t num_maps,
+                                        float near_depth, float* maps, void* workspace, size_t workspace_bytes,
+                                        void* stream) {
+  if (!mesh || !cameras || num_maps < 0 || (num_maps > 0 && !maps) || (uintptr_t)maps % 4)
+    return fail(EPBR_ERR_INVALID_ARG, "shadow_maps: mesh, cameras or maps NULL / misaligned, or num_maps < 0");
+  if (num_maps == 0) return ok();
+  epbr_status st = validate_mesh(mesh, near_depth);
+  if (st) return st;
+  const int S = cameras[0].width;
+  for (int i = 0; i < num_maps; ++i) {
+    const epbr_camera& c = cameras[i];
+    if (c.width != S || c.height != S || S < 1 || S > (1 << 15) || !(c.fov_y > 0.0f && c.fov_y < 3.1f))
+      return fail(EPBR_ERR_INVALID_ARG, "shadow_maps: camera %d must be square, of the first camera's size (%d), "
+                                        "with a field of view in (0, 3.1) rad", i, S);
+    for (int k = 0; k < 16; ++k)
+      if (!std::isfinite(c.view_to_world[k])) return fail(EPBR_ERR_INVALID_ARG, "shadow_maps: camera %d not finite", i);
+  }
+  RasterLayout l = raster_layout(mesh->num_triangles, S, S);
+  if (!workspace || (uintptr_t)workspace % 256 || workspace_bytes < l.bytes)
+    return fail(EPBR_ERR_INVALID_ARG, "shadow_maps: workspace NULL, not 256-byte aligned or below %zu bytes", l.bytes);
+  char* ws = (char*)workspace;
+  cudaStream_t s = (cudaStream_t)stream;
+  dim3 blk(32, 8), grd((S + 31) / 32, (S + 7) / 8);
+  for (int i = 0; i < num_maps; ++i) {  // one light after the other through the same workspace (stream order)
+    if ((st = raster_keys(mesh, make_raster_cam(cameras[i], near_depth), l, ws, s))) return st;
+    k_raster_depth<<<grd, blk, 0, s>>>((const unsigned long long*)(ws + l.keys), S, S, maps + (size_t)i * S * S,
+                                       4LL * S);
+  }
+  if ((st = check_launch("shadow_maps"))) return st;
   return ok();
 }

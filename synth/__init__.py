@@ -248,22 +248,32 @@ def light_camera(light_pos, target=(0.0, 0.0, 0.0)) -> np.ndarray:
     return camera_matrix(light_pos, target, up)
 
 
-def make_shadow_maps(scene: "Scene", size: int, fov_deg: float = 90.0, target=(0.0, 0.0, 0.0)):
-    """Per-light shadow maps of the analytic scene: each light's camera (light_camera) renders a
-    size x size map of eye depths (+inf = nothing) by the same float64 ray cast as the G-buffer.
-    Returns (maps (NL, size, size) float32, cams (NL, 16) float32): cams[i, :12] are the rows of the
-    world->light-view matrix, cams[i, 12] = 1 / tan(fov / 2)."""
+def shadow_cameras(scene: "Scene", fov_deg: float = 90.0, target=(0.0, 0.0, 0.0)):
+    """Each light's shadow camera (light_camera): returns (view_to_world list of (4, 4) float64,
+    cams (NL, 16) float32) with cams[i, :12] the rows of the world->light-view matrix and
+    cams[i, 12] = 1 / tan(fov / 2)."""
     nl = len(scene.lights)
-    maps = np.zeros((nl, size, size), np.float32)
     cams = np.zeros((nl, 16), np.float32)
     f = 1.0 / math.tan(math.radians(fov_deg) / 2)
+    v2ws = []
     for i in range(nl):
         v2w = light_camera(scene.lights[i, :3].astype(np.float64), target)
-        sc = replace(scene, width=size, height=size, view_to_world=v2w, fov_y=math.radians(fov_deg))
-        maps[i] = raycast_gbuffer(sc).depth
+        v2ws.append(v2w)
         w2v = np.linalg.inv(v2w)
         cams[i, :12] = w2v[:3, :4].reshape(-1)
         cams[i, 12] = f
+    return v2ws, cams
+
+
+def make_shadow_maps(scene: "Scene", size: int, fov_deg: float = 90.0, target=(0.0, 0.0, 0.0)):
+    """Per-light shadow maps of the analytic scene: each light's camera (light_camera) renders a
+    size x size map of eye depths (+inf = nothing) by the same float64 ray cast as the G-buffer.
+    Returns (maps (NL, size, size) float32, cams (NL, 16) float32) as shadow_cameras describes."""
+    v2ws, cams = shadow_cameras(scene, fov_deg, target)
+    maps = np.zeros((len(v2ws), size, size), np.float32)
+    for i, v2w in enumerate(v2ws):
+        sc = replace(scene, width=size, height=size, view_to_world=v2w, fov_y=math.radians(fov_deg))
+        maps[i] = raycast_gbuffer(sc).depth
     return maps, cams
 
 

@@ -237,3 +237,30 @@ def test_surfel_checks(lib):
     assert call(ok, out=gbuf(fmt=F.EPBR_GBUFFER_COMPACT)) == INVALID
     assert call(ok, wp=FAKE + 2, wpitch=64 * 4) == INVALID              # weight misaligned
     assert call(ok, wp=FAKE, wpitch=63 * 4) == INVALID                  # weight pitch too small
+
+
+def test_shadow_maps_checks(lib):
+    """epbr_shadow_maps refuses bad arguments synchronously, before any launch."""
+    n = C.c_size_t()
+    assert lib.epbr_shadow_maps_workspace_size(1000, 128, C.byref(n)) == F.EPBR_OK and n.value > 0
+    assert lib.epbr_shadow_maps_workspace_size(1000, 0, C.byref(n)) == INVALID
+    mesh = F.epbr_mesh(FAKE, 3, FAKE, 1)
+    cams = (F.epbr_camera * 2)(camera(32, 32), camera(32, 32))
+    for c in cams:
+        c.fov_y = 1.5
+    assert lib.epbr_shadow_maps_workspace_size(1, 32, C.byref(n)) == F.EPBR_OK
+    call = lambda cs=cams, k=2, near=0.05, maps=FAKE, ws=FAKE, wsb=n.value: lib.epbr_shadow_maps(
+        C.byref(mesh), cs, k, near, maps, ws, wsb, None)
+    assert call(k=0) == F.EPBR_OK                      # nothing to render
+    assert call(near=0.0) == INVALID
+    assert call(maps=None) == INVALID
+    assert call(maps=FAKE + 2) == INVALID              # misaligned maps
+    assert call(ws=FAKE + 16) == INVALID               # workspace not 256-byte aligned
+    assert call(wsb=n.value - 1) == INVALID            # workspace too small
+    odd = (F.epbr_camera * 2)(camera(32, 32), camera(32, 16))
+    for c in odd:
+        c.fov_y = 1.5
+    assert call(cs=odd) == INVALID and "square" in last_error(lib)
+    wide = (F.epbr_camera * 2)(camera(32, 32), camera(32, 32))
+    wide[1].fov_y = 3.2
+    assert call(cs=wide) == INVALID

@@ -146,3 +146,83 @@ def test_invalid_shadow_arguments():
     with pytest.raises(ep.EpbrError):  # no output
         ep.epbr_shade_shadows(d["gb"], d["cam"], d["lights"], None, ep.shade_params(ep.EPBR_SHADE_DIRECT),
                               ep.Shadows(m, c), None, 0)
+
+
+# ------------------------------------------------------------------------------------------
+# shadow maps rendered on the device from the scene's triangle mesh (Sec. 5.1)
+# ------------------------------------------------------------------------------------------
+NEAR = 0.05
+
+
+def _light_cameras(sc, S, fov_deg=90.0):
+    """The lights' shadow cameras for the ABI and for the oracle (the ABI's FP32 field of view),
+    and the world -> light-view rows the shading takes."""
+    import math
+    v2ws, cams = synth.shadow_cameras(sc, fov_deg)
+    cols = [np.asarray(v, np.float32).T.reshape(-1) for v in v2ws]
+    fov = math.radians(fov_deg)
+    return ([ep.camera(c, fov, S, S) for c in cols], [oracle.camera(c, float(np.float32(fov)), S, S) for c in cols],
+            cams)
+
+
+def _device_maps(mesh, ep_cams, S):
+    maps = torch.full((len(ep_cams), S, S), float("nan"), device="cuda")
+    ep.epbr_shadow_maps(mesh, ep_cams, NEAR, maps)
+    torch.cuda.synchronize()
+    return maps
+
+
+@pytest.mark.parametrize("S,lights", [(128, 4), (97, 3), (1, 2)])
+def test_device_shadow_maps_equal_the_oracle_raster(S, lights):
+    """Each map is the depth plane of the mesh rendered from the light's camera: identical, bit for
+    bit, to the oracle's G-buffer pass (same coverage, depth and tie rules), +inf where empty."""
+    inp = make_inputs("small", W=64, H=48, lights=lights)
+    verts, tris = synth.make_mesh_scene(inp.scene, 10, 20, 12)
+    mesh = ep.Mesh(torch.from_numpy(verts).cuda(), torch.from_numpy(tris).cuda())
+    ep_cams, o_cams, _ = _light_cameras(inp.scene, S)
+    maps = _device_maps(mesh, ep_cams, S).cpu().numpy()
+    for i, oc in enumerate(o_cams):
+        ogb, _ = oracle.raster(verts, tris, oc, NEAR)
+        np.testing.assert_array_equal(maps[i], ogb[..., 8].astype(np.float32))
+    if S > 1:
+        assert np.isfinite(maps).mean() > 0.5
+
+
+def test_shadowed_compose_fed_by_device_maps():
+    """epbr_shade_shadows fed only by maps epbr_shadow_maps rendered on the device, against the
+    oracle fed by its own maps (its G-buffer pass from the same light cameras), within the tie
+    bounds; the mesh's shadows darken part of the frame."""
+    inp = make_inputs("small", W=160, H=96)
+    verts, tris = synth.make_mesh_scene(inp.scene, 12, 24, 16)
+    mesh = ep.Mesh(torch.from_numpy(verts).cuda(), torch.from_numpy(tris).cuda())
+    S = 128
+    ep_cams, o_cams, cams = _light_cameras(inp.scene, S)
+    maps_dev = _device_maps(mesh, ep_cams, S)
+    d = gpu_inputs(inp)
+    ibl = gpu_ibl(inp, d["env"])
+    sh = ep.Shadows(maps_dev, torch.from_numpy(cams).cuda(), B0, B1)
+    hdr = torch.zeros(inp.H, inp.W, 4, device="cuda")
+    ep.epbr_shade_shadows(d["gb"], d["cam"], d["lights"], ibl, ep.shade_params(ep.EPBR_SHADE_ALL, None, 2), sh, hdr, 0)
+    torch.cuda.synchronize()
+    omaps = np.stack([oracle.raster(verts, tris, oc, NEAR)[0][..., 8] for oc in o_cams]).astype(np.float32)
+    out, lo, hi = oracle_of(inp, omaps, cams, ep.EPBR_SHADE_ALL)
+    check_bounds(hdr.cpu().numpy()[..., :3], lo, hi)
+    unshadowed = oracle.shade(decoded(inp), oracle_camera(inp), inp.scene.lights, oracle_ibl(inp), ep.EPBR_SHADE_ALL)
+    assert (out < unshadowed - 1e-6).any()
+
+
+def test_shadow_maps_invalid_arguments():
+    inp = make_inputs("small", W=16, H=8, lights=2)
+    verts, tris = synth.make_mesh_scene(inp.scene, 4, 8, 2)
+    mesh = ep.Mesh(torch.from_numpy(verts).cuda(), torch.from_numpy(tris).cuda())
+    ep_cams, _, _ = _light_cameras(inp.scene, 16)
+    maps = torch.zeros(2, 16, 16, device="cuda")
+    with pytest.raises(ep.EpbrError):  # near must be > 0
+        ep.epbr_shadow_maps(mesh, ep_cams, 0.0, maps)
+    bad = [ep_cams[0], ep.camera(list(ep_cams[1].view_to_world), ep_cams[1].fov_y, 16, 15)]
+    with pytest.raises(ep.EpbrError):  # not square
+        ep.epbr_shadow_maps(mesh, bad, NEAR, maps)
+    with pytest.raises(ValueError):  # maps too small for two 16 x 16 maps
+        ep.epbr_shadow_maps(mesh, ep_cams, NEAR, torch.zeros(1, 16, 16, device="cuda"))
+    with pytest.raises(ep.EpbrError):  # workspace too small
+        ep.epbr_shadow_maps(mesh, ep_cams, NEAR, maps, workspace=torch.empty(512, dtype=torch.uint8, device="cuda"))
