@@ -40,7 +40,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=2000)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="epbr", choices=["epbr", "reference"])
-    ap.add_argument("--workload", default=WORKLOAD, choices=sorted(synth.CONFIGS) + ["batch", "serve", "edl"])
+    ap.add_argument("--workload", default=WORKLOAD,
+                    choices=sorted(synth.CONFIGS) + ["batch", "batch_small", "serve", "edl"])
     ap.add_argument("--serve-requests", type=int, default=300, help="requests per rate (serve workload)")
     ap.add_argument("--serve-seconds", type=float, default=3.0, help="arrival window per rate (serve workload)")
     ap.add_argument("--serve-streams", type=int, default=8, help="server streams (serve workload)")
@@ -809,6 +810,11 @@ def run_gpu(args):
         mb = measure_batch(args, max_steps=10)
         line["batch"] = {k: mb[k] for k in ("value", "unit", "speedup_vs_plain", "plain_per_view", "ms_per_step",
                                             "steps", "plan", "workload", "clocks", "l2")}
+        # many small views (the serving workload's 256x256 class), where the per-view loop is
+        # bound by its launches and partly idle grids
+        ms_ = measure_batch(args, max_steps=10, specs=small_batch_views())
+        line["batch_small_views"] = {k: ms_[k] for k in ("value", "unit", "speedup_vs_plain", "plain_per_view",
+                                                         "ms_per_step", "steps", "plan", "workload", "clocks")}
         ms = measure_serve(args, rates=SERVE_DEFAULT_RATES)
         line["serve"] = {"value": ms["value"], "unit": "Mpixels/s", "speedup_vs_fifo": ms["speedup_vs_fifo"],
                          "fifo_mpx_s": ms["fifo_one_at_a_time"]["mpx_s"],
@@ -929,12 +935,20 @@ def _gen_view(spec):
     return g.rt0, g.rt1, g.depth, sc.lights, sc.camera_array(), sc.fov_y
 
 
-def measure_batch(args, max_steps: int = 20) -> dict:
+def small_batch_views(n_views: int = 256, seed: int = 3000):
+    """Many small views: n_views of 256x256 (the serving workload's smallest resolution class),
+    16-256 lights (log-uniform), 8 environments, as (W, H, lights, env, seed) like batch_views."""
+    rng = synth.PCG32(seed, stream=31)
+    return [(256, 256, int(round(math.exp(rng.uniform(math.log(16.0), math.log(256.0))))), i % 8, seed + i)
+            for i in range(n_views)]
+
+
+def measure_batch(args, max_steps: int = 20, specs=None) -> dict:
     """The multi-view workload: 64 views in one persistent launch replayed from a CUDA graph
     against the plain per-view loop (3 launches per view) on the same views and stream."""
     import multiprocessing as mp
 
-    specs = synth.batch_views()
+    specs = synth.batch_views() if specs is None else specs
     ctx = mp.get_context("spawn")  # no CUDA state in the workers
     with ctx.Pool(max(1, min(16, os.cpu_count() or 1))) as pool:
         gen = list(pool.imap(_gen_view, specs))
@@ -1012,7 +1026,7 @@ def measure_batch(args, max_steps: int = 20) -> dict:
     return {"value": batched, "unit": "Mpixels/s", "steps": steps, "ms_per_step": sum(batch_ms) / steps,
             "views": len(specs), "pixels_per_step": total_px,
             "workload": f"batch: {len(specs)} views, {total_px / 1e6:.1f} Mpx, resolutions "
-                        "{512^2, 1280x720, 1920x1080, 3840x2160}, 16-256 lights (log-uniform), "
+                        f"{sorted(set((W, H) for W, H, *_r in specs))}, 16-256 lights (log-uniform), "
                         "8 environments 1024x512 (M=8, N_s=1024, LUT 64^2), SSAO 32 + 7x7",
             "plan": {"mode": ["fused", "staged"][plan[0]], "tile_w": plan[1], "tile_h": plan[2],
                      "light_chunk": plan[3]},
@@ -1025,7 +1039,7 @@ def measure_batch(args, max_steps: int = 20) -> dict:
 def run_batch(args):
     import torch
     torch.cuda.set_device(0)
-    m = measure_batch(args)
+    m = measure_batch(args, specs=small_batch_views() if args.workload == "batch_small" else None)
     line = {"metric": METRIC, "value": m["value"], "unit": "Mpixels/s", "n_gpus": 1, "steps": m["steps"],
             "warmup": args.warmup, "ms_per_step": m["ms_per_step"], "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
@@ -1209,7 +1223,7 @@ def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
-    elif args.workload == "batch":
+    elif args.workload in ("batch", "batch_small"):
         run_batch(args)
     elif args.workload == "serve":
         run_serve(args)
