@@ -4,9 +4,11 @@
 // A scheduler thread owns admission.  Requests queue in arrival order; whenever a slot is free
 // and the device-memory arena (one allocation of `memory_budget` bytes, first-fit with
 // coalescing, bookkept on the host) can hold a request's buffers, the head request is admitted:
-// its G-buffer and lights are copied in, SSAO + blur + compose + tone map are enqueued, the 8-bit
-// image is copied out, all on one of the server's streams, so admitted requests overlap on the
-// device.  A host-function callback at the end of each request's stream work stamps its
+// its G-buffer is copied in as chunks spread over the server's copy streams (one host-to-device
+// copy on one stream moves a fraction of what the host link carries; several in parallel fill
+// it), its lights are copied and SSAO + blur + compose + tone map enqueued on one of the server's
+// compute streams, which waits for the chunks, and the 8-bit image is copied out on it, so
+// admitted requests overlap on the device.  A host-function callback at the end of each request's stream work stamps its
 // completion and wakes the scheduler, which returns the memory and admits more.  Queued requests
 // whose deadline passes are cancelled on the host (EPBR_ERR_TIMEOUT); nothing waits on the GPU
 // without a bound.
@@ -28,6 +30,8 @@ namespace {
 
 using Clock = std::chrono::steady_clock;
 constexpr size_t kAlign = 256;
+constexpr int kCopyStreams = 4;                  // G-buffer upload streams
+constexpr size_t kUploadChunk = (size_t)8 << 20;  // bytes per upload copy
 
 size_t up(size_t x) { return (x + kAlign - 1) & ~(kAlign - 1); }
 
@@ -122,6 +126,9 @@ struct epbr_server {
   Arena arena;
   std::vector<cudaStream_t> streams;
   int next_stream = 0;
+  std::vector<cudaStream_t> copy_streams;  // G-buffer uploads, chunk by chunk
+  std::vector<cudaEvent_t> copy_events;    // one per copy stream: its latest chunk
+  int next_copy = 0;
   std::mutex mu;
   std::condition_variable cv_sched, cv_done;
   std::deque<Req*> queue;
@@ -179,9 +186,20 @@ epbr_status enqueue(epbr_server* s, Req* q) {
     if (!q->L.bpp[i]) continue;
     g.rt[i] = base + q->L.rt[i];
     g.pitch[i] = (int64_t)r.width * q->L.bpp[i];
-    size_t n = (size_t)r.width * r.height * q->L.bpp[i];
-    if (cudaMemcpyAsync(base + q->L.rt[i], r.rt[i], n, cudaMemcpyHostToDevice, st) != cudaSuccess)
-      return epbr::fail(EPBR_ERR_CUDA, "serve: G-buffer upload: %s", cudaGetErrorString(cudaGetLastError()));
+    const size_t n = (size_t)r.width * r.height * q->L.bpp[i];
+    // chunks of at most kUploadChunk bytes round-robin over the copy streams; the compute stream
+    // waits for each (cudaStreamWaitEvent takes the event's latest record, so an event is free
+    // for the next chunk of its stream as soon as the wait is enqueued)
+    for (size_t o = 0; o < n; o += kUploadChunk) {
+      const size_t c = n - o < kUploadChunk ? n - o : kUploadChunk;
+      const int k = s->next_copy;
+      s->next_copy = (s->next_copy + 1) % (int)s->copy_streams.size();
+      if (cudaMemcpyAsync(base + q->L.rt[i] + o, (const char*)r.rt[i] + o, c, cudaMemcpyHostToDevice,
+                          s->copy_streams[k]) != cudaSuccess ||
+          cudaEventRecord(s->copy_events[k], s->copy_streams[k]) != cudaSuccess ||
+          cudaStreamWaitEvent(st, s->copy_events[k], 0) != cudaSuccess)
+        return epbr::fail(EPBR_ERR_CUDA, "serve: G-buffer upload: %s", cudaGetErrorString(cudaGetLastError()));
+    }
   }
   epbr_light* d_lights = (epbr_light*)(base + q->L.lights);
   if (r.num_lights > 0 &&
@@ -303,6 +321,22 @@ extern "C" epbr_status epbr_serve_create(const epbr_serve_config* cfg, epbr_serv
     }
     s->streams.push_back(st);
   }
+  for (int i = 0; i < kCopyStreams; ++i) {
+    cudaStream_t cs;
+    cudaEvent_t ev;
+    if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) {
+      cudaGetLastError();
+      epbr_serve_destroy(s);
+      return fail(EPBR_ERR_CUDA, "serve: copy stream creation failed");
+    }
+    s->copy_streams.push_back(cs);
+    if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) {
+      cudaGetLastError();
+      epbr_serve_destroy(s);
+      return fail(EPBR_ERR_CUDA, "serve: event creation failed");
+    }
+    s->copy_events.push_back(ev);
+  }
   s->sched = std::thread(scheduler, s);
   *out = s;
   return ok();
@@ -414,11 +448,16 @@ extern "C" epbr_status epbr_serve_destroy(epbr_server* s) {
     s->stop = true;
     s->cv_sched.notify_one();
   }
-  s->sched.join();
+  if (s->sched.joinable()) s->sched.join();
   for (cudaStream_t st : s->streams) {
     cudaStreamSynchronize(st);
     cudaStreamDestroy(st);
   }
+  for (cudaStream_t st : s->copy_streams) {
+    cudaStreamSynchronize(st);
+    cudaStreamDestroy(st);
+  }
+  for (cudaEvent_t ev : s->copy_events) cudaEventDestroy(ev);
   cudaFree(s->d_arena);
   for (auto& kv : s->reqs) delete kv.second;
   delete s;
