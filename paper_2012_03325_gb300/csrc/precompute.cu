@@ -3,7 +3,8 @@
 //   k_irradiance_part   exact-quadrature irradiance, per-block partial sums over a slice of
 //                       source texels staged in shared memory (packed FP32x2 over output pairs,
 //                       plain sums per staged tile, Kahan across tiles)
-//   k_irradiance_final  sums the partials in a fixed order (deterministic) and normalises
+//   k_irradiance_final  one warp per output: lanes sum the block partials, a shuffle butterfly
+//                       adds the lanes (fixed order: deterministic), then the ratio
 //   k_prefilter         GGX-prefiltered levels 1..M-1, one block per row of a level: the row's
 //                       sample geometry computed once (the sampling frame turns with the texel
 //                       about the pole axis), each texel sums its samples at shifted columns
@@ -180,21 +181,26 @@ __global__ void __launch_bounds__(kIrrThreads) k_irradiance_part(const float4* _
   }
 }
 
+// One warp per output texel: lane l sums the partials of blocks l, l + 32, ... (Kahan), then the
+// lanes' sums are added by a butterfly of shuffles (a fixed order: deterministic).
 __global__ void k_irradiance_final(const float4* __restrict__ part, int nblocks, int nout,
                                    float4* __restrict__ out) {
-  int o = blockIdx.x * blockDim.x + threadIdx.x;
-  if (o >= nout) return;
+  const int o = (int)((blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5);
+  const int lane = threadIdx.x & 31;
+  if (o >= nout) return;  // warp-uniform
   Kahan s[4];
-  for (int b = 0; b < nblocks; ++b) {
-    float4 p = part[(size_t)b * nout + o];
+  for (int b = lane; b < nblocks; b += 32) {
+    float4 p = __ldg(part + (size_t)b * nout + o);
     s[0].add(p.x);
     s[1].add(p.y);
     s[2].add(p.z);
     s[3].add(p.w);
   }
-  float den = s[3].s - s[3].c;
+  const float r = warp_sum(s[0].s - s[0].c), g = warp_sum(s[1].s - s[1].c);
+  const float bl = warp_sum(s[2].s - s[2].c), den = warp_sum(s[3].s - s[3].c);
+  if (lane != 0) return;
   float inv = den > 0.0f ? 1.0f / den : 0.0f;  // no texel centre in the hemisphere: 0
-  out[o] = make_float4((s[0].s - s[0].c) * inv, (s[1].s - s[1].c) * inv, (s[2].s - s[2].c) * inv, 1.0f);
+  out[o] = make_float4(r * inv, g * inv, bl * inv, 1.0f);
 }
 
 // ------------------------------------------------------------------------------------------
@@ -519,7 +525,8 @@ extern "C" epbr_status epbr_irradiance(const epbr_env* env, int32_t Wi, int32_t 
                                                Hi, (float4*)ws);
   if ((st = check_launch("k_irradiance_part"))) return st;
   int nout = Wi * Hi;
-  k_irradiance_final<<<(nout + 255) / 256, 256, 0, s>>>((const float4*)ws, nb, nout, (float4*)out);
+  k_irradiance_final<<<(unsigned)(((long long)nout * 32 + 255) / 256), 256, 0, s>>>((const float4*)ws, nb, nout,
+                                                                                   (float4*)out);
   if ((st = check_launch("k_irradiance_final"))) return st;
   return ok();
 }
@@ -620,7 +627,8 @@ extern "C" epbr_status epbr_irradiance_noalloc(const epbr_env* env, int32_t Wi, 
                                                (float4*)ws);
   if ((st = check_launch("k_irradiance_part"))) return st;
   int nout = Wi * Hi;
-  k_irradiance_final<<<(nout + 255) / 256, 256, 0, s>>>((const float4*)ws, nb, nout, (float4*)out);
+  k_irradiance_final<<<(unsigned)(((long long)nout * 32 + 255) / 256), 256, 0, s>>>((const float4*)ws, nb, nout,
+                                                                                   (float4*)out);
   if ((st = check_launch("k_irradiance_final"))) return st;
   return ok();
 }
