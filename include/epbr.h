@@ -271,12 +271,14 @@ epbr_status epbr_ssao_tiled(const epbr_gbuffer* gbuffer, const epbr_ssao_params*
  * their stream first). */
 epbr_status epbr_ssao_tile_timeouts(uint32_t* count);
 
-/* Test hook for the tiled form's fallback path: sets the limit of the first wait for the depth
- * tile (nanoseconds, at most the default 50 ms) used by later epbr_ssao_raw launches and returns
- * the previous limit in *previous_ns (nullable).  0 makes every tiled warp give up at once, read
- * its taps from the depth plane (the same AO) and count itself in epbr_ssao_tile_timeouts; the
- * second wait before a block exits keeps its 50 ms bound.  Process-wide; not for production use.
- * EPBR_ERR_INVALID_ARG above the default. */
+/* Test hook for the fallback paths of the library's TMA staging: sets the limit of the first wait
+ * for a staged copy (nanoseconds, at most the default 50 ms) used by later launches — the SSAO
+ * depth tiles of epbr_ssao_raw and the compose's light list (epbr_shade, epbr_shade_tonemap) —
+ * and returns the previous limit in *previous_ns (nullable).  0 makes every tiled SSAO warp and
+ * every compose block give up at once, read global memory instead (the same results) and count
+ * itself in epbr_ssao_tile_timeouts / epbr_shade_light_timeouts; the second wait before a block
+ * exits keeps its 50 ms bound.  Process-wide; not for production use.  EPBR_ERR_INVALID_ARG
+ * above the default. */
 epbr_status epbr_ssao_set_tile_wait(uint64_t first_wait_ns, uint64_t* previous_ns);
 
 /* Depth-aware blur of an AO image: out_p = sum_q w_q ao_q / sum_q w_q over the
@@ -349,6 +351,16 @@ epbr_status epbr_shade_tonemap(const epbr_gbuffer* gbuffer, const epbr_camera* c
                                const epbr_shade_params* params, void* hdr, int32_t hdr_format,
                                int64_t hdr_pitch, const epbr_tonemap_params* tonemap,
                                uint8_t* ldr, int64_t ldr_pitch, void* stream);
+
+/* epbr_shade and epbr_shade_tonemap copy a list of at most 256 lights into each block's shared
+ * memory with one TMA bulk copy.  Number of compose blocks whose wait for that copy ran out (50 ms
+ * by default; epbr_ssao_set_tile_wait sets this first wait too) since the last call, then reset
+ * to 0.  Such blocks read the list from global memory instead, so their result is unaffected.
+ * Such a block waits once more (50 ms) before it exits; if that wait runs out too, its copy may
+ * still land in shared memory that a later block uses, and this call returns
+ * EPBR_ERR_DEVICE_STATUS (with *count set, the flag cleared).  Synchronous copies on the current
+ * device; synchronise the launches' stream first. */
+epbr_status epbr_shade_light_timeouts(uint32_t* count);
 
 /* ---------------------------------------------------------------------------------------- */
 /* The G-buffer pass of mesh rendering (Sec. 4.1): triangles rasterised into the G-buffer    */

@@ -262,8 +262,8 @@ def epbr_ssao_tile_timeouts() -> int:
 
 
 def epbr_ssao_set_tile_wait(first_wait_ns: int) -> int:
-    """Test hook: limit of the tiled form's first depth-tile wait (0 = give up at once); returns
-    the previous limit."""
+    """Test hook: limit of the first wait for the library's TMA-staged copies (SSAO depth tiles,
+    the compose's light list; 0 = give up at once); returns the previous limit."""
     prev = C.c_uint64()
     _check(lib().epbr_ssao_set_tile_wait(int(first_wait_ns), C.byref(prev)))
     return prev.value
@@ -306,6 +306,13 @@ def epbr_shade(g: GBuffer, cam: F.epbr_camera, lights: torch.Tensor | None, ibl:
     hp = _image(hdr, g.struct.height, g.struct.width, 4, "hdr", _hdr_dtype(hdr_format))
     _check(lib().epbr_shade(C.byref(g.struct), C.byref(cam), lp, nl, C.byref(ibl.struct) if ibl else None,
                             C.byref(params), hp, hdr_format, _pitch(hdr, 1), _stream(stream)))
+
+
+def epbr_shade_light_timeouts() -> int:
+    """Compose blocks whose wait for their light list's TMA copy ran out since the last call (then reset)."""
+    n = C.c_uint32()
+    _check(lib().epbr_shade_light_timeouts(C.byref(n)))
+    return n.value
 
 
 def tonemap_params(exposure: float = 1.0, op: int = EPBR_TONEMAP_ACES) -> F.epbr_tonemap_params:

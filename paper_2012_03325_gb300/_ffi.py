@@ -167,6 +167,7 @@ PROTOTYPES = {
     "epbr_shade_tonemap": [P(epbr_gbuffer), P(epbr_camera), vp, i32, P(epbr_ibl), P(epbr_shade_params), vp,
                            i32, i64, P(epbr_tonemap_params), vp, i64, vp],
     "epbr_tonemap": [vp, i32, i32, i32, i64, P(epbr_tonemap_params), vp, i64, vp],
+    "epbr_shade_light_timeouts": [P(C.c_uint32)],
     "epbr_raster_workspace_size": [i32, i32, i32, P(sz)],
     "epbr_raster_gbuffer": [P(epbr_mesh), P(epbr_camera), C.c_float, P(epbr_gbuffer), vp, i64, vp, sz, vp],
     "epbr_shadow_maps_workspace_size": [i32, i32, P(sz)],

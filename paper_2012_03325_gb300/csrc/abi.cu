@@ -3,10 +3,11 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <atomic>
 #include <cmath>
 #include <string>
 
-#include "epbr_internal.cuh"
+#include "tma.cuh"
 
 namespace epbr {
 
@@ -32,6 +33,12 @@ epbr_status check_launch(const char* what) {
   if (e != cudaSuccess) return fail(EPBR_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
   return EPBR_OK;
 }
+
+static std::atomic<unsigned long long> g_tma_first_wait_ns{kTmaWaitNs};
+
+unsigned long long tma_first_wait_ns() { return g_tma_first_wait_ns.load(); }
+
+unsigned long long set_tma_first_wait_ns(unsigned long long ns) { return g_tma_first_wait_ns.exchange(ns); }
 
 int num_sms() {
   int dev = 0, n = 0;

@@ -1,6 +1,7 @@
 // Deferred compose and tone mapping of one view.
 //   k_shade    two pixels per thread in 32x8 blocks (32x16 pixel tiles): G-buffer decode,
-//              Cook-Torrance over the point lights (staged in shared memory in chunks of 256;
+//              Cook-Torrance over the point lights (a list of up to 256 copied into shared
+//              memory by a TMA bulk copy, longer lists staged in chunks of 256 by plain loads;
 //              monochrome chunks in packed FP32x2 arithmetic), split-sum IBL times AO,
 //              background from the environment; optional fused tone-map epilogue (Sec. 5.4).
 //              The per-pixel arithmetic lives in shade_core.cuh.
@@ -10,6 +11,7 @@
 #include <algorithm>
 
 #include "shade_core.cuh"
+#include "tma.cuh"
 
 namespace epbr {
 
@@ -22,18 +24,30 @@ constexpr int kShadeTileH = 2 * kShadeBY;  // pixel rows per block
 #define EPBR_SHADE_MIN_BLOCKS 2  // resident blocks per SM the register budget targets
 #endif
 
-// Two vertically adjacent pixels per thread, a 32 x 2*EPBR_SHADE_BY tile per block.  The G-buffer
-// loads are issued before the lights are staged so that they are in flight during the staging
-// barrier.  Lights are staged in chunks of 256; a chunk whose lights are all monochrome takes the
-// packed two-pixel loop (px_direct_mono2), any other chunk the per-pixel colour loop.
+// Compose blocks whose wait for the TMA copy of their light list ran out (they read the list from
+// global memory instead: the same values); read and cleared by epbr_shade_light_timeouts.  The
+// second flag records a block whose drain wait before exiting ran out as well.
+__device__ unsigned int g_light_stage_timeouts;
+__device__ unsigned int g_light_stage_lost;
+
+// Two vertically adjacent pixels per thread, a 32 x 2*EPBR_SHADE_BY tile per block.  A list of at
+// most 256 lights is copied into shared memory by one TMA bulk copy (issued first, completing on
+// an mbarrier, bounded wait) while the G-buffer loads are in flight; the block then stages it as
+// (pos, I c) and the packed loop's duplicated form.  Longer lists are staged in chunks of 256 by
+// plain loads.  A chunk whose lights are all monochrome takes the packed two-pixel loop
+// (px_direct_mono2), any other chunk the per-pixel colour loop.
 template <int FMT, int HDR, bool LDR>
 __global__ void __launch_bounds__(kShadeBX* kShadeBY, EPBR_SHADE_MIN_BLOCKS)
     k_shade(GbufDev g, CamDev cam, const float4* __restrict__ lights, int NL, IblDev ibl, ShadeDev p, void* hdr,
-            long long hdr_pitch, uint8_t* ldr, long long ldr_pitch) {
+            long long hdr_pitch, uint8_t* ldr, long long ldr_pitch, unsigned long long wait_ns) {
   __shared__ float4 s_lights[2 * kLightChunk];
   __shared__ float4 s_dup[2 * kLightChunk];
+  __shared__ __align__(16) float4 s_raw[2 * kLightChunk];  // the list as the bulk copy lands it
+  __shared__ __align__(8) unsigned long long s_bar;
   constexpr int kThreads = kShadeBX * kShadeBY;
   int tid = threadIdx.y * kShadeBX + threadIdx.x;
+  const bool tma = NL > 0 && NL <= kLightChunk;  // launch-uniform
+  if (tma && tid == 0) tma_load_bulk(s_raw, lights, smem_addr(&s_bar), (unsigned)NL * 32u);
   // Rows are dispatched bottom-up: the costliest tiles (ground and objects) usually fill the
   // bottom of a view and the cheap background the top, so the expensive work starts first and
   // the tail of the launch is short.  Any order gives the same image.
@@ -45,8 +59,17 @@ __global__ void __launch_bounds__(kShadeBX* kShadeBY, EPBR_SHADE_MIN_BLOCKS)
 #pragma unroll
   for (int h = 0; h < 2; ++h)
     if (in[h]) raw[h] = px_load<FMT>(g, x, yy[h]);
-  bool mono = false;
-  if (NL <= kLightChunk) mono = __syncthreads_and(stage_lights(s_lights, lights, 0, NL, tid, kThreads, s_dup));
+  bool mono = false, staged = true;
+  if (tma) {
+    __syncthreads();  // orders the mbarrier's initialisation before every thread's wait
+    // wait_ns = 0 gives up at once (the fallback path, exercised by a test)
+    staged = __syncthreads_and(wait_ns != 0 && mbar_wait_bounded(smem_addr(&s_bar), 0, wait_ns));
+    if (!staged && tid == 0) atomicAdd(&g_light_stage_timeouts, 1u);
+    mono = __syncthreads_and(staged ? stage_lights<true>(s_lights, s_raw, 0, NL, tid, kThreads, s_dup)
+                                    : stage_lights(s_lights, lights, 0, NL, tid, kThreads, s_dup));
+  } else if (NL == 0) {
+    mono = true;
+  }
   Px s[2];
   bool act[2];
 #pragma unroll
@@ -69,6 +92,10 @@ __global__ void __launch_bounds__(kShadeBX* kShadeBY, EPBR_SHADE_MIN_BLOCKS)
     if (hdr) store_hdr<HDR>(hdr, hdr_pitch, x, yy[h], c[h]);
     if (LDR) ((unsigned*)(ldr + (size_t)yy[h] * ldr_pitch))[x] = pack_rgba8(c[h], p.exposure, p.op);
   }
+  // a copy that had not landed is waited for once more (bounded) before the block's shared memory
+  // can go to another block; if that wait runs out too, the launch is flagged
+  if (tma && !staged && !mbar_wait_bounded(smem_addr(&s_bar), 0, kTmaWaitNs) && tid == 0)
+    atomicOr(&g_light_stage_lost, 1u);
 }
 
 template <int HDR>
@@ -105,10 +132,11 @@ template <int FMT, int HDR>
 static void launch_shade(dim3 grd, dim3 blk, cudaStream_t s, const GbufDev& g, const CamDev& c, const float4* L,
                          int NL, const IblDev& ibl, const ShadeDev& p, void* hdr, long long hp, uint8_t* ldr,
                          long long lp) {
+  const unsigned long long w = tma_first_wait_ns();
   if (ldr)
-    k_shade<FMT, HDR, true><<<grd, blk, 0, s>>>(g, c, L, NL, ibl, p, hdr, hp, ldr, lp);
+    k_shade<FMT, HDR, true><<<grd, blk, 0, s>>>(g, c, L, NL, ibl, p, hdr, hp, ldr, lp, w);
   else
-    k_shade<FMT, HDR, false><<<grd, blk, 0, s>>>(g, c, L, NL, ibl, p, hdr, hp, ldr, lp);
+    k_shade<FMT, HDR, false><<<grd, blk, 0, s>>>(g, c, L, NL, ibl, p, hdr, hp, ldr, lp, w);
 }
 
 static epbr_status shade_common(const epbr_gbuffer* g, const epbr_camera* cam, const epbr_light* lights,
@@ -201,6 +229,24 @@ extern "C" epbr_status epbr_shade_tonemap(const epbr_gbuffer* g, const epbr_came
                                           uint8_t* ldr, int64_t ldr_pitch, void* stream) {
   if (!ldr) return fail(EPBR_ERR_INVALID_ARG, "ldr is NULL");
   return shade_common(g, cam, lights, NL, ibl, sp, hdr, hdr_format, hdr_pitch, tp, ldr, ldr_pitch, stream);
+}
+
+extern "C" epbr_status epbr_shade_light_timeouts(uint32_t* count) {
+  if (!count) return fail(EPBR_ERR_INVALID_ARG, "count is NULL");
+  unsigned v = 0, lost = 0;
+  const unsigned zero = 0;
+  if (cudaMemcpyFromSymbol(&v, g_light_stage_timeouts, sizeof(v)) != cudaSuccess ||
+      cudaMemcpyToSymbol(g_light_stage_timeouts, &zero, sizeof(zero)) != cudaSuccess ||
+      cudaMemcpyFromSymbol(&lost, g_light_stage_lost, sizeof(lost)) != cudaSuccess ||
+      cudaMemcpyToSymbol(g_light_stage_lost, &zero, sizeof(zero)) != cudaSuccess)
+    return fail(EPBR_ERR_CUDA, "shade_light_timeouts: %s", cudaGetErrorString(cudaGetLastError()));
+  *count = v;
+  if (lost)
+    return fail(EPBR_ERR_DEVICE_STATUS,
+                "shade_light_timeouts: a block's light-list copy did not complete within two waits of %llu ms; "
+                "the results of launches since the last call are suspect",
+                (unsigned long long)(kTmaWaitNs / 1000000));
+  return ok();
 }
 
 extern "C" epbr_status epbr_tonemap(const void* hdr, int32_t hdr_format, int32_t W, int32_t H, int64_t hdr_pitch,

@@ -186,12 +186,14 @@ __device__ __forceinline__ Px px_setup(const GbufDev& g, const CamDev& cam, int 
 // the flags with __syncthreads_and to pick the monochrome loop for the chunk.  With s_dup, each
 // light is also written as (x, x, y, y), (z, z, Ic, Ic): the operands of the two-pixel packed
 // loop (px_direct_mono2), each coordinate already duplicated into both halves of a pair.
+// FROM_SMEM: `lights` is a copy of the list in shared memory (staged by a TMA bulk copy).
+template <bool FROM_SMEM = false>
 __device__ __forceinline__ bool stage_lights(float4* s_lights, const float4* __restrict__ lights, int first,
                                              int cnt, int tid, int nthreads, float4* s_dup = nullptr) {
   bool mono = true;
   for (int q = tid; q < cnt; q += nthreads) {
-    float4 a = __ldg(lights + 2 * (first + q));
-    float4 c = __ldg(lights + 2 * (first + q) + 1);
+    float4 a = FROM_SMEM ? lights[2 * (first + q)] : __ldg(lights + 2 * (first + q));
+    float4 c = FROM_SMEM ? lights[2 * (first + q) + 1] : __ldg(lights + 2 * (first + q) + 1);
     float4 ic = make_float4(a.w * c.x, a.w * c.y, a.w * c.z, 0.0f);
     s_lights[2 * q] = make_float4(a.x, a.y, a.z, ic.x);  // .w: Ic of a monochrome light
     s_lights[2 * q + 1] = ic;

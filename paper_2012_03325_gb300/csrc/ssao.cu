@@ -14,9 +14,9 @@
 #include <cuda.h>  // CUtensorMap and its encoder's enums (the encoder is fetched at run time)
 #include <string.h>
 
-#include <atomic>
 
 #include "ssao_core.cuh"
+#include "tma.cuh"
 
 namespace epbr {
 
@@ -78,7 +78,6 @@ constexpr int kSsaoHalo = 32;
 constexpr int kSsaoTileW = 64 + 2 * kSsaoHalo, kSsaoTileH = 32 + 2 * kSsaoHalo;
 constexpr unsigned kSsaoTileN = kSsaoTileW * kSsaoTileH;
 constexpr unsigned kSsaoTileBytes = kSsaoTileN * 4;
-constexpr unsigned long long kTmaWaitNs = 50ull * 1000 * 1000;  // a tile copy takes microseconds
 
 // Warps of k_ssao_raw<TILED> whose first wait for their tile copy ran out (their taps then all
 // read the depth plane, so the AO is unaffected); read and cleared by epbr_ssao_tile_timeouts.
@@ -87,50 +86,6 @@ __device__ unsigned int g_ssao_tile_timeouts;
 // still in flight towards shared memory another block may reuse: the AO of such a launch is
 // suspect.  Read and cleared by epbr_ssao_tile_timeouts, which then reports an error.
 __device__ unsigned int g_ssao_tile_lost;
-
-__device__ __forceinline__ unsigned smem_addr(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ unsigned long long global_ns() {
-  unsigned long long t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
-}
-
-__device__ __forceinline__ bool mbar_try_wait(unsigned bar, unsigned parity) {
-  unsigned done;
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-      "selp.u32 %0, 1, 0, p;\n\t}"
-      : "=r"(done)
-      : "r"(bar), "r"(parity)
-      : "memory");
-  return done != 0;
-}
-
-// Waits for phase `parity` of the mbarrier for at most `limit_ns`; false when it ran out.
-__device__ __forceinline__ bool mbar_wait_bounded(unsigned bar, unsigned parity, unsigned long long limit_ns) {
-  if (mbar_try_wait(bar, parity)) return true;
-  const unsigned long long t0 = global_ns();
-  while (!mbar_try_wait(bar, parity))
-    if (global_ns() - t0 > limit_ns) return false;
-  return true;
-}
-
-// One thread: arms the block's mbarrier for `bytes` and starts the 2-D tile copy of `map` at
-// element (x, y) into `dst` (the tensor map's box fixes the tile's shape).
-__device__ __forceinline__ void tma_load_tile_2d(const CUtensorMap* map, void* dst, unsigned bar, int x, int y,
-                                                 unsigned bytes) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
-  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
-  asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::
-          "r"(smem_addr(dst)),
-      "l"(reinterpret_cast<unsigned long long>(map)), "r"(x), "r"(y), "r"(bar)
-      : "memory");
-}
 
 // floor(x) as an unsigned pixel index without the conversion unit: x + 1.5 * 2^23 rounded down
 // lies on the float grid of spacing 1, so for |x| < 2^22 it is exactly floor(x) + 1.5 * 2^23 and
@@ -408,9 +363,6 @@ static EncodeTiledFn encode_tiled() {
 // the untiled form, at its higher occupancy, is used.
 constexpr int kSsaoTiledMaxRows = 1536;
 
-// Limit of the tiled form's first wait for its depth tile, passed to every launch; changed only
-// by epbr_ssao_set_tile_wait (a test of the fallback path sets 0).
-static std::atomic<unsigned long long> g_tile_wait_ns{kTmaWaitNs};
 
 static bool depth_tile_map(const epbr_gbuffer* g, const epbr_ssao_params* p, CUtensorMap* map) {
   if (p->scale != 2 || g->height > kSsaoTiledMaxRows || (uintptr_t)g->rt[3] % 16 || g->pitch[3] % 16 ||
@@ -476,7 +428,7 @@ extern "C" epbr_status epbr_ssao_raw(const epbr_gbuffer* g, const epbr_camera* c
     // function and device, and setting it again is harmless
     if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSsaoTileBytes) != cudaSuccess)
       return fail(EPBR_ERR_CUDA, "ssao_raw: shared-memory attribute: %s", cudaGetErrorString(cudaGetLastError()));
-    k<<<grd, blk, kSsaoTileBytes, s>>>(map, gd, cd, sd, ao, ao_pitch, Wa, Ha, g_tile_wait_ns.load());
+    k<<<grd, blk, kSsaoTileBytes, s>>>(map, gd, cd, sd, ao, ao_pitch, Wa, Ha, tma_first_wait_ns());
   } else if (fp32)
     k_ssao_raw<EPBR_GBUFFER_FP32, false><<<grd, blk, 0, s>>>(map, gd, cd, sd, ao, ao_pitch, Wa, Ha, 0ull);
   else
@@ -517,7 +469,7 @@ extern "C" epbr_status epbr_ssao_set_tile_wait(uint64_t first_wait_ns, uint64_t*
   if (first_wait_ns > kTmaWaitNs)
     return fail(EPBR_ERR_INVALID_ARG, "ssao_set_tile_wait: %llu ns above the default %llu ns",
                 (unsigned long long)first_wait_ns, (unsigned long long)kTmaWaitNs);
-  const unsigned long long prev = g_tile_wait_ns.exchange(first_wait_ns);
+  const unsigned long long prev = set_tma_first_wait_ns(first_wait_ns);
   if (previous_ns) *previous_ns = prev;
   return ok();
 }

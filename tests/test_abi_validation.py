@@ -98,6 +98,7 @@ def test_ssao_tiled_query(lib):
     assert lib.epbr_ssao_tiled(C.byref(tall), C.byref(p), C.byref(t)) == F.EPBR_OK and t.value == 0
     assert lib.epbr_ssao_tile_timeouts(None) == INVALID
     assert lib.epbr_ssao_set_tile_wait(50_000_001, None) == INVALID  # above the default 50 ms
+    assert lib.epbr_shade_light_timeouts(None) == INVALID
 
 
 @pytest.mark.parametrize("field,value", [("num_samples", 0), ("num_samples", 257), ("scale", 3), ("radius", 0.0),

@@ -363,3 +363,31 @@ def test_shade_colored_light_behind_a_grazing_view(nv, el):
             assert ref.max() > 0
             rel = np.abs(got - ref) / np.abs(ref).max()
             assert rel.max() <= REL_TOL_FP32, (metal, rough, phi, rel.max())
+
+
+@pytest.mark.parametrize("NL", [7, 256])
+def test_light_list_staging_wait_runs_out(NL):
+    """The compose copies a list of up to 256 lights into shared memory with a TMA bulk copy
+    completing on an mbarrier.  With the first wait's limit at 0 every block gives up on the copy
+    at once, stages the list from global memory and counts itself; the image is identical bit for
+    bit, and with the default limit nothing times out."""
+    inp = make_inputs("small", W=131, H=77, lights=NL)
+    d = gpu_inputs(inp)
+    ibl = gpu_ibl(inp, d["env"])
+    sp = ep.shade_params(ep.EPBR_SHADE_ALL)
+    ref = torch.zeros(inp.H, inp.W, 4, device="cuda")
+    ep.epbr_shade(d["gb"], d["cam"], d["lights"], ibl, sp, ref)
+    torch.cuda.synchronize()
+    assert ep.epbr_shade_light_timeouts() == 0
+    out = torch.zeros(inp.H, inp.W, 4, device="cuda")
+    prev = ep.epbr_ssao_set_tile_wait(0)
+    try:
+        ep.epbr_shade(d["gb"], d["cam"], d["lights"], ibl, sp, out)
+        torch.cuda.synchronize()
+    finally:
+        assert ep.epbr_ssao_set_tile_wait(prev) == 0
+    assert ep.epbr_shade_light_timeouts() == ((inp.W + 31) // 32) * ((inp.H + 15) // 16)
+    assert torch.equal(out, ref)
+    ep.epbr_shade(d["gb"], d["cam"], d["lights"], ibl, sp, out)
+    torch.cuda.synchronize()
+    assert ep.epbr_shade_light_timeouts() == 0 and torch.equal(out, ref)
