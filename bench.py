@@ -148,7 +148,8 @@ FLOP_SHADOW = 40         # lit pair with shadows: light-view transform (18), 1/z
 SHADOW = {"size": 512, "fov_deg": 90.0, "bias_const": 0.02, "bias_slope": 0.01}
 MESH = {"n_lat": 16, "n_lon": 32, "ground_cells": 64, "near": 0.05}
 RASTER_LAUNCHES = 7  # key reset, set-up, three scan kernels, coverage, resolve
-SHADOW_MAP_LAUNCHES = 6  # per light: set-up, three scan kernels, coverage, depth resolve (the key reset is a memset)
+SHADOW_MAP_LAUNCHES = 6  # per group of up to 8 lights: set-up, three scan kernels, coverage, depth resolve
+SHADOW_MAP_GROUP = 8     # (the key reset is a memset)
 SURFELS = {"per_sphere": 4000, "ground": 400000, "overlap": 1.2, "seed": 11, "near": 0.05, "tolerance": 0.01}
 SURFEL_LAUNCHES = 10  # depth and sum resets, pixel rays, set-up, three scan kernels, two coverage passes, resolve
 
@@ -576,7 +577,7 @@ def run_gpu(args):
         compose(gb, shp, hdr, ldr, lights, record)
 
     launches_per_step = 3 + (BLOOM_LAUNCHES if args.bloom else 0) + (RASTER_LAUNCHES if args.mesh else 0) + \
-        (SURFEL_LAUNCHES if args.surfels else 0) + (SHADOW_MAP_LAUNCHES * len(scams) if smaps_dev else 0)
+        (SURFEL_LAUNCHES if args.surfels else 0) + (SHADOW_MAP_LAUNCHES * -(-len(scams) // SHADOW_MAP_GROUP) if smaps_dev else 0)
     with torch.cuda.stream(stream):
         for _ in range(max(3, args.warmup)):
             step()
@@ -771,7 +772,7 @@ def run_gpu(args):
     if smaps_dev:
         line["shadow_maps"] = {"ms": statistics.mean(a.elapsed_time(b) for a, b in ev_smaps), "maps": len(scams),
                                "size": SHADOW["size"], "triangles": smesh.struct.num_triangles,
-                               "launches": SHADOW_MAP_LAUNCHES * len(scams)}
+                               "launches": SHADOW_MAP_LAUNCHES * -(-len(scams) // SHADOW_MAP_GROUP)}
     if args.surfels:
         line["surfels"] = {"ms": statistics.mean(a.elapsed_time(b) for a, b in ev_raster), "surfels": len(srec),
                            "launches": SURFEL_LAUNCHES, **SURFELS}

@@ -394,8 +394,9 @@ epbr_status epbr_raster_gbuffer(const epbr_mesh* mesh, const epbr_camera* camera
                                 const epbr_gbuffer* out, int32_t* ids, int64_t ids_pitch, void* workspace,
                                 size_t workspace_bytes, void* stream);
 
-/* Device workspace epbr_shadow_maps needs for maps of size x size texels (one light's key image
- * and triangle set-up, reused light after light). */
+/* Device workspace epbr_shadow_maps needs for maps of size x size texels: the key images and
+ * triangle set-ups of up to 8 lights at a time (8 x (8 B per texel + 88 B per triangle), about
+ * 160 MB for 512^2 maps of a 200,000-triangle mesh), reused group after group. */
 epbr_status epbr_shadow_maps_workspace_size(int32_t num_triangles, int32_t size, size_t* bytes);
 
 /* Shadow maps by rendering the mesh "only as a depth map" from each light as from a normal
@@ -404,9 +405,11 @@ epbr_status epbr_shadow_maps_workspace_size(int32_t num_triangles, int32_t size,
  * writes for that camera (same coverage, depth and tie rules; +inf where nothing is drawn).
  * `maps` is DEVICE float[num_maps][S][S] (dense rows), the layout epbr_shadows.maps takes; the
  * cameras are host structs (the world -> light-view rows epbr_shadows.cameras holds for shading
- * are the inverse of each camera's view_to_world).  The lights are rendered one after the other
- * through `workspace` (DEVICE, 256-byte aligned, epbr_shadow_maps_workspace_size bytes), stream-
- * ordered; no allocation.  Re-render when the scene or a light moves. */
+ * are the inverse of each camera's view_to_world).  Up to 8 lights are rendered by one set of
+ * launches (set-up, scan, coverage, depth), groups one after the other through `workspace`
+ * (DEVICE, 256-byte aligned, epbr_shadow_maps_workspace_size bytes), stream-ordered; no
+ * allocation.  EPBR_ERR_UNSUPPORTED above 2^28 triangles.  Re-render when the scene or a light
+ * moves. */
 epbr_status epbr_shadow_maps(const epbr_mesh* mesh, const epbr_camera* cameras, int32_t num_maps,
                              float near_depth, float* maps, void* workspace, size_t workspace_bytes, void* stream);
 

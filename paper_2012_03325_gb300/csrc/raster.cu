@@ -19,6 +19,7 @@
 // pixel is reproducible bit for bit.
 #include <string.h>
 
+#include <algorithm>
 #include <cmath>
 
 #include "epbr_internal.cuh"
@@ -41,6 +42,13 @@ struct RasterCam {
   float eye[3];
   float kx, ky, hw, hh, near;
   int W, H;
+};
+
+// The cameras of a group of views rendered by one set of launches (the lights' shadow maps);
+// a single view uses c[0].
+constexpr int kMaxViews = 8;
+struct RasterCams {
+  RasterCam c[kMaxViews];
 };
 
 struct RVert {
@@ -79,11 +87,15 @@ __device__ __forceinline__ int edge_excl(int ax, int ay, int bx, int by) {
   return (dy < 0 || (dy == 0 && dx > 0)) ? 0 : 1;
 }
 
+// blockIdx.y = the view: its set-ups and counts follow the previous views' (entry view * T + t).
 __global__ void __launch_bounds__(256) k_raster_setup(const float* __restrict__ verts, int V, const int* __restrict__ tris,
-                                                      int T, RasterCam cam, TriSetup* __restrict__ setup,
-                                                      long long* __restrict__ counts) {
+                                                      int T, const __grid_constant__ RasterCams cams,
+                                                      TriSetup* __restrict__ setup, long long* __restrict__ counts) {
   int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= T) return;
+  const RasterCam& cam = cams.c[blockIdx.y];
+  setup += (size_t)blockIdx.y * T;
+  counts += (size_t)blockIdx.y * T;
   int i[3] = {__ldg(tris + 3 * (size_t)t), __ldg(tris + 3 * (size_t)t + 1), __ldg(tris + 3 * (size_t)t + 2)};
   long long cnt = 0;
   TriSetup s;
@@ -212,9 +224,12 @@ constexpr int kCoverThreads = 256;
 // Threads take runs of 8 consecutive items: a binary search for the first item's triangle, then a
 // walk along the box rows and on to the next triangles (each found by a binary search as well:
 // a view that culls most triangles leaves long stretches of empty ones between two with items).
+// T set-ups of views of Tv triangles each (set-up t: view t / Tv, triangle t % Tv); view v's keys
+// start at keys + v * view_px.
 __global__ void __launch_bounds__(kCoverThreads) k_raster_cover(const TriSetup* __restrict__ setup,
                                                                 const long long* __restrict__ offsets, int T,
-                                                                const long long* __restrict__ total_p, int W,
+                                                                const long long* __restrict__ total_p, int W, int Tv,
+                                                                long long view_px,
                                                                 unsigned long long* __restrict__ keys) {
   const long long total = *total_p;
   const long long runs = (total + kRunItems - 1) / kRunItems;
@@ -286,8 +301,9 @@ __global__ void __launch_bounds__(kCoverThreads) k_raster_cover(const TriSetup* 
       float s0 = __fmul_rn(__ll2float_rn(wa), s.iz.x), s1 = __fmul_rn(__ll2float_rn(wb), s.iz.y);
       float s2 = __fmul_rn(__ll2float_rn(wc), s.iz.z);
       float z = __fdiv_rn(s.iz.w, __fadd_rn(__fadd_rn(s0, s1), s2));
-      unsigned long long key = ((unsigned long long)__float_as_uint(z) << 32) | (unsigned)t;
-      atomicMin(keys + (size_t)y * W + x, key);
+      const int v = t / Tv, tri = t - v * Tv;
+      unsigned long long key = ((unsigned long long)__float_as_uint(z) << 32) | (unsigned)tri;
+      atomicMin(keys + (size_t)v * view_px + (size_t)y * W + x, key);
     }
   }
 }
@@ -353,6 +369,8 @@ __global__ void __launch_bounds__(256) k_raster_depth(const unsigned long long* 
                                                       float* __restrict__ out, long long pitch) {
   int x = blockIdx.x * 32 + threadIdx.x, y = blockIdx.y * 8 + threadIdx.y;
   if (x >= W || y >= H) return;
+  keys += (size_t)blockIdx.z * W * H;  // view blockIdx.z: dense W x H images
+  out = (float*)((char*)out + (size_t)blockIdx.z * H * pitch);
   const unsigned long long key = keys[(size_t)y * W + x];
   ((float*)((char*)out + (size_t)y * pitch))[x] =
       key == ~0ULL ? __int_as_float(0x7f800000) : __uint_as_float((unsigned)(key >> 32));
@@ -364,17 +382,19 @@ struct RasterLayout {
   size_t keys, setup, offsets, sums, bytes;
 };
 
-static RasterLayout raster_layout(long long T, int W, int H) {
+// The workspace of `views` views of W x H pixels and T triangles each.
+static RasterLayout raster_layout(long long T, int W, int H, int views = 1) {
   RasterLayout l;
   size_t off = 0;
+  const long long n = T * views;
   l.keys = off;
-  off = align256(off + sizeof(unsigned long long) * (size_t)W * H);
+  off = align256(off + sizeof(unsigned long long) * (size_t)W * H * views);
   l.setup = off;
-  off = align256(off + sizeof(TriSetup) * (size_t)T);
+  off = align256(off + sizeof(TriSetup) * (size_t)n);
   l.offsets = off;
-  off = align256(off + sizeof(long long) * (size_t)(T + 1));
+  off = align256(off + sizeof(long long) * (size_t)(n + 1));
   l.sums = off;
-  long long nb = scan_num_blocks(T);
+  long long nb = scan_num_blocks(n);
   off = align256(off + sizeof(long long) * (size_t)(nb + 1));
   l.bytes = off;
   return l;
@@ -419,23 +439,26 @@ static RasterCam make_raster_cam(const epbr_camera& camera, float near_depth) {
   return rc;
 }
 
-// Set-up, scan and coverage of the mesh seen by `rc`: the nearest (depth, triangle) key of
-// every pixel in the workspace's key image.
-static epbr_status raster_keys(const epbr_mesh* mesh, const RasterCam& rc, const RasterLayout& l, char* ws,
-                               cudaStream_t s) {
+// Set-up, scan and coverage of the mesh seen by `views` cameras (same size): the nearest (depth,
+// triangle) key of every pixel of every view in the workspace's key images.
+static epbr_status raster_keys(const epbr_mesh* mesh, const RasterCams& rc, int views, const RasterLayout& l,
+                               char* ws, cudaStream_t s) {
   const int T = mesh->num_triangles;
+  const int W = rc.c[0].W, H = rc.c[0].H;
   unsigned long long* keys = (unsigned long long*)(ws + l.keys);
   TriSetup* setup = (TriSetup*)(ws + l.setup);
   long long* offsets = (long long*)(ws + l.offsets);
   long long* sums = (long long*)(ws + l.sums);
-  if (cudaMemsetAsync(keys, 0xff, sizeof(unsigned long long) * (size_t)rc.W * rc.H, s) != cudaSuccess)
+  if (cudaMemsetAsync(keys, 0xff, sizeof(unsigned long long) * (size_t)W * H * views, s) != cudaSuccess)
     return fail(EPBR_ERR_CUDA, "raster: memset failed");
   if (T > 0) {
-    k_raster_setup<<<(T + 255) / 256, 256, 0, s>>>(mesh->vertices, mesh->num_vertices, mesh->triangles, T, rc, setup,
-                                                   offsets);
-    const long long nb = scan_num_blocks(T);
-    launch_exclusive_scan(offsets, T, sums, s);
-    k_raster_cover<<<num_sms() * 8, kCoverThreads, 0, s>>>(setup, offsets, T, sums + nb, rc.W, keys);
+    const long long n = (long long)T * views;
+    k_raster_setup<<<dim3((T + 255) / 256, views), 256, 0, s>>>(mesh->vertices, mesh->num_vertices, mesh->triangles,
+                                                                T, rc, setup, offsets);
+    const long long nb = scan_num_blocks(n);
+    launch_exclusive_scan(offsets, n, sums, s);
+    k_raster_cover<<<num_sms() * 8, kCoverThreads, 0, s>>>(setup, offsets, (int)n, sums + nb, W, T, (long long)W * H,
+                                                          keys);
   }
   return EPBR_OK;
 }
@@ -459,7 +482,9 @@ extern "C" epbr_status epbr_raster_gbuffer(const epbr_mesh* mesh, const epbr_cam
     return fail(EPBR_ERR_INVALID_ARG, "raster: workspace NULL, not 256-byte aligned or below %zu bytes", l.bytes);
   char* ws = (char*)workspace;
   cudaStream_t s = (cudaStream_t)stream;
-  if ((st = raster_keys(mesh, make_raster_cam(*camera, near_depth), l, ws, s))) return st;
+  RasterCams rc;
+  rc.c[0] = make_raster_cam(*camera, near_depth);
+  if ((st = raster_keys(mesh, rc, 1, l, ws, s))) return st;
   GbufDev gd = make_gbuf(*out);
   dim3 blk(32, 8), grd((W + 31) / 32, (H + 7) / 8);
   k_raster_resolve<<<grd, blk, 0, s>>>(mesh->vertices, (const TriSetup*)(ws + l.setup),
@@ -469,7 +494,10 @@ extern "C" epbr_status epbr_raster_gbuffer(const epbr_mesh* mesh, const epbr_cam
 }
 
 extern "C" epbr_status epbr_shadow_maps_workspace_size(int32_t num_triangles, int32_t size, size_t* bytes) {
-  return epbr_raster_workspace_size(num_triangles, size, size, bytes);
+  if (!bytes || num_triangles < 0 || size < 1 || size > (1 << 15))
+    return fail(EPBR_ERR_INVALID_ARG, "shadow_maps: bytes NULL, num_triangles < 0 or size outside [1, 32768]");
+  *bytes = raster_layout(num_triangles, size, size, kMaxViews).bytes;
+  return ok();
 }
 
 extern "C" epbr_status epbr_shadow_maps(const epbr_mesh* mesh, const epbr_camera* cameras, int32_t num_maps,
@@ -489,15 +517,23 @@ extern "C" epbr_status epbr_shadow_maps(const epbr_mesh* mesh, const epbr_camera
     for (int k = 0; k < 16; ++k)
       if (!std::isfinite(c.view_to_world[k])) return fail(EPBR_ERR_INVALID_ARG, "shadow_maps: camera %d not finite", i);
   }
-  RasterLayout l = raster_layout(mesh->num_triangles, S, S);
-  if (!workspace || (uintptr_t)workspace % 256 || workspace_bytes < l.bytes)
-    return fail(EPBR_ERR_INVALID_ARG, "shadow_maps: workspace NULL, not 256-byte aligned or below %zu bytes", l.bytes);
+  const long long T = mesh->num_triangles;
+  if (T * kMaxViews >= (1LL << 31))
+    return fail(EPBR_ERR_UNSUPPORTED, "shadow_maps: %lld triangles x %d views exceed 2^31 set-ups", T, kMaxViews);
+  const RasterLayout full = raster_layout(T, S, S, kMaxViews);
+  if (!workspace || (uintptr_t)workspace % 256 || workspace_bytes < full.bytes)
+    return fail(EPBR_ERR_INVALID_ARG, "shadow_maps: workspace NULL, not 256-byte aligned or below %zu bytes",
+                full.bytes);
   char* ws = (char*)workspace;
   cudaStream_t s = (cudaStream_t)stream;
-  dim3 blk(32, 8), grd((S + 31) / 32, (S + 7) / 8);
-  for (int i = 0; i < num_maps; ++i) {  // one light after the other through the same workspace (stream order)
-    if ((st = raster_keys(mesh, make_raster_cam(cameras[i], near_depth), l, ws, s))) return st;
-    k_raster_depth<<<grd, blk, 0, s>>>((const unsigned long long*)(ws + l.keys), S, S, maps + (size_t)i * S * S,
+  for (int i0 = 0; i0 < num_maps; i0 += kMaxViews) {  // up to kMaxViews lights per set of launches
+    const int views = std::min(kMaxViews, num_maps - i0);
+    const RasterLayout l = raster_layout(T, S, S, views);
+    RasterCams rc;
+    for (int v = 0; v < views; ++v) rc.c[v] = make_raster_cam(cameras[i0 + v], near_depth);
+    if ((st = raster_keys(mesh, rc, views, l, ws, s))) return st;
+    dim3 blk(32, 8), grd((S + 31) / 32, (S + 7) / 8, views);
+    k_raster_depth<<<grd, blk, 0, s>>>((const unsigned long long*)(ws + l.keys), S, S, maps + (size_t)i0 * S * S,
                                        4LL * S);
   }
   if ((st = check_launch("shadow_maps"))) return st;

@@ -172,10 +172,11 @@ def _device_maps(mesh, ep_cams, S):
     return maps
 
 
-@pytest.mark.parametrize("S,lights", [(128, 4), (97, 3), (1, 2)])
+@pytest.mark.parametrize("S,lights", [(128, 4), (97, 3), (1, 2), (64, 11)])
 def test_device_shadow_maps_equal_the_oracle_raster(S, lights):
     """Each map is the depth plane of the mesh rendered from the light's camera: identical, bit for
-    bit, to the oracle's G-buffer pass (same coverage, depth and tie rules), +inf where empty."""
+    bit, to the oracle's G-buffer pass (same coverage, depth and tie rules), +inf where empty.
+    Eleven lights take two groups of launches (eight lights per group)."""
     inp = make_inputs("small", W=64, H=48, lights=lights)
     verts, tris = synth.make_mesh_scene(inp.scene, 10, 20, 12)
     mesh = ep.Mesh(torch.from_numpy(verts).cuda(), torch.from_numpy(tris).cuda())
