@@ -142,8 +142,11 @@ __device__ __forceinline__ float2 ssao_samples(const SsaoRows& a, const SsaoRows
     const float2 fx = __ffma2_rn(X, inv, hw), fy = __ffma2_rn(Y, inv, hh);
     const unsigned ix0 = floor_px(fx.x), iy0 = floor_px(fy.x);
     const unsigned ix1 = floor_px(fx.y), iy1 = floor_px(fy.y);
-    const bool v0 = Z.x > 0.0f && ix0 < W && iy0 < H;
-    const bool v1 = Z.y > 0.0f && ix1 < W && iy1 < H;
+    // From the tile no test is needed: a tap outside the image reads the zeros the copy filled in
+    // (0 never passes eb > 0), and a warp reads the tile only when its samples lie in front of
+    // the camera (were Z <= 0 after rounding, Z - bias < 0 <= eb would reject the tap anyway).
+    const bool v0 = FROM_TILE || (Z.x > 0.0f && ix0 < W && iy0 < H);
+    const bool v1 = FROM_TILE || (Z.y > 0.0f && ix1 < W && iy1 < H);
     float eb0, eb1;
     if (FROM_TILE) {
       eb0 = s_dep[min(iy0 * (unsigned)kSsaoTileW + ix0 - tbase, kSsaoTileN - 1)];
