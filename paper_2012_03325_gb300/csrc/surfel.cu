@@ -3,8 +3,8 @@
 //   k_surfel_rays     the view-space ray (u_x, u_y, -1) of every pixel column and row
 //   k_surfel_setup    one thread per surfel: view-space frame (centre, unit normal, orthogonalised
 //                     unit tangent, bitangent), the near rule, and the pixel box of the projected
-//                     rectangle widened by a pixel; a box of more than 1024 pixels counts as
-//                     tasks of 1024 pixels (0 tasks for the others)
+//                     ellipse (its image conic's extent, widened by 1/8 pixel); a box of more
+//                     than 1024 pixels counts as tasks of 1024 pixels (0 tasks for the others)
 //   k_surfel_cover    one warp per surfel with a box of at most 1024 pixels, then one warp per
 //                     task of the larger boxes (a binary search over the scanned task counts finds
 //                     its surfel), the lanes walking the pixels in row order: the ellipse test
@@ -90,19 +90,46 @@ __global__ void __launch_bounds__(256) k_surfel_setup(const float4* __restrict__
   const float b2 = __fsub_rn(__fmul_rn(n0, t1), __fmul_rn(n1, t0));
   ok = ok && __fsub_rn(-c[2], __fadd_rn(a, b)) >= cam.near;
   if (ok) {
-    // pixel box of the rectangle c +- a t^ +- b b^ (every corner at eye depth >= near), widened by
-    // a pixel so that it holds every pixel the rounded ellipse test can accept
-    float xmin = inf, xmax = -inf, ymin = inf, ymax = -inf;
+    // Pixel box of the projected ellipse (the whole disk lies at eye depth >= near).  With
+    // G = [a t^, b b^, c] the disk's boundary is G (cos, sin, 1); M maps view space to
+    // homogeneous pixel coordinates taken relative to the projected centre (Xc, Yc), so
+    // H = M G maps the unit circle onto the image conic, whose tangent lines l satisfy
+    // l^T H D H^T l = 0 with D = diag(1, 1, -1).  The lines X' = x are l = (1, 0, -x): the
+    // silhouette's extent along x is the two roots of C00 - 2 x C02 + x^2 C22 = 0 (C = H D H^T),
+    // likewise along y.  The box holds every pixel whose centre lies within 1/8 pixel (plus 1e-4
+    // of the extent) of that range: FP32 errors of these bounds are below 1e-3 pixel, and pixels
+    // that the rounded ellipse test accepts lie within ~1e-6 of the ellipse's size of it.
+    const float ec = -c[2];
+    const float Xc = cam.hw * (1.0f + cam.kx * c[0] / ec), Yc = cam.hh * (1.0f - cam.ky * c[1] / ec);
+    const float g0[3] = {a * t0, b * b0, c[0]}, g1[3] = {a * t1, b * b1, c[1]}, g2[3] = {a * t2, b * b2, c[2]};
+    float h0[3], h1[3], h2[3];
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const float sa = (q & 1) ? a : -a, sb = (q & 2) ? b : -b;
-      const float x = c[0] + sa * t0 + sb * b0, y = c[1] + sa * t1 + sb * b1, e = -(c[2] + sa * t2 + sb * b2);
-      const float X = cam.hw * (1.0f + x / e * cam.kx), Y = cam.hh * (1.0f - y / e * cam.ky);
-      xmin = fminf(xmin, X), xmax = fmaxf(xmax, X), ymin = fminf(ymin, Y), ymax = fmaxf(ymax, Y);
+    for (int k = 0; k < 3; ++k) {
+      h0[k] = cam.hw * cam.kx * g0[k] + (Xc - cam.hw) * g2[k];
+      h1[k] = -cam.hh * cam.ky * g1[k] + (Yc - cam.hh) * g2[k];
+      h2[k] = -g2[k];
     }
-    const float fx0 = fmaxf(floorf(xmin - 0.5f) - 1.0f, 0.0f), fy0 = fmaxf(floorf(ymin - 0.5f) - 1.0f, 0.0f);
-    const float fx1 = fminf(ceilf(xmax - 0.5f) + 1.0f, (float)(cam.W - 1));
-    const float fy1 = fminf(ceilf(ymax - 0.5f) + 1.0f, (float)(cam.H - 1));
+    auto dd = [](const float* u, const float* v) { return u[0] * v[0] + u[1] * v[1] - u[2] * v[2]; };
+    const float C22 = dd(h2, h2);  // a^2 t_z^2 + b^2 b_z^2 - e_c^2 < 0 for a disk in front of the eye
+    float lo[2], hi[2];
+    const float* hr[2] = {h0, h1};
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      const float C00 = dd(hr[q], hr[q]), C02 = dd(hr[q], h2);
+      const float sq = sqrtf(fmaxf(C02 * C02 - C00 * C22, 0.0f));
+      const float r0 = (C02 + sq) / C22, r1 = (C02 - sq) / C22;
+      const float m = 0.125f + 1e-4f * fabsf(r1 - r0);
+      lo[q] = fminf(r0, r1) - m;
+      hi[q] = fmaxf(r0, r1) + m;
+    }
+    float fx0 = fmaxf(ceilf(Xc + lo[0] - 0.5f), 0.0f), fy0 = fmaxf(ceilf(Yc + lo[1] - 0.5f), 0.0f);
+    float fx1 = fminf(floorf(Xc + hi[0] - 0.5f), (float)(cam.W - 1));
+    float fy1 = fminf(floorf(Yc + hi[1] - 0.5f), (float)(cam.H - 1));
+    if (!(C22 < 0.0f)) {  // a disk grazing the eye plane (rounding only): the whole view
+      fx0 = fy0 = 0.0f;
+      fx1 = (float)(cam.W - 1);
+      fy1 = (float)(cam.H - 1);
+    }
     if (fx1 >= fx0 && fy1 >= fy0) {  // false for a NaN bound as well
       const int x0 = (int)fx0, y0 = (int)fy0, w = (int)fx1 - x0 + 1, h = (int)fy1 - y0 + 1;
       const long long area = (long long)w * h;

@@ -127,3 +127,45 @@ def test_invalid_surfel_arguments():
         ep.epbr_surfel_gbuffer(s, ep.camera(sc.camera_array(), sc.fov_y, 33, 16), NEAR, 0.01, gb)
     with pytest.raises(ValueError):
         ep.Surfels(rec[:, :12].contiguous())
+
+
+@pytest.mark.parametrize("seed", [21, 22])
+def test_oblique_near_and_large_surfels(seed):
+    """Disks of every orientation (a fifth of them within a few degrees of edge-on), sizes from a
+    fraction of a pixel to much of the view, and depths down to the near rule.  The device searches
+    each disk's pixel box taken from its image conic; the oracle searches the wider box of the
+    projected rectangle, so any accepted pixel outside the device's box would show as a coverage
+    or depth difference."""
+    W, H = 160, 96
+    inp = make_inputs("small", W=W, H=H)
+    sc = inp.scene
+    rng = np.random.default_rng(seed)
+    R = sc.view_to_world[:3, :3]
+    eye = sc.view_to_world[:3, 3]
+    N = 4000
+    e = np.exp(rng.uniform(np.log(NEAR + 0.02), np.log(12.0), N))
+    th = math.tan(0.5 * sc.fov_y)
+    cv = np.stack([rng.uniform(-1.2, 1.2, N) * th * W / H * e, rng.uniform(-1.2, 1.2, N) * th * e, -e], 1)
+    size = np.exp(rng.uniform(np.log(0.002), np.log(0.8), N)) * e
+    a = np.minimum(size, 0.49 * (e - NEAR))
+    b = a * rng.uniform(0.3, 1.0, N)
+    n = rng.normal(size=(N, 3))
+    n /= np.linalg.norm(n, axis=1, keepdims=True)
+    edge = rng.random(N) < 0.2  # nearly edge-on: the normal almost perpendicular to the view ray
+    ray = cv / np.linalg.norm(cv, axis=1, keepdims=True)
+    n[edge] -= ray[edge] * np.sum(n[edge] * ray[edge], 1, keepdims=True)
+    n[edge] += ray[edge] * rng.uniform(-0.05, 0.05, (int(edge.sum()), 1))
+    n /= np.linalg.norm(n, axis=1, keepdims=True)
+    t = rng.normal(size=(N, 3))
+    t -= n * np.sum(t * n, 1, keepdims=True)
+    t /= np.linalg.norm(t, axis=1, keepdims=True)
+    rec = np.zeros((N, 16))
+    rec[:, 0:3] = eye + cv @ R.T
+    rec[:, 3], rec[:, 7] = a, b
+    rec[:, 4:7] = n @ R.T
+    rec[:, 8:11] = t @ R.T
+    rec[:, 11] = rng.uniform(0, 1, N)
+    rec[:, 12:15] = rng.uniform(0, 1, (N, 3))
+    rec[:, 15] = rng.uniform(0.05, 1, N)
+    covered = check(*splat_both(sc, W, H, rec.astype(np.float32)))
+    assert covered > 0.3
