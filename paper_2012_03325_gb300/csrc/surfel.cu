@@ -207,12 +207,27 @@ __global__ void __launch_bounds__(256) k_surfel_cover(const SurfelSetup* __restr
   const int lane = threadIdx.x & 31;
   const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const long long warps = ((long long)gridDim.x * blockDim.x) >> 5;
-  for (long long i = warp; i < N; i += warps) {  // boxes of at most kSurfelChunk pixels: one warp each
-    const SurfelSetup s = setup[i];
+  // boxes of at most kSurfelChunk pixels: one warp each, the next surfel's set-up loaded while the
+  // current one's pixels are tested
+  // (pass 1: and its material from the records)
+  SurfelSetup next;
+  float4 next_mat = make_float4(0, 0, 0, 0);
+  float next_metal = 0.0f;
+  if (warp < N) {
+    next = setup[warp];
+    if (PASS == 1) next_mat = __ldg(rec + 4 * (size_t)warp + 3), next_metal = __ldg(rec + 4 * (size_t)warp + 2).w;
+  }
+  for (long long i = warp; i < N; i += warps) {
+    const SurfelSetup s = next;
+    const float4 mat = next_mat;
+    const float metal = next_metal;
+    if (i + warps < N) {
+      next = setup[i + warps];
+      if (PASS == 1)
+        next_mat = __ldg(rec + 4 * (size_t)(i + warps) + 3), next_metal = __ldg(rec + 4 * (size_t)(i + warps) + 2).w;
+    }
     const int area = s.box.z * s.box.w;
     if (area == 0 || area > kSurfelChunk) continue;
-    const float4 mat = PASS == 1 ? __ldg(rec + 4 * (size_t)i + 3) : make_float4(0, 0, 0, 0);
-    const float metal = PASS == 1 ? __ldg(rec + 4 * (size_t)i + 2).w : 0.0f;
     surfel_pixels<PASS>(s, mat, metal, 0, area, lane, ux, uy, f, W, depth, acc_a, acc_b, acc_w);
   }
   const long long total = *total_p;  // tasks of the larger boxes
