@@ -80,7 +80,10 @@ struct CamDev {
   float r[9];   // view_to_world rotation, r[3*i + j] = row i, column j
   float eye[3];
   float sx, sy;  // px = (2 (x + 0.5) / W - 1) * sx, py = (1 - 2 (y + 0.5) / H) * sy
-  float ax, bx, ay, by;  // the same as px = ax x + bx, py = ay y + by (coefficients in FP64)
+  // the same as px = (x + cx) ax, py = (y + cy) ay with cx = 1/2 - W/2, cy = 1/2 - H/2: x + cx is
+  // exact in FP32 (a multiple of 1/2 below 2^15), so px has one rounding of the product however
+  // far from the centre the image reaches (ax, ay rounded from FP64)
+  float ax, cx, ay, cy;
   float ix_scale, iy_scale;  // view -> pixel: x = 0.5 W (1 + px / sx), y = 0.5 H (1 - py / sy)
   int W, H;
 };
@@ -97,9 +100,9 @@ __host__ inline CamDev make_cam(const epbr_camera& c) {
   d.sy = (float)t;
   d.sx = (float)sx;
   d.ax = (float)(2.0 * sx / c.width);
-  d.bx = (float)(sx * (1.0 / c.width - 1.0));
+  d.cx = (float)(0.5 - 0.5 * c.width);
   d.ay = (float)(-2.0 * t / c.height);
-  d.by = (float)(t * (1.0 - 1.0 / c.height));
+  d.cy = (float)(0.5 - 0.5 * c.height);
   d.ix_scale = (float)(0.5 * c.width / sx);
   d.iy_scale = (float)(0.5 * c.height / t);
   d.W = c.width;
@@ -109,7 +112,7 @@ __host__ inline CamDev make_cam(const epbr_camera& c) {
 
 // View-space ray (px, py, -1) of the centre of pixel (x, y).
 __device__ __forceinline__ float3 view_ray(const CamDev& c, int x, int y) {
-  return f3(fmaf((float)x, c.ax, c.bx), fmaf((float)y, c.ay, c.by), -1.0f);
+  return f3(((float)x + c.cx) * c.ax, ((float)y + c.cy) * c.ay, -1.0f);
 }
 __device__ __forceinline__ float3 rot(const CamDev& c, float3 a) {
   return f3(fmaf(c.r[0], a.x, fmaf(c.r[1], a.y, c.r[2] * a.z)),

@@ -138,3 +138,31 @@ def test_batch_largest_blur_and_sample_count():
                 assert (np.abs(g - r) / np.maximum(np.abs(r), 1e-6)).max() <= 1e-6, md
     finally:
         b.close()
+
+
+@pytest.mark.parametrize("W,H", [(32768, 8), (8, 32768)])
+def test_frame_at_the_largest_view_dimension(W, H):
+    """Views 32768 pixels wide or tall (the ABI's limit): SSAO (the tiled form for the wide view,
+    the untiled one for the tall view) and the fused compose against the oracle, every pixel."""
+    inp = make_inputs("small", W=W, H=H)
+    d = gpu_inputs(inp)
+    p = ep.SsaoParams(d["kernel"], d["noise"], radius=0.5, scale=2, blur_radius=3)
+    assert ep.epbr_ssao_tiled(d["gb"], p) == (H <= 1536)
+    Ha, Wa = p.ao_shape(W, H)
+    ao = torch.full((Ha, Wa), -1.0, device="cuda")
+    ep.epbr_ssao(d["gb"], d["cam"], p, ao)
+    gb = decoded(inp)
+    cam = oracle_camera(inp)
+    a, lo, hi = oracle.ssao(gb, cam, K=inp.cfg["ssao_k"], scale=2, radius=0.5, bias=0.025, blur_radius=3,
+                            sigma_s=2.0, sigma_z=0.1, kernel=inp.kernel, noise=inp.noise, blurred=True)
+    ao_np = np_(ao)
+    assert ao_tie_check(ao_np, a, lo, hi) > 0.5
+    ibl = gpu_ibl(inp, d["env"])
+    hdr = torch.zeros(H, W, 4, device="cuda")
+    ldr = torch.zeros(H, W, 4, dtype=torch.uint8, device="cuda")
+    ep.epbr_shade_tonemap(d["gb"], d["cam"], d["lights"], ibl, ep.shade_params(ep.EPBR_SHADE_ALL, ao, 2), hdr,
+                          ep.EPBR_HDR_RGBA32F, ep.tonemap_params(), ldr)
+    ref = oracle.shade(gb, cam, inp.lights, oracle_ibl(inp), ep.EPBR_SHADE_ALL, ao=ao_np.astype(np.float64), ao_scale=2)
+    check_hdr(np_(hdr)[..., :3], ref, REL_TOL_FP32, gb=gb, cam=cam, lights=inp.lights, ibl=oracle_ibl(inp),
+              flags=ep.EPBR_SHADE_ALL, ao=ao_np.astype(np.float64), ao_scale=2)
+    assert (gb[..., 8] < np.inf).sum() > 200  # geometry in view (a 32768 x 8 strip sees ~180 degrees across)
