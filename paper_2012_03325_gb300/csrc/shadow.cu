@@ -78,10 +78,31 @@ __global__ void __launch_bounds__(256, 4)
   for (int base = 0; base < NL; base += kShadowChunk) {
     const int cnt = min(kShadowChunk, NL - base);
     __syncthreads();  // the previous chunk has been read
-    stage_lights(s_lights, lights, base, cnt, tid, 256);
     for (int q = tid; q < 4 * cnt; q += 256) s_cams[q] = __ldg(sh.cams + 4 * (size_t)base + q);
-    __syncthreads();
+    // a chunk of monochrome lights keeps one sum per kind (each channel's sum would be the same)
+    const bool mono = __syncthreads_and(stage_lights(s_lights, lights, base, cnt, tid, 256));
     if (!active) continue;
+    if (mono && !diffuse_only) {
+      float sa = 0.0f, sb = 0.0f, sbf = 0.0f;
+      for (int i = 0; i < cnt; ++i) {
+        const float4 lp = s_lights[2 * i];
+        LightTerms t = light_terms(s, d, lp);
+        if (t.a > 0.0f || t.b > 0.0f) {
+          const float v = shadow_visibility(s_cams + 4 * i, s.P, sh.maps + (size_t)(base + i) * sh.map_texels, sh.S,
+                                            sh.b0, sh.b1);
+          t.a *= v;
+          t.b *= v;
+          t.bf *= v;
+        }
+        sa = sa + lp.w * t.a;  // lp.w: the light's Ic
+        sb = sb + lp.w * t.b;
+        sbf = sbf + lp.w * t.bf;
+      }
+      d.sa = d.sa + f3(sa, sa, sa);
+      d.sb = d.sb + f3(sb, sb, sb);
+      d.sbf = d.sbf + f3(sbf, sbf, sbf);
+      continue;
+    }
     float3 sa = d.sa, sb = d.sb, sbf = d.sbf;
     for (int i = 0; i < cnt; ++i) {
       float4 lp = s_lights[2 * i], lc = s_lights[2 * i + 1];
