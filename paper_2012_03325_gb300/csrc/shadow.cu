@@ -36,14 +36,22 @@ __device__ __forceinline__ float shadow_visibility(const float4* cam, float3 P, 
   if (!(fabsf(s) < 1e9f && fabsf(t) < 1e9f)) return 1.0f;  // far outside the frustum
   int i0 = __float2int_rd(s), j0 = __float2int_rd(t);
   float thr = fmaf(-b1, z, z) - b0;  // lit when d >= z - b1 z - b0
-  int lit = 0;
-  if (i0 >= 1 && i0 < S - 1 && j0 >= 1 && j0 < S - 1) {  // the whole block inside: no per-tap bounds
-    const float* p0 = map + (size_t)(j0 - 1) * S + (i0 - 1);
+  // the whole block inside (1 <= i0, j0 < S - 1, one unsigned compare each; none for S <= 2): no
+  // per-tap bounds
+  const unsigned inner = (unsigned)max(S - 2, 0);
+  if ((unsigned)(i0 - 1) < inner && (unsigned)(j0 - 1) < inner) {
+    // the lit taps counted in FP32 (sums of 0 and 1, exact): a compare-and-set and an add per tap
+    // in the FMA pipe, which this kernel leaves less busy than the integer pipe; the offset within
+    // the map fits 32 bits (S <= 8192)
+    const float* p0 = map + ((j0 - 1) * S + (i0 - 1));
+    float lit = 0.0f;
 #pragma unroll
     for (int dy = 0; dy < 3; ++dy, p0 += S)
-      lit += (int)(__ldg(p0) >= thr) + (int)(__ldg(p0 + 1) >= thr) + (int)(__ldg(p0 + 2) >= thr);
-    return (float)lit * (1.0f / 9.0f);
+      lit += ((__ldg(p0) >= thr) ? 1.0f : 0.0f) + ((__ldg(p0 + 1) >= thr) ? 1.0f : 0.0f) +
+             ((__ldg(p0 + 2) >= thr) ? 1.0f : 0.0f);
+    return lit * (1.0f / 9.0f);
   }
+  int lit = 0;
 #pragma unroll
   for (int dy = -1; dy <= 1; ++dy) {
     int j = j0 + dy;
@@ -84,12 +92,12 @@ __global__ void __launch_bounds__(256, 4)
     if (!active) continue;
     if (mono && !diffuse_only) {
       float sa = 0.0f, sb = 0.0f, sbf = 0.0f;
-      for (int i = 0; i < cnt; ++i) {
+      const float* map = sh.maps + (size_t)base * sh.map_texels;
+      for (int i = 0; i < cnt; ++i, map += sh.map_texels) {
         const float4 lp = s_lights[2 * i];
         LightTerms t = light_terms(s, d, lp);
         if (t.a > 0.0f || t.b > 0.0f) {
-          const float v = shadow_visibility(s_cams + 4 * i, s.P, sh.maps + (size_t)(base + i) * sh.map_texels, sh.S,
-                                            sh.b0, sh.b1);
+          const float v = shadow_visibility(s_cams + 4 * i, s.P, map, sh.S, sh.b0, sh.b1);
           t.a *= v;
           t.b *= v;
           t.bf *= v;

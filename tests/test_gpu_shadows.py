@@ -109,6 +109,17 @@ def test_mixed_monochrome_and_coloured_chunks_ragged_view(flags):
     assert (out < unlit - 1e-6).any()
 
 
+@pytest.mark.parametrize("S", [1, 2, 3])
+def test_tiny_maps(S):
+    """Maps of 1, 2 and 3 texels a side: no 3x3 block lies inside (S <= 2) or only the centre texel's
+    does (S = 3), so the per-tap bounds path decides nearly every tap."""
+    inp = make_inputs("small", W=64, H=40, lights=6)
+    maps, cams = synth.make_shadow_maps(inp.scene, S)
+    g, _ = run(inp, maps, cams, ep.EPBR_SHADE_ALL)
+    _, lo, hi = oracle_of(inp, maps, cams, ep.EPBR_SHADE_ALL)
+    check_bounds(g, lo, hi)
+
+
 def test_tonemapped_output_where_no_decision_is_tied():
     inp = make_inputs("small")
     maps, cams = synth.make_shadow_maps(inp.scene, 128)
