@@ -40,9 +40,9 @@ __device__ __forceinline__ float shadow_visibility(const float4* cam, float3 P, 
   // per-tap bounds
   const unsigned inner = (unsigned)max(S - 2, 0);
   if ((unsigned)(i0 - 1) < inner && (unsigned)(j0 - 1) < inner) {
-    // the lit taps counted in FP32 (sums of 0 and 1, exact): a compare-and-set and an add per tap
-    // in the FMA pipe, which this kernel leaves less busy than the integer pipe; the offset within
-    // the map fits 32 bits (S <= 8192)
+    // the lit taps counted in FP32 (sums of 0 and 1, exact): a compare-and-set and an FP32 add per
+    // tap instead of an integer select and add, fewer instructions for the integer pipe, the busier
+    // one in this kernel; the offset within the map fits 32 bits (S <= 8192)
     const float* p0 = map + ((j0 - 1) * S + (i0 - 1));
     float lit = 0.0f;
 #pragma unroll
