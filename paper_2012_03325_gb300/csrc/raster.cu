@@ -129,7 +129,10 @@ __global__ void __launch_bounds__(256) k_raster_setup(const float* __restrict__ 
       }
     }
   }
-  setup[t] = s;
+  // only triangles with work items are ever read back (the coverage finds a triangle through its
+  // non-empty item range, the resolves through a covered pixel's winner), so a culled one writes
+  // its count alone: no set-up traffic for the triangles a view does not see
+  if (cnt > 0) setup[t] = s;
   counts[t] = cnt;
 }
 
