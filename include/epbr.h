@@ -374,7 +374,7 @@ typedef struct epbr_mesh {
 } epbr_mesh;
 
 /* Device workspace epbr_raster_gbuffer needs: 8 B per pixel (nearest (depth, triangle) key),
- * 80 B and 8 B per triangle (set-up, item offsets), each part 256-byte aligned. */
+ * 64 B and 8 B per triangle (set-up, item offsets), each part 256-byte aligned. */
 epbr_status epbr_raster_workspace_size(int32_t num_triangles, int32_t width, int32_t height, size_t* bytes);
 
 /* Writes the FP32 G-buffer `out` (rt[0] albedo + metal, rt[1] normal + rough, rt[3] eye depth;
@@ -395,8 +395,8 @@ epbr_status epbr_raster_gbuffer(const epbr_mesh* mesh, const epbr_camera* camera
                                 size_t workspace_bytes, void* stream);
 
 /* Device workspace epbr_shadow_maps needs for maps of size x size texels: the key images and
- * triangle set-ups of up to 8 lights at a time (8 x (8 B per texel + 88 B per triangle), about
- * 160 MB for 512^2 maps of a 200,000-triangle mesh), reused group after group. */
+ * triangle set-ups of up to 8 lights at a time (8 x (8 B per texel + 72 B per triangle), about
+ * 130 MB for 512^2 maps of a 200,000-triangle mesh), reused group after group. */
 epbr_status epbr_shadow_maps_workspace_size(int32_t num_triangles, int32_t size, size_t* bytes);
 
 /* Shadow maps by rendering the mesh "only as a depth map" from each light as from a normal

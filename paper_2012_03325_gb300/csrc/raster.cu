@@ -29,13 +29,15 @@ namespace epbr {
 constexpr int kScanThreads = 256, kScanItems = 4, kScanBlock = kScanThreads * kScanItems;
 constexpr int kRunItems = 8;
 
+// 64 bytes, two 32-byte sectors for the coverage's read of a triangle
 struct TriSetup {
   int4 qab;    // snapped screen positions of a and b (1/256 px)
   int4 qc_xy;  // c, then the box origin x0, y0
-  int4 box;    // box width, height, then the vertex indices of a and b
-  int4 vc;     // vertex index of c, unused x3
   float4 iz;   // 1/z of a, b, c, then the area as a float
+  int4 meta;   // box width | height << 16 (each at most 32768), then the vertex indices of a, b, c
 };
+
+__device__ __forceinline__ int box_width(const TriSetup& s) { return s.meta.x & 0xffff; }
 
 struct RasterCam {
   float r[9];  // view_to_world rotation, row-major
@@ -123,8 +125,7 @@ __global__ void __launch_bounds__(256) k_raster_setup(const float* __restrict__ 
         cnt = (x1 - x0 + 1) * (y1 - y0 + 1);
         s.qab = make_int4(a.qx, a.qy, b.qx, b.qy);
         s.qc_xy = make_int4(c.qx, c.qy, (int)x0, (int)y0);
-        s.box = make_int4((int)(x1 - x0 + 1), (int)(y1 - y0 + 1), ia, ib);
-        s.vc = make_int4(ic, 0, 0, 0);
+        s.meta = make_int4((int)((x1 - x0 + 1) | ((y1 - y0 + 1) << 16)), ia, ib, ic);
         s.iz = make_float4(a.iz, b.iz, c.iz, __ll2float_rn(area));
       }
     }
@@ -275,8 +276,8 @@ __global__ void __launch_bounds__(kCoverThreads) k_raster_cover(const TriSetup* 
       }
       if (fresh) {  // position of this item in the triangle's box
         const long long local = item - t_begin;
-        ly = (int)(local / s.box.x);
-        lx = (int)(local - (long long)ly * s.box.x);
+        ly = (int)(local / box_width(s));
+        lx = (int)(local - (long long)ly * box_width(s));
         // E(p) = (b.x - a.x)(p.y - a.y) - (b.y - a.y)(p.x - a.x): a step of one pixel in x adds
         // -256 (b.y - a.y)
         dc = -256LL * (s.qab.w - s.qab.y);
@@ -295,7 +296,7 @@ __global__ void __launch_bounds__(kCoverThreads) k_raster_cover(const TriSetup* 
         wa += da;
         wb += db;
       }
-      if (++lx == s.box.x) lx = 0, ++ly;
+      if (++lx == box_width(s)) lx = 0, ++ly;
       if (wc < 0 || wa < 0 || wb < 0) continue;
       if ((wc == 0 && edge_excl(s.qab.x, s.qab.y, s.qab.z, s.qab.w)) ||
           (wa == 0 && edge_excl(s.qab.z, s.qab.w, s.qc_xy.x, s.qc_xy.y)) ||
@@ -344,9 +345,9 @@ __global__ void __launch_bounds__(256) k_raster_resolve(const float* __restrict_
   // vertex values 3 .. 10 (normal, albedo, metal, rough) read as three float4 of each 48-byte
   // record (16-byte aligned, checked on the host): normal.x is the w of the first, normal.yz and
   // albedo.rg fill the second, albedo.b, metal and rough lead the third
-  const float4* A = (const float4*)(verts + 12 * (size_t)s.box.z);
-  const float4* B = (const float4*)(verts + 12 * (size_t)s.box.w);
-  const float4* C = (const float4*)(verts + 12 * (size_t)s.vc.x);
+  const float4* A = (const float4*)(verts + 12 * (size_t)s.meta.y);
+  const float4* B = (const float4*)(verts + 12 * (size_t)s.meta.z);
+  const float4* C = (const float4*)(verts + 12 * (size_t)s.meta.w);
   float at[8];
   {
     const float4 a0 = __ldg(A), a1 = __ldg(A + 1), a2 = __ldg(A + 2);
