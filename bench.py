@@ -68,6 +68,9 @@ def parse():
                          "(the scene or a light moved)")
     ap.add_argument("--bloom", action="store_true",
                     help="add the bloom pass (Sec. 5.3) to the frame: shade to HDR, then bloom + tone map")
+    ap.add_argument("--no-early-start", action="store_true",
+                    help="launch the compose after the SSAO blur has finished (default: EPBR_SHADE_EARLY_START, "
+                         "the compose's light loop overlaps the blur)")
     return ap.parse_args()
 
 
@@ -483,7 +486,8 @@ def run_gpu(args):
     hdr_fmt = ep.EPBR_HDR_RGBA16F if compact else ep.EPBR_HDR_RGBA32F
     hdr = torch.empty(H, W, 4, dtype=torch.float16 if compact else torch.float32, device=dev)
     ldr = torch.empty(H, W, 4, dtype=torch.uint8, device=dev)
-    shp = ep.shade_params(ep.EPBR_SHADE_ALL, ao, 2)
+    shade_flags = ep.EPBR_SHADE_ALL | (0 if args.no_early_start else ep.EPBR_SHADE_EARLY_START)
+    shp = ep.shade_params(shade_flags, ao, 2)
     tp = ep.tonemap_params(1.0, ep.EPBR_TONEMAP_ACES)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
 
@@ -598,7 +602,7 @@ def run_gpu(args):
             for i in range(args.steps):
                 flush.zero_()  # L2 flush, outside the timed events
                 ev[i][0].record(stream)
-                step(record=True)
+                step()  # no events inside a step: one between the blur and the compose would end the overlap
                 ev[i][1].record(stream)
         stream.synchronize()
         torch.cuda.synchronize()
@@ -606,15 +610,16 @@ def run_gpu(args):
         clk.mark_end()
     step_ms = [a.elapsed_time(b) for a, b in ev]
     total_ms = sum(step_ms)
-    shade_ms = statistics.mean(a.elapsed_time(b) for a, b in ev_shade)
     total_ms = max_over_ranks(total_ms, dev)
-    # SSAO kernel times from separate steps (events between the SSAO launches, outside the
-    # timed region above, whose steps carry events around the compose only)
+    # Kernel times from the same number of further steps (at most 200) with events between the
+    # launches, right after the timed region: each kernel alone (an event before the compose also
+    # keeps it from starting early), the durations the roofline divides by.
     with torch.cuda.stream(stream):
         for _ in range(min(args.steps, 200)):
             flush.zero_()
-            step(ssao_events=True)
+            step(record=True, ssao_events=True)
     stream.synchronize()
+    shade_ms = statistics.mean(a.elapsed_time(b) for a, b in ev_shade)
     ssao_raw_ms = statistics.mean(e[0].elapsed_time(e[1]) for e in ev_ssao)
     ssao_blur_ms = statistics.mean(e[1].elapsed_time(e[2]) for e in ev_ssao)
     if world > 1:
@@ -635,7 +640,7 @@ def run_gpu(args):
         g_ = ep.GBuffer.compact(*rts) if compact else ep.GBuffer.fp32(rts[0], rts[1], rts[3])
         ao_r, ao_b = torch.empty(Ha, Wa, device=dev), torch.empty(Ha, Wa, device=dev)
         return dict(rts=rts, gb=g_, lights=torch.empty_like(lights), ao_raw=ao_r, ao=ao_b,
-                    shp=ep.shade_params(ep.EPBR_SHADE_ALL, ao_b, 2), hdr=torch.empty_like(hdr),
+                    shp=ep.shade_params(shade_flags, ao_b, 2), hdr=torch.empty_like(hdr),
                     ldr=torch.empty_like(ldr))
 
     sets = [buffer_set(), buffer_set()]
@@ -745,6 +750,9 @@ def run_gpu(args):
                                             "median_step_ms": statistics.median(step_ms),
                                             "ssao_raw_ms": ssao_raw_ms, "ssao_blur_ms": ssao_blur_ms,
                                             "ssao_tiled": ep.epbr_ssao_tiled(gb, sp),
+                                            "compose_early_start": not args.no_early_start,
+                                            "kernel_times": f"{min(args.steps, 200)} further steps with events "
+                                                            "between the launches (each kernel alone)",
                                             "wall_s": wall,
                                             **({"step": "ssao_raw + ssao_blur + shade (HDR) + bloom with the tone map "
                                                         "fused per frame; lighting set precomputed once",
@@ -992,11 +1000,14 @@ def measure_batch(args, max_steps: int = 20, specs=None) -> dict:
     tp = ep.tonemap_params()
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
 
+    # the per-view loop with the same early start as the batch's staged graph
+    plain_flags = ep.EPBR_SHADE_ALL | (0 if args.no_early_start else ep.EPBR_SHADE_EARLY_START)
+
     def plain_step():
         for gb, cam, lt, env, ldr, ao_raw, ao in per:
             ep.epbr_ssao_raw(gb, cam, sp, ao_raw, stream=stream)
             ep.epbr_ssao_blur(gb, sp, ao_raw, ao, stream=stream)
-            ep.epbr_shade_tonemap(gb, cam, lt, ibls[env], ep.shade_params(ep.EPBR_SHADE_ALL, ao, 2), None,
+            ep.epbr_shade_tonemap(gb, cam, lt, ibls[env], ep.shade_params(plain_flags, ao, 2), None,
                                   ep.EPBR_HDR_RGBA32F, tp, ldr, stream=stream)
 
     batch = ep.Batch(views, ibls, ep.batch_params(sp), keep=[per, keep])

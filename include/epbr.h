@@ -302,7 +302,15 @@ enum {
   EPBR_SHADE_IBL = 2,           /* split-sum ambient term (needs ibl) */
   EPBR_SHADE_MULTISCATTER = 4,  /* Fdez-Aguera energy compensation of the IBL term */
   EPBR_SHADE_DIFFUSE_ONLY = 8,  /* Lambert only: albedo/pi direct, albedo*irradiance ambient */
-  EPBR_SHADE_ALL = 7
+  EPBR_SHADE_ALL = 7,
+  /* Scheduling only (the image is the same): the compose may start while the kernel just
+   * before it on the stream is still running (programmatic dependent launch).  It decodes the
+   * G-buffer and sums the point lights at once, and waits for that kernel to finish before it
+   * reads the AO image and before it writes its outputs.  Set it only when that kernel writes
+   * none of the G-buffer, the lights, the lighting set and the shadow maps, and reads none of
+   * the outputs: the SSAO passes of this library (epbr_ssao_raw, epbr_ssao_blur, epbr_ssao)
+   * qualify, and the blur lets a compose start only after the raw AO it reads has finished. */
+  EPBR_SHADE_EARLY_START = 16
 };
 enum { EPBR_HDR_RGBA32F = 0, EPBR_HDR_RGBA16F = 1 };
 

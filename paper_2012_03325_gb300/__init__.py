@@ -13,8 +13,8 @@ import torch
 
 from . import _ffi as F
 from ._ffi import (EPBR_GBUFFER_COMPACT, EPBR_GBUFFER_FP32, EPBR_HDR_RGBA16F, EPBR_HDR_RGBA32F,  # noqa: F401
-                   EPBR_SHADE_ALL, EPBR_SHADE_DIFFUSE_ONLY, EPBR_SHADE_DIRECT, EPBR_SHADE_IBL,
-                   EPBR_SHADE_MULTISCATTER, EPBR_TONEMAP_ACES, EPBR_TONEMAP_REINHARD)
+                   EPBR_SHADE_ALL, EPBR_SHADE_DIFFUSE_ONLY, EPBR_SHADE_DIRECT, EPBR_SHADE_EARLY_START,
+                   EPBR_SHADE_IBL, EPBR_SHADE_MULTISCATTER, EPBR_TONEMAP_ACES, EPBR_TONEMAP_REINHARD)
 
 
 class EpbrError(RuntimeError):

@@ -29,6 +29,7 @@ EPBR_SHADE_IBL = 2
 EPBR_SHADE_MULTISCATTER = 4
 EPBR_SHADE_DIFFUSE_ONLY = 8
 EPBR_SHADE_ALL = 7
+EPBR_SHADE_EARLY_START = 16
 EPBR_HDR_RGBA32F = 0
 EPBR_HDR_RGBA16F = 1
 EPBR_TONEMAP_ACES = 0

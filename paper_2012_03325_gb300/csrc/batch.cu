@@ -184,6 +184,7 @@ __global__ void __launch_bounds__(kMvBX* kMvBY, 4)
   __shared__ float4 s_kernel[kBatchMaxK];
   __shared__ ViewDev s_view;
   int tid = threadIdx.y * kMvBX + threadIdx.x;
+  griddep_launch_dependents();  // the blur may put its blocks beside this grid's last wave
   int4 td = __ldg(tiles + blockIdx.x);
   for (int k = tid; k < bp.ssao.K; k += kMvBX * kMvBY) s_kernel[k] = __ldg(bp.ssao.kernel + k);
   mv_stage_view(views, nullptr, td.x, s_view, nullptr, tid, kMvBX * kMvBY);
@@ -201,6 +202,10 @@ __global__ void __launch_bounds__(kMvBX* kMvBY) k_mv_ssao_blur(const ViewDev* __
   __shared__ float s_ao[THd * TWd];
   __shared__ float s_e[THd * TWd];
   __shared__ ViewDev s_view;
+  // after the raw pass by a programmatic edge: nothing is read before it has finished, and the
+  // compose may start once every block is past this point
+  griddep_wait();
+  griddep_launch_dependents();
   int tid = threadIdx.y * kMvBX + threadIdx.x;
   int4 td = __ldg(tiles + blockIdx.x);
   mv_stage_view(views, nullptr, td.x, s_view, nullptr, tid, kMvBX * kMvBY);
@@ -254,14 +259,18 @@ __global__ void __launch_bounds__(kMvBX* kMvBY, 2)
   if (nl <= kLightChunk) mono = __syncthreads_and(stage_lights(s_lights, v.lights, 0, nl, tid, kThreads, s_dup));
   Px s[2];
   bool act[2];
-  float ao[2];
 #pragma unroll
   for (int h = 0; h < 2; ++h) {
     if (in[h]) s[h] = px_decode<FMT>(raw[h], v.cam, x, yy[h]);
     act[h] = in[h] && s[h].surface;
-    ao[h] = act[h] ? __ldg(v.ao + (size_t)(yy[h] >> 1) * v.ao_w + (x >> 1)) : 1.0f;
   }
   shade_lights(s, act, nl, bp.flags, v.lights, s_lights, s_dup, kLightChunk, nl <= kLightChunk, mono, tid, kThreads);
+  // after the blur by a programmatic edge: the blur may still be running up to here; the AO is read,
+  // and the images written, after it has finished
+  griddep_wait();
+  float ao[2];
+#pragma unroll
+  for (int h = 0; h < 2; ++h) ao[h] = act[h] ? __ldg(v.ao + (size_t)(yy[h] >> 1) * v.ao_w + (x >> 1)) : 1.0f;
   float3 c[2];
 #pragma unroll
   for (int h = 0; h < 2; ++h)
@@ -392,15 +401,26 @@ static epbr_status build_tiles(epbr_batch* b) {
   return EPBR_OK;
 }
 
+// Adds a kernel node after `dep` (if any).  With `early` the edge is programmatic: the node's blocks
+// may start once every block of `dep` has started and called griddep_launch_dependents (or
+// exited), and the kernel calls griddep_wait before it reads what `dep` writes.
 static epbr_status add_kernel(epbr_batch* b, cudaGraphNode_t* node, const cudaGraphNode_t* dep, void* func,
-                              dim3 grid, dim3 block, void** args) {
+                              dim3 grid, dim3 block, void** args, bool early = false) {
   cudaKernelNodeParams kp = {};
   kp.func = func;
   kp.gridDim = grid;
   kp.blockDim = block;
   kp.kernelParams = args;
-  if (cudaGraphAddKernelNode(node, b->graph, dep, dep ? 1 : 0, &kp) != cudaSuccess)
+  const bool prog = early && dep;
+  if (cudaGraphAddKernelNode(node, b->graph, prog ? nullptr : dep, (dep && !prog) ? 1 : 0, &kp) != cudaSuccess)
     return fail(EPBR_ERR_CUDA, "batch: kernel node failed: %s", cudaGetErrorString(cudaGetLastError()));
+  if (prog) {
+    cudaGraphEdgeData ed = {};
+    ed.from_port = cudaGraphKernelNodePortProgrammatic;
+    ed.type = cudaGraphDependencyTypeProgrammatic;
+    if (cudaGraphAddDependencies(b->graph, dep, node, &ed, 1) != cudaSuccess)
+      return fail(EPBR_ERR_CUDA, "batch: programmatic edge failed: %s", cudaGetErrorString(cudaGetLastError()));
+  }
   return EPBR_OK;
 }
 
@@ -453,8 +473,10 @@ static epbr_status build_graph(epbr_batch* b) {
     cudaGraphNode_t n0, n1, n2;
     dim3 blk(kMvBX, kMvBY);
     if ((st = add_kernel(b, &n0, nullptr, raw, dim3(b->n_ao_tiles), blk, b->args[0]))) return st;
-    if ((st = add_kernel(b, &n1, &n0, blur, dim3(b->n_ao_tiles), blk, b->args[1]))) return st;
-    if ((st = add_kernel(b, &n2, &n1, shade, dim3(b->ntiles), blk, b->args[2]))) return st;
+    // programmatic edges: the blur's blocks wait on the SMs the raw pass's last wave leaves free, and
+    // the compose's light loops run while the blur does (each waits before it reads the AO)
+    if ((st = add_kernel(b, &n1, &n0, blur, dim3(b->n_ao_tiles), blk, b->args[1], true))) return st;
+    if ((st = add_kernel(b, &n2, &n1, shade, dim3(b->ntiles), blk, b->args[2], true))) return st;
     b->grid = b->ntiles;
   }
   if (cudaGraphInstantiate(&b->exec, b->graph, 0) != cudaSuccess)

@@ -23,11 +23,44 @@ int num_sms();
 long long scan_num_blocks(long long n);
 void launch_exclusive_scan(long long* data, long long n, long long* sums, cudaStream_t s);
 
+// Launches kernel k; with `early` under programmatic stream serialisation, so that its blocks may
+// start once every block of the previous kernel on the stream has started and called
+// griddep_launch_dependents (or exited), instead of after that kernel has finished.  A kernel
+// launched this way must call griddep_wait before it reads anything the previous kernel writes and
+// before it writes anything the previous kernel reads.  Returns the launch's CUDA error.
+template <typename... Params, typename... Args>
+cudaError_t launch_kernel(void (*k)(Params...), dim3 grd, dim3 blk, size_t smem, cudaStream_t s, bool early,
+                          Args&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grd;
+  cfg.blockDim = blk;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = early ? 1 : 0;
+  return cudaLaunchKernelEx(&cfg, k, static_cast<Args&&>(args)...);
+}
+
 constexpr float kPi = 3.14159265358979323846f;
 constexpr float kInvPi = 0.318309886183790671538f;
 constexpr float kInv2Pi = 0.159154943091895335769f;
 constexpr float kRoughMin = 0.045f;
 constexpr float kNvMin = 1e-4f;
+
+// ------------------------------------------------------------------------------------------
+// device: programmatic dependent launch (PTX griddepcontrol, sm_90 and later)
+// ------------------------------------------------------------------------------------------
+// Waits until the grid this one depends on (the previous kernel on the stream, for a launch with
+// `early` set) has completed and its memory operations are visible; returns at once for a grid
+// launched without it.
+__device__ __forceinline__ void griddep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+// Allows a dependent grid launched with `early` to start its blocks before this grid completes.
+__device__ __forceinline__ void griddep_launch_dependents() {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
 
 // ------------------------------------------------------------------------------------------
 // device: small vector algebra on float3

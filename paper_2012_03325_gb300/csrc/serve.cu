@@ -212,7 +212,7 @@ epbr_status enqueue(epbr_server* s, Req* q) {
                             q->L.ao - q->L.ao_raw, st);
   if (e) return e;
   epbr_shade_params sp;
-  sp.flags = s->cfg.flags;
+  sp.flags = s->cfg.flags | EPBR_SHADE_EARLY_START;  // the kernel before it is the SSAO blur (or raw pass)
   sp.ao_scale = 2;
   sp.ao = ao;
   sp.ao_pitch = (int64_t)Wa * 4;

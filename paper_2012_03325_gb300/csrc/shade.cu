@@ -77,10 +77,13 @@ __global__ void __launch_bounds__(kShadeBX* kShadeBY, EPBR_SHADE_MIN_BLOCKS)
     if (in[h]) s[h] = px_decode<FMT>(raw[h], cam, x, yy[h]);
     act[h] = in[h] && s[h].surface;
   }
-  float ao[2];  // loaded before the light loop, which hides their latency
+  shade_lights(s, act, NL, p.flags, lights, s_lights, s_dup, kLightChunk, NL <= kLightChunk, mono, tid, kThreads);
+  // Launched early (EPBR_SHADE_EARLY_START), the kernel before this one on the stream may still be
+  // running up to here: the AO it writes is read, and the outputs written, only after it ends.
+  griddep_wait();
+  float ao[2];
 #pragma unroll
   for (int h = 0; h < 2; ++h) ao[h] = act[h] ? ao_at(p, x, yy[h]) : 1.0f;
-  shade_lights(s, act, NL, p.flags, lights, s_lights, s_dup, kLightChunk, NL <= kLightChunk, mono, tid, kThreads);
   // Both pixels' lookups are issued before either is stored.
   float3 c[2];
 #pragma unroll
@@ -129,14 +132,15 @@ static epbr_status make_ibl_dev(const epbr_ibl* ibl, IblDev* d) {
 }
 
 template <int FMT, int HDR>
-static void launch_shade(dim3 grd, dim3 blk, cudaStream_t s, const GbufDev& g, const CamDev& c, const float4* L,
+static cudaError_t launch_shade(dim3 grd, dim3 blk, cudaStream_t s, const GbufDev& g, const CamDev& c, const float4* L,
                          int NL, const IblDev& ibl, const ShadeDev& p, void* hdr, long long hp, uint8_t* ldr,
                          long long lp) {
   const unsigned long long w = tma_first_wait_ns();
-  if (ldr)
-    k_shade<FMT, HDR, true><<<grd, blk, 0, s>>>(g, c, L, NL, ibl, p, hdr, hp, ldr, lp, w);
-  else
-    k_shade<FMT, HDR, false><<<grd, blk, 0, s>>>(g, c, L, NL, ibl, p, hdr, hp, ldr, lp, w);
+  const bool early = (p.flags & EPBR_SHADE_EARLY_START) != 0;
+  cudaError_t e = launch_kernel(ldr ? k_shade<FMT, HDR, true> : k_shade<FMT, HDR, false>, grd, blk, 0, s, early, g, c, L,
+                                NL, ibl, p, hdr, hp, ldr, lp, w);
+  if (e != cudaSuccess) cudaGetLastError();
+  return e;
 }
 
 static epbr_status shade_common(const epbr_gbuffer* g, const epbr_camera* cam, const epbr_light* lights,
@@ -148,7 +152,8 @@ static epbr_status shade_common(const epbr_gbuffer* g, const epbr_camera* cam, c
   if (st) return st;
   if ((st = validate_camera(cam, g))) return st;
   if (!sp) return fail(EPBR_ERR_INVALID_ARG, "shade params is NULL");
-  if (sp->flags & ~(unsigned)(EPBR_SHADE_DIRECT | EPBR_SHADE_IBL | EPBR_SHADE_MULTISCATTER | EPBR_SHADE_DIFFUSE_ONLY))
+  if (sp->flags & ~(unsigned)(EPBR_SHADE_DIRECT | EPBR_SHADE_IBL | EPBR_SHADE_MULTISCATTER | EPBR_SHADE_DIFFUSE_ONLY |
+                              EPBR_SHADE_EARLY_START))
     return fail(EPBR_ERR_INVALID_ARG, "shade flags 0x%x has unknown bits", sp->flags);
   if (NL < 0 || NL > 65536) return fail(EPBR_ERR_INVALID_ARG, "num_lights %d outside [0, 65536]", NL);
   if (NL > 0 && (sp->flags & EPBR_SHADE_DIRECT) && (!lights || (uintptr_t)lights % 16))
@@ -197,17 +202,23 @@ static epbr_status shade_common(const epbr_gbuffer* g, const epbr_camera* cam, c
       return st;
     return ok();
   }
+  cudaError_t e;
   if (g->format == EPBR_GBUFFER_FP32) {
     if (hdr_format == EPBR_HDR_RGBA32F)
-      launch_shade<EPBR_GBUFFER_FP32, EPBR_HDR_RGBA32F>(grd, blk, s, gd, cd, L, nl, ib, p, hdr, hdr_pitch, ldr, ldr_pitch);
+      e = launch_shade<EPBR_GBUFFER_FP32, EPBR_HDR_RGBA32F>(grd, blk, s, gd, cd, L, nl, ib, p, hdr, hdr_pitch, ldr,
+                                                            ldr_pitch);
     else
-      launch_shade<EPBR_GBUFFER_FP32, EPBR_HDR_RGBA16F>(grd, blk, s, gd, cd, L, nl, ib, p, hdr, hdr_pitch, ldr, ldr_pitch);
+      e = launch_shade<EPBR_GBUFFER_FP32, EPBR_HDR_RGBA16F>(grd, blk, s, gd, cd, L, nl, ib, p, hdr, hdr_pitch, ldr,
+                                                            ldr_pitch);
   } else {
     if (hdr_format == EPBR_HDR_RGBA32F)
-      launch_shade<EPBR_GBUFFER_COMPACT, EPBR_HDR_RGBA32F>(grd, blk, s, gd, cd, L, nl, ib, p, hdr, hdr_pitch, ldr, ldr_pitch);
+      e = launch_shade<EPBR_GBUFFER_COMPACT, EPBR_HDR_RGBA32F>(grd, blk, s, gd, cd, L, nl, ib, p, hdr, hdr_pitch, ldr,
+                                                               ldr_pitch);
     else
-      launch_shade<EPBR_GBUFFER_COMPACT, EPBR_HDR_RGBA16F>(grd, blk, s, gd, cd, L, nl, ib, p, hdr, hdr_pitch, ldr, ldr_pitch);
+      e = launch_shade<EPBR_GBUFFER_COMPACT, EPBR_HDR_RGBA16F>(grd, blk, s, gd, cd, L, nl, ib, p, hdr, hdr_pitch, ldr,
+                                                               ldr_pitch);
   }
+  if (e != cudaSuccess) return fail(EPBR_ERR_CUDA, "k_shade: %s", cudaGetErrorString(e));
   if ((st = check_launch("k_shade"))) return st;
   return ok();
 }

@@ -145,6 +145,9 @@ __global__ void __launch_bounds__(256, 4)
     else
       px_direct_end(s, d);
   }
+  // Launched early (EPBR_SHADE_EARLY_START), the kernel before this one on the stream may still be
+  // running up to here: the AO it writes is read, and the outputs written, only after it ends.
+  griddep_wait();
   const float ao = active ? ao_at(p, x, y) : 1.0f;
   float3 c = px_finish(s, ibl, p.flags, ao);
   if (hdr) store_hdr<HDR>(hdr, hdr_pitch, x, y, c);
@@ -152,13 +155,14 @@ __global__ void __launch_bounds__(256, 4)
 }
 
 template <int FMT, int HDR>
-static void launch_shadow(dim3 grd, dim3 blk, cudaStream_t st, const GbufDev& g, const CamDev& c, const float4* L,
-                          int NL, const IblDev& ibl, const ShadeDev& p, const ShadowDev& sh, void* hdr, long long hp,
-                          uint8_t* ldr, long long lp) {
-  if (ldr)
-    k_shade_shadow<FMT, HDR, true><<<grd, blk, 0, st>>>(g, c, L, NL, ibl, p, sh, hdr, hp, ldr, lp);
-  else
-    k_shade_shadow<FMT, HDR, false><<<grd, blk, 0, st>>>(g, c, L, NL, ibl, p, sh, hdr, hp, ldr, lp);
+static cudaError_t launch_shadow(dim3 grd, dim3 blk, cudaStream_t st, const GbufDev& g, const CamDev& c,
+                                 const float4* L, int NL, const IblDev& ibl, const ShadeDev& p, const ShadowDev& sh,
+                                 void* hdr, long long hp, uint8_t* ldr, long long lp) {
+  const bool early = (p.flags & EPBR_SHADE_EARLY_START) != 0;
+  cudaError_t e = launch_kernel(ldr ? k_shade_shadow<FMT, HDR, true> : k_shade_shadow<FMT, HDR, false>, grd, blk, 0, st,
+                                early, g, c, L, NL, ibl, p, sh, hdr, hp, ldr, lp);
+  if (e != cudaSuccess) cudaGetLastError();
+  return e;
 }
 
 epbr_status launch_shade_shadows(const GbufDev& g, const CamDev& c, int fmt, const float4* L, int NL,
@@ -173,17 +177,21 @@ epbr_status launch_shade_shadows(const GbufDev& g, const CamDev& c, int fmt, con
   ShadowDev sh{s->maps, (const float4*)s->cameras, (long long)s->size * s->size, s->size, s->bias_const,
                s->bias_slope};
   dim3 blk(32, 8), grd((g.W + 31) / 32, (g.H + 7) / 8);
+  cudaError_t e;
   if (fmt == EPBR_GBUFFER_FP32) {
     if (hdr_format == EPBR_HDR_RGBA32F)
-      launch_shadow<EPBR_GBUFFER_FP32, EPBR_HDR_RGBA32F>(grd, blk, st, g, c, L, NL, ibl, p, sh, hdr, hp, ldr, lp);
+      e = launch_shadow<EPBR_GBUFFER_FP32, EPBR_HDR_RGBA32F>(grd, blk, st, g, c, L, NL, ibl, p, sh, hdr, hp, ldr, lp);
     else
-      launch_shadow<EPBR_GBUFFER_FP32, EPBR_HDR_RGBA16F>(grd, blk, st, g, c, L, NL, ibl, p, sh, hdr, hp, ldr, lp);
+      e = launch_shadow<EPBR_GBUFFER_FP32, EPBR_HDR_RGBA16F>(grd, blk, st, g, c, L, NL, ibl, p, sh, hdr, hp, ldr, lp);
   } else {
     if (hdr_format == EPBR_HDR_RGBA32F)
-      launch_shadow<EPBR_GBUFFER_COMPACT, EPBR_HDR_RGBA32F>(grd, blk, st, g, c, L, NL, ibl, p, sh, hdr, hp, ldr, lp);
+      e = launch_shadow<EPBR_GBUFFER_COMPACT, EPBR_HDR_RGBA32F>(grd, blk, st, g, c, L, NL, ibl, p, sh, hdr, hp, ldr,
+                                                                lp);
     else
-      launch_shadow<EPBR_GBUFFER_COMPACT, EPBR_HDR_RGBA16F>(grd, blk, st, g, c, L, NL, ibl, p, sh, hdr, hp, ldr, lp);
+      e = launch_shadow<EPBR_GBUFFER_COMPACT, EPBR_HDR_RGBA16F>(grd, blk, st, g, c, L, NL, ibl, p, sh, hdr, hp, ldr,
+                                                                lp);
   }
+  if (e != cudaSuccess) return fail(EPBR_ERR_CUDA, "k_shade_shadow: %s", cudaGetErrorString(e));
   return check_launch("k_shade_shadow");
 }
 

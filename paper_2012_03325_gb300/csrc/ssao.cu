@@ -173,6 +173,9 @@ __global__ void __launch_bounds__(256, TILED ? EPBR_SSAO_TILED_MIN_BLOCKS : EPBR
   __shared__ float4 s_kernel[kMaxSsaoSamples];
   __shared__ __align__(8) unsigned long long s_bar;
   extern __shared__ __align__(128) float s_dep[];  // TILED: kSsaoTileH x kSsaoTileW depths
+  // a blur launched early after this kernel may put its blocks on the SMs this grid's last wave
+  // leaves free; it waits for this grid before it reads the AO
+  griddep_launch_dependents();
   const int tid = threadIdx.y * 32 + threadIdx.x;
   // tile origin in pixels (a scale-2 block covers pixels [64 bx, 64 bx + 64) x [32 by, 32 by + 32))
   const int tx0 = (int)blockIdx.x * 64 - kSsaoHalo, ty0 = (int)blockIdx.y * 32 - kSsaoHalo;
@@ -231,6 +234,10 @@ __global__ void __launch_bounds__(kBlurBX* kBlurBY) k_ssao_blur(GbufDev g, SsaoD
                                                                 long long out_pitch, int Wa, int Ha) {
   __shared__ float s_ao[kBlurTH][kBlurTW];
   __shared__ float s_e[kBlurTH][kBlurTW];
+  // launched early: nothing is read before the previous kernel (the raw AO's) has finished;
+  // a compose launched early after this one may start once every block is past this point
+  griddep_wait();
+  griddep_launch_dependents();
   const int R = p.R;
   const int tw = kBlurBX + 2 * R, th = kBlurBY + 2 * R;
   const int i0 = blockIdx.x * kBlurBX - R, j0 = blockIdx.y * kBlurBY - R;
@@ -265,6 +272,8 @@ __global__ void __launch_bounds__(kBlurBX* kBlurBY) k_ssao_blur2(GbufDev g, Ssao
                                                                  long long in_pitch, float* __restrict__ out,
                                                                  long long out_pitch, int Wa, int Ha) {
   __shared__ float2 s_ae[kBlur2TH][kBlur2TW];
+  griddep_wait();  // as k_ssao_blur
+  griddep_launch_dependents();
   const int i0 = blockIdx.x * kBlurBX - kBlur2R, j0 = blockIdx.y * (2 * kBlurBY) - kBlur2R;
   const float inf = __int_as_float(0x7f800000);
   for (int q = threadIdx.y * kBlurBX + threadIdx.x; q < kBlur2TW * kBlur2TH; q += kBlurBX * kBlurBY) {
@@ -491,16 +500,22 @@ extern "C" epbr_status epbr_ssao_blur(const epbr_gbuffer* g, const epbr_ssao_par
   GbufDev gd = make_gbuf(*g);
   SsaoDev sd = make_ssao(*p);
   cudaStream_t s = (cudaStream_t)stream;
+  // Launched early (programmatic stream serialisation): the blocks may take the SMs that the
+  // previous kernel's last wave leaves free and wait there for it (griddep_wait before any read),
+  // which hides the launch gap after the raw AO pass.
+  const bool fp32 = g->format == EPBR_GBUFFER_FP32;
+  cudaError_t e;
   if (p->blur_radius == kBlur2R) {  // the 7x7 blur: two texels per thread
     dim3 grd2((Wa + kBlurBX - 1) / kBlurBX, (Ha + 2 * kBlurBY - 1) / (2 * kBlurBY));
-    if (g->format == EPBR_GBUFFER_FP32)
-      k_ssao_blur2<EPBR_GBUFFER_FP32><<<grd2, blk, 0, s>>>(gd, sd, in, in_pitch, out, out_pitch, Wa, Ha);
-    else
-      k_ssao_blur2<EPBR_GBUFFER_COMPACT><<<grd2, blk, 0, s>>>(gd, sd, in, in_pitch, out, out_pitch, Wa, Ha);
-  } else if (g->format == EPBR_GBUFFER_FP32) {
-    k_ssao_blur<EPBR_GBUFFER_FP32><<<grd, blk, 0, s>>>(gd, sd, in, in_pitch, out, out_pitch, Wa, Ha);
+    e = launch_kernel(fp32 ? k_ssao_blur2<EPBR_GBUFFER_FP32> : k_ssao_blur2<EPBR_GBUFFER_COMPACT>, grd2, blk, 0, s,
+                      true, gd, sd, in, (long long)in_pitch, out, (long long)out_pitch, Wa, Ha);
   } else {
-    k_ssao_blur<EPBR_GBUFFER_COMPACT><<<grd, blk, 0, s>>>(gd, sd, in, in_pitch, out, out_pitch, Wa, Ha);
+    e = launch_kernel(fp32 ? k_ssao_blur<EPBR_GBUFFER_FP32> : k_ssao_blur<EPBR_GBUFFER_COMPACT>, grd, blk, 0, s, true,
+                      gd, sd, in, (long long)in_pitch, out, (long long)out_pitch, Wa, Ha);
+  }
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(EPBR_ERR_CUDA, "k_ssao_blur: %s", cudaGetErrorString(e));
   }
   if ((st = check_launch("k_ssao_blur"))) return st;
   return ok();

@@ -156,7 +156,7 @@ def shade_call(lib, g=None, cam=None, lights=FAKE, nl=4, flags=F.EPBR_SHADE_DIRE
 
 
 def test_shade_checks(lib):
-    assert shade_call(lib, flags=0x10) == INVALID                     # unknown flag bit
+    assert shade_call(lib, flags=0x20) == INVALID                     # unknown flag bit
     assert shade_call(lib, flags=F.EPBR_SHADE_ALL) == INVALID         # IBL requested, no lighting set
     assert shade_call(lib, nl=-1) == INVALID
     assert shade_call(lib, nl=65537) == INVALID
