@@ -50,6 +50,20 @@ def test_binding_covers_every_symbol_and_matches_struct_sizes():
     assert ctypes.sizeof(_ffi.epbr_ibl) == 8 + 8 + 8 + 8 + 16 * 8 + 16 * 4 * 2
 
 
+def test_binding_constants_match_the_header():
+    """Every enumerator of include/*.h (EPBR_NAME = value) exists in the binding with its value."""
+    from paper_2012_03325_gb300 import _ffi
+    consts = {}
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        src = re.sub(r"/\*.*?\*/", "", open(h).read(), flags=re.S)
+        for body in re.findall(r"enum\s*\{(.*?)\}", src, flags=re.S):
+            for name, val in re.findall(r"\b(EPBR_[A-Z0-9_]+)\s*=\s*(-?\d+)", body):
+                consts[name] = int(val)
+    assert consts.get("EPBR_SHADE_EARLY_START") == 16
+    wrong = {n: (v, getattr(_ffi, n, None)) for n, v in consts.items() if getattr(_ffi, n, None) != v}
+    assert not wrong, wrong
+
+
 def test_oracle_is_not_imported_by_the_product():
     for f in glob.glob(os.path.join(ROOT, "paper_2012_03325_gb300", "**", "*.*"), recursive=True):
         if f.endswith((".py", ".cu", ".cuh", ".h", ".inc")):
