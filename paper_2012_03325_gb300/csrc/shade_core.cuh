@@ -436,8 +436,9 @@ __device__ __forceinline__ void px_direct_mono2(const Frame2& f, Sums2& S, const
     float2 nlc = pmul(make_float2(fmaxf(Lz.x, 0.0f), fmaxf(Lz.y, 0.0f)), rs);  // max(n.l, 0)
     float2 xx = pfma(mhalf, make_float2(sqrt_ftz(hh.x), sqrt_ftz(hh.y)), one);  // 1 - v.h
     float2 x2 = pmul(xx, xx);
-    float2 fc = pmul(pmul(x2, x2), xx);  // (1 - v.h)^5 in the FMA pipe (the MUFU pipe is the busier one here)
-    float2 icw = pmul(pmul(IC, pmul(rs, rs)), nlc);        // Ic (n.l) / d^2
+    float2 fc = pmul(pmul(x2, x2), xx);  // (1 - v.h)^5 in the FMA pipe (as ex2(5 lg2) the MUFU pipe would be the bound)
+    // Ic (n.l) / d^2, with 1 / d^2 from the MUFU pipe (which has room here) instead of rs * rs
+    float2 icw = pmul(pmul(IC, make_float2(rcp_ftz(d2.x), rcp_ftz(d2.y))), nlc);
     float2 q = pmul(pmul(den, den), pfma(nlc, f.omk, f.k));
     float2 icb = pmul(icw, pmul(pmul(hh, hh), make_float2(rcp_ftz(q.x), rcp_ftz(q.y))));
     sw = padd(sw, icw);
