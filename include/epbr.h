@@ -247,7 +247,9 @@ epbr_status epbr_ssao_workspace_size(const epbr_gbuffer* gbuffer,
  * fetched; the sample occludes by [e_b <= e_S - bias] * smoothstep(0, 1, radius / |e_P - e_b|).
  * Off-screen, behind-camera and background samples do not occlude.  AO = 1 - sum / K.  AO of a
  * background pixel is 1.  `ao` is DEVICE float, rows of `ao_pitch` bytes.  EPBR_ERR_UNSUPPORTED
- * when the depth plane spans more than 2^32 texels (height x pitch[3] / 4). */
+ * when the depth plane spans more than 2^32 texels (height x pitch[3] / 4).  Scheduling: its
+ * blocks release programmatic dependents (a kernel launched next with programmatic stream
+ * serialisation, such as epbr_ssao_blur) at their start; results do not depend on it. */
 epbr_status epbr_ssao_raw(const epbr_gbuffer* gbuffer, const epbr_camera* camera,
                           const epbr_ssao_params* params, float* ao, int64_t ao_pitch,
                           void* stream);
@@ -283,7 +285,11 @@ epbr_status epbr_ssao_set_tile_wait(uint64_t first_wait_ns, uint64_t* previous_n
 
 /* Depth-aware blur of an AO image: out_p = sum_q w_q ao_q / sum_q w_q over the
  * (2R+1)^2 window (clipped to the image) with w_q = exp(-(dx^2+dy^2)/(2 sigma_s^2)) *
- * exp(-|e_q - e_p| / (sigma_z e_p)), background taps weighted 0; background pixels get 1. */
+ * exp(-|e_q - e_p| / (sigma_z e_p)), background taps weighted 0; background pixels get 1.
+ * Scheduling: launched as a programmatic dependent of the previous kernel on the stream; every
+ * block waits for that kernel to finish (griddepcontrol.wait) before its first memory access, and
+ * only then releases its own dependents (a compose launched with EPBR_SHADE_EARLY_START).
+ */
 epbr_status epbr_ssao_blur(const epbr_gbuffer* gbuffer, const epbr_ssao_params* params,
                            const float* ao_in, int64_t in_pitch, float* ao_out,
                            int64_t out_pitch, void* stream);
@@ -573,7 +579,9 @@ typedef struct epbr_batch_params {
  *   EPBR_BATCH_FUSED   one persistent kernel; per tile of tile_w x tile_h pixels: unblurred
  *                      SSAO with a halo, blur, compose, tone map, all in shared memory
  *   EPBR_BATCH_STAGED  three kernels (SSAO, blur, compose + tone map), each over the tiles of
- *                      every view, AO images in batch-owned memory */
+ *                      every view, AO images in batch-owned memory; the graph joins them by
+ *                      programmatic edges (the compose's light loop may run while the blur does,
+ *                      its AO read waits for the blur) */
 enum { EPBR_BATCH_FUSED = 0, EPBR_BATCH_STAGED = 1 };
 
 /* Library-owned batch: device copies of the view descriptors, the tile list and a CUDA graph
