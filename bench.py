@@ -1208,11 +1208,12 @@ def measure_serve(args, rates=(10, 30, 100, 300, 1000, 2000)) -> dict:
         for rate in rates:
             n = int(min(n_req, max(20, rate * args.serve_seconds)))
             per_rate.append(run(served, make_requests(n, 100 + rate), rate))
-        # saturation: the same burst served and one at a time, three interleaved pairs (a pair's two
-        # runs see the same host conditions; the host link and CPU are shared with other jobs): the
-        # pair with the median ratio is reported, every pair is listed
+        # saturation: the same burst served and one at a time, seven interleaved pairs (a pair's two
+        # runs see the same host conditions; the host link and CPU are shared with other jobs, and a
+        # burst lasts only tens of milliseconds): the pair with the median ratio is reported, every
+        # pair is listed
         pairs = []
-        for k in range(3):
+        for k in range(7):
             b_ = run(served, make_requests(n_req, 9 + k), None)
             f_ = run(fifo, make_requests(n_req, 9 + k), None)
             pairs.append((b_["mpx_s"] / f_["mpx_s"], b_, f_))
