@@ -822,7 +822,7 @@ def run_gpu(args):
         torch.cuda.empty_cache()
         mb = measure_batch(args, max_steps=10)
         line["batch"] = {k: mb[k] for k in ("value", "unit", "speedup_vs_plain", "plain_per_view", "ms_per_step",
-                                            "steps", "plan", "workload", "clocks", "l2")}
+                                            "steps", "plan", "workload", "clocks", "l2", "timing")}
         # many small views (the serving workload's 256x256 class), where the per-view loop is
         # bound by its launches and partly idle grids
         ms_ = measure_batch(args, max_steps=10, specs=small_batch_views())
@@ -1015,26 +1015,29 @@ def measure_batch(args, max_steps: int = 20, specs=None) -> dict:
     with torch.cuda.stream(stream):
         plan = batch.autotune(cache, stream=stream)
 
-    def timed(fn, steps):
-        ms = []
+    def timed_interleaved(fns, steps):
+        """Steps of every form alternated (a flushed L2 before each), so that all forms see the same
+        conditions of a shared box; per form the list of step times."""
+        ev = [[] for _ in fns]
         with torch.cuda.stream(stream):
             for _ in range(max(3, args.warmup)):
-                fn()
+                for fn in fns:
+                    fn()
             for _ in range(steps):
-                flush.zero_()
-                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                a.record(stream)
-                fn()
-                b.record(stream)
-                ms.append((a, b))
+                for k, fn in enumerate(fns):
+                    flush.zero_()
+                    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    a.record(stream)
+                    fn()
+                    b.record(stream)
+                    ev[k].append((a, b))
         stream.synchronize()
-        return [a.elapsed_time(b) for a, b in ms]
+        return [[a.elapsed_time(b) for a, b in e] for e in ev]
 
     steps = max(3, min(args.steps, max_steps))
     with ClockSampler(torch.cuda.current_device()) as clk:
         clk.mark_start()
-        plain_ms = timed(plain_step, steps)
-        batch_ms = timed(lambda: batch.launch(stream=stream), steps)
+        plain_ms, batch_ms = timed_interleaved([plain_step, lambda: batch.launch(stream=stream)], steps)
         clk.mark_end()
     batch.close()
     plain = total_px * steps / (sum(plain_ms) * 1e-3) / 1e6
@@ -1049,7 +1052,8 @@ def measure_batch(args, max_steps: int = 20, specs=None) -> dict:
             "plain_per_view": {"value": plain, "unit": "Mpixels/s", "ms_per_step": sum(plain_ms) / steps,
                                "launches_per_step": 3 * len(specs)},
             "speedup_vs_plain": batched / plain, "clocks": clk.summary(),
-            "l2": "flushed between timed steps (256 MB write)"}
+            "l2": "flushed between timed steps (256 MB write)",
+            "timing": "plain and batched steps alternated, each timed alone"}
 
 
 def run_batch(args):
@@ -1059,7 +1063,7 @@ def run_batch(args):
     line = {"metric": METRIC, "value": m["value"], "unit": "Mpixels/s", "n_gpus": 1, "steps": m["steps"],
             "warmup": args.warmup, "ms_per_step": m["ms_per_step"], "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": m["workload"], "plan": m["plan"], "l2": m["l2"]},
+            "config": {"workload": m["workload"], "plan": m["plan"], "l2": m["l2"], "timing": m["timing"]},
             "plain_per_view": m["plain_per_view"], "speedup_vs_plain": m["speedup_vs_plain"], "gpu_launches": 1,
             "clocks": m["clocks"]}
     print(json.dumps(line), flush=True)
