@@ -1047,7 +1047,7 @@ def measure_batch(args, max_steps: int = 20, specs=None) -> dict:
             "workload": f"batch: {len(specs)} views, {total_px / 1e6:.1f} Mpx, resolutions "
                         f"{sorted(set((W, H) for W, H, *_r in specs))}, 16-256 lights (log-uniform), "
                         "8 environments 1024x512 (M=8, N_s=1024, LUT 64^2), SSAO 32 + 7x7",
-            "plan": {"mode": ["fused", "staged"][plan[0]], "tile_w": plan[1], "tile_h": plan[2],
+            "plan": {"mode": ["fused", "staged", "per_view"][plan[0]], "tile_w": plan[1], "tile_h": plan[2],
                      "light_chunk": plan[3]},
             "plain_per_view": {"value": plain, "unit": "Mpixels/s", "ms_per_step": sum(plain_ms) / steps,
                                "launches_per_step": 3 * len(specs)},

@@ -581,8 +581,11 @@ typedef struct epbr_batch_params {
  *   EPBR_BATCH_STAGED  three kernels (SSAO, blur, compose + tone map), each over the tiles of
  *                      every view, AO images in batch-owned memory; the graph joins them by
  *                      programmatic edges (the compose's light loop may run while the blur does,
- *                      its AO read waits for the blur) */
-enum { EPBR_BATCH_FUSED = 0, EPBR_BATCH_STAGED = 1 };
+ *                      its AO read waits for the blur)
+ *   EPBR_BATCH_PER_VIEW epbr_ssao_raw, epbr_ssao_blur and epbr_shade_tonemap (with
+ *                      EPBR_SHADE_EARLY_START) of every view, recorded into the graph by stream
+ *                      capture: the per-view kernels without per-launch host work */
+enum { EPBR_BATCH_FUSED = 0, EPBR_BATCH_STAGED = 1, EPBR_BATCH_PER_VIEW = 2 };
 
 /* Library-owned batch: device copies of the view descriptors, the tile list and a CUDA graph
  * (memset of the tile counter -> the fused kernel).  The views' buffers are referenced, not
@@ -596,7 +599,7 @@ epbr_status epbr_batch_create(const epbr_view* views, int32_t n_views, const epb
                               int32_t n_ibls, const epbr_batch_params* params, epbr_batch** out);
 /* Enqueues one replay of the batch's graph on `stream`. */
 epbr_status epbr_batch_launch(epbr_batch* batch, void* stream);
-/* Times every plan (each fused tile shape x light chunk, and the staged mode) on this batch and
+/* Times every plan (each fused tile shape x light chunk, the staged and the per-view mode) on this batch and
  * keeps the fastest (synchronises `stream`).  With `cache_path`, a plan stored for the same
  * batch key is reused without timing, and new results are appended as text lines
  * "key mode tile_w tile_h chunk ms". */

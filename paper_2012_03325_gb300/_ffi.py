@@ -36,6 +36,7 @@ EPBR_TONEMAP_ACES = 0
 EPBR_TONEMAP_REINHARD = 1
 EPBR_BATCH_FUSED = 0
 EPBR_BATCH_STAGED = 1
+EPBR_BATCH_PER_VIEW = 2
 
 
 class epbr_camera(C.Structure):

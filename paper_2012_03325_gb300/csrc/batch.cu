@@ -1,4 +1,4 @@
-// Many views in one persistent launch (the batching form of the pass).
+// Many views in one graph launch (the batching form of the pass).
 //
 // k_batch: 256-thread blocks pull tiles of TW x TH pixels from an atomic counter over a tile
 // list that spans every view (views with the most light work first).  Per tile, without leaving
@@ -296,7 +296,7 @@ struct TileShape {
 };
 static const TileShape kShapes[] = {{64, 32}, {128, 32}, {64, 64}};
 static const int kChunks[] = {128, 256};
-enum { kModeFused = 0, kModeStaged = 1 };
+enum { kModeFused = 0, kModeStaged = 1, kModePerView = 2 };
 
 typedef void (*BatchKernel)(const ViewDev*, const IblDev*, const int4*, int, int*, BatchDev);
 
@@ -330,6 +330,11 @@ struct epbr_batch {
   cudaGraphExec_t exec = nullptr;
   int grid = 0;
   void* args[3][6];
+  // per-view plan: the views, lighting sets and parameters as passed to epbr_batch_create (the
+  // per-view entry points are recorded into the graph by stream capture)
+  std::vector<epbr_view> src_views;
+  std::vector<epbr_ibl> src_ibls;
+  epbr_batch_params params;
 };
 
 static void drop_graph(epbr_batch* b) {
@@ -424,7 +429,53 @@ static epbr_status add_kernel(epbr_batch* b, cudaGraphNode_t* node, const cudaGr
   return EPBR_OK;
 }
 
+// Per-view plan: epbr_ssao_raw, epbr_ssao_blur and epbr_shade_tonemap (EPBR_SHADE_EARLY_START)
+// of every view, recorded into the batch's graph by capturing a private stream, so the graph
+// replays the per-view kernels (TMA-tiled SSAO, two-texel blur, two-pixel compose) with the
+// programmatic edges of their early launches and without per-launch host work.  Replaces the
+// graph created by build_graph.
+static epbr_status capture_per_view(epbr_batch* b) {
+  cudaGraphDestroy(b->graph);
+  b->graph = nullptr;
+  cudaStream_t cs;
+  if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess)
+    return fail(EPBR_ERR_CUDA, "batch: capture stream: %s", cudaGetErrorString(cudaGetLastError()));
+  if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+    cudaStreamDestroy(cs);
+    return fail(EPBR_ERR_CUDA, "batch: begin capture: %s", cudaGetErrorString(cudaGetLastError()));
+  }
+  epbr_status st = EPBR_OK;
+  const epbr_batch_params& p = b->params;
+  for (int i = 0; i < b->n_views && !st; ++i) {
+    const epbr_view& v = b->src_views[i];
+    const ViewDev& d = b->views[i];
+    const int64_t ap = (int64_t)d.ao_w * 4;
+    st = epbr_ssao_raw(&v.gbuffer, &v.camera, &p.ssao, d.ao_raw, ap, cs);
+    if (!st) st = epbr_ssao_blur(&v.gbuffer, &p.ssao, d.ao_raw, ap, d.ao, ap, cs);
+    if (!st) {
+      epbr_shade_params sp;
+      sp.flags = p.flags | EPBR_SHADE_EARLY_START;
+      sp.ao_scale = 2;
+      sp.ao = d.ao;
+      sp.ao_pitch = ap;
+      st = epbr_shade_tonemap(&v.gbuffer, &v.camera, v.lights, v.num_lights, &b->src_ibls[v.ibl_index], &sp, v.hdr,
+                              p.hdr_format, v.hdr_pitch, &p.tonemap, v.ldr, v.ldr_pitch, cs);
+    }
+  }
+  cudaGraph_t g = nullptr;
+  const cudaError_t e = cudaStreamEndCapture(cs, &g);
+  cudaStreamDestroy(cs);
+  if (st) {
+    if (g) cudaGraphDestroy(g);
+    return st;
+  }
+  if (e != cudaSuccess || !g) return fail(EPBR_ERR_CUDA, "batch: end capture: %s", cudaGetErrorString(e));
+  b->graph = g;
+  return EPBR_OK;
+}
+
 // Fused: memset(counter) -> k_batch.  Staged: k_mv_ssao_raw -> k_mv_ssao_blur -> k_mv_shade.
+// Per view: the per-view entry points of every view, captured.
 static epbr_status build_graph(epbr_batch* b) {
   drop_graph(b);
   b->bp.light_chunk = b->chunk;
@@ -456,7 +507,7 @@ static epbr_status build_graph(epbr_batch* b) {
     if (cudaGraphAddMemsetNode(&n_memset, b->graph, nullptr, 0, &mp) != cudaSuccess)
       return fail(EPBR_ERR_CUDA, "batch: memset node failed");
     if ((st = add_kernel(b, &n_kernel, &n_memset, (void*)k, dim3(b->grid), dim3(kBatchThreads), a))) return st;
-  } else {
+  } else if (b->mode == kModeStaged) {
     void* raw = fp32 ? (void*)k_mv_ssao_raw<EPBR_GBUFFER_FP32> : (void*)k_mv_ssao_raw<EPBR_GBUFFER_COMPACT>;
     void* blur = fp32 ? (void*)k_mv_ssao_blur<EPBR_GBUFFER_FP32> : (void*)k_mv_ssao_blur<EPBR_GBUFFER_COMPACT>;
     void* shade = fp32 ? (void*)k_mv_shade<EPBR_GBUFFER_FP32> : (void*)k_mv_shade<EPBR_GBUFFER_COMPACT>;
@@ -478,6 +529,9 @@ static epbr_status build_graph(epbr_batch* b) {
     if ((st = add_kernel(b, &n1, &n0, blur, dim3(b->n_ao_tiles), blk, b->args[1], true))) return st;
     if ((st = add_kernel(b, &n2, &n1, shade, dim3(b->ntiles), blk, b->args[2], true))) return st;
     b->grid = b->ntiles;
+  } else {
+    if ((st = capture_per_view(b))) return st;
+    b->grid = b->ntiles;
   }
   if (cudaGraphInstantiate(&b->exec, b->graph, 0) != cudaSuccess)
     return fail(EPBR_ERR_CUDA, "batch: graph instantiation failed: %s", cudaGetErrorString(cudaGetLastError()));
@@ -486,7 +540,7 @@ static epbr_status build_graph(epbr_batch* b) {
 
 static bool plan_valid(int mode, int tw, int th, int chunk) {
   if (chunk < 1 || chunk > kLightChunk) return false;
-  if (mode == kModeStaged) return true;
+  if (mode == kModeStaged || mode == kModePerView) return true;
   return mode == kModeFused && pick_kernel<EPBR_GBUFFER_FP32>(tw, th) != nullptr;
 }
 
@@ -585,6 +639,9 @@ extern "C" epbr_status epbr_batch_create(const epbr_view* views, int32_t n_views
     d.S = std::max(1, s.lut_size);
     d.M = std::max(1, s.num_levels);
   }
+  b->src_views.assign(views, views + n_views);
+  b->src_ibls.assign(ibls, ibls + n_ibls);
+  b->params = *p;
   memset(&b->bp, 0, sizeof(b->bp));
   b->bp.flags = p->flags;
   b->bp.hdr_format = p->hdr_format;
@@ -660,6 +717,7 @@ extern "C" epbr_status epbr_batch_autotune(epbr_batch* b, const char* cache_path
   for (const TileShape& sh : kShapes)
     for (int ch : kChunks) cands.push_back({kModeFused, sh.w, sh.h, ch});
   cands.push_back({kModeStaged, kMvBX, kMvBY, kLightChunk});
+  cands.push_back({kModePerView, kMvBX, kMvBY, kLightChunk});
   cudaStream_t s = (cudaStream_t)stream;
   cudaEvent_t e0, e1;
   if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)

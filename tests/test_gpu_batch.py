@@ -68,7 +68,7 @@ def test_batch_equals_per_view_for_every_plan(compact):
     b = ep.Batch(views, ibls, ep.batch_params(sp), keep=keep)
     try:
         plans = [(ep.F.EPBR_BATCH_FUSED, tw, th, ch) for tw, th in [(64, 32), (128, 32), (64, 64)]
-                 for ch in (128, 256)] + [(ep.F.EPBR_BATCH_STAGED, 32, 8, 256)]
+                 for ch in (128, 256)] + [(ep.F.EPBR_BATCH_STAGED, 32, 8, 256), (ep.F.EPBR_BATCH_PER_VIEW, 32, 8, 256)]
         for md, tw, th, ch in plans:
             for _, _, ldr, hdr, _ in per:
                 ldr.zero_()
@@ -129,7 +129,7 @@ def test_batch_colored_lights_equal_per_view():
             d["lights"].copy_(torch.from_numpy(inp.scene.lights))
     ref = _per_view(per, ibls, sp)
     b = ep.Batch(views, ibls, ep.batch_params(sp), keep=keep)
-    for md in (ep.F.EPBR_BATCH_FUSED, ep.F.EPBR_BATCH_STAGED):
+    for md in (ep.F.EPBR_BATCH_FUSED, ep.F.EPBR_BATCH_STAGED, ep.F.EPBR_BATCH_PER_VIEW):
         b.set_plan(md, 64, 32, 128)
         b.launch()
         torch.cuda.synchronize()
@@ -180,7 +180,7 @@ def test_batch_hdr_against_oracle(compact, hdr16):
         tied = np.repeat(np.repeat(lo != hi, 2, 0), 2, 1)[:inp.H, :inp.W].reshape(-1)
         refs.append((gb, cam, a, ref, tied))
     try:
-        for md in (ep.F.EPBR_BATCH_FUSED, ep.F.EPBR_BATCH_STAGED):
+        for md in (ep.F.EPBR_BATCH_FUSED, ep.F.EPBR_BATCH_STAGED, ep.F.EPBR_BATCH_PER_VIEW):
             b.set_plan(md, 64, 32, 128)
             b.launch()
             torch.cuda.synchronize()

@@ -71,7 +71,8 @@ def test_batch_writes_stay_inside_each_view():
         guards += [ldr, hdr]
     b = ep.Batch(views, [ibl], ep.batch_params(sp), keep=keep)
     for plan in [(ep.F.EPBR_BATCH_FUSED, 64, 32, 256), (ep.F.EPBR_BATCH_FUSED, 128, 32, 128),
-                 (ep.F.EPBR_BATCH_FUSED, 64, 64, 256), (ep.F.EPBR_BATCH_STAGED, 32, 8, 256)]:
+                 (ep.F.EPBR_BATCH_FUSED, 64, 64, 256), (ep.F.EPBR_BATCH_STAGED, 32, 8, 256),
+                 (ep.F.EPBR_BATCH_PER_VIEW, 32, 8, 256)]:
         b.set_plan(*plan)
         b.launch()
         torch.cuda.synchronize()

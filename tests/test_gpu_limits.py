@@ -128,7 +128,8 @@ def test_batch_largest_blur_and_sample_count():
             ep.epbr_shade_tonemap(d["gb"], d["cam"], d["lights"], ibl, ep.shade_params(ep.EPBR_SHADE_ALL, ao, 2),
                                   h, ep.EPBR_HDR_RGBA32F, ep.tonemap_params(), ldr)
             refs.append(np_(h))
-        for md, tw, th in ((ep.F.EPBR_BATCH_FUSED, 64, 32), (ep.F.EPBR_BATCH_STAGED, 32, 8)):
+        for md, tw, th in ((ep.F.EPBR_BATCH_FUSED, 64, 32), (ep.F.EPBR_BATCH_STAGED, 32, 8),
+                           (ep.F.EPBR_BATCH_PER_VIEW, 32, 8)):
             for _, _, hdr in per:
                 hdr.zero_()
             b.set_plan(md, tw, th, 256)
