@@ -9,8 +9,13 @@
 //   3. compose of every pixel (shade_core.cuh) with its view's lights staged in shared memory
 //      and its lighting set, AO read from shared memory, tone map fused, stores.
 // The counter is reset by a memset node and the kernel launched by a kernel node of one CUDA
-// graph, built explicitly (no stream capture) and replayed per frame.  epbr_batch_autotune times
-// the tile shapes and light-chunk sizes on the batch itself and keeps the fastest.
+// graph, built explicitly and replayed per frame.
+// Staged plan: k_mv_ssao_raw, k_mv_ssao_blur and k_mv_shade, each one launch over the tiles of
+// every view, joined by programmatic edges in an explicitly built graph.
+// Per-view plan: the per-view entry points of every view recorded into the graph by stream
+// capture (the only plan built that way).
+// epbr_batch_autotune times the fused tile shapes and light-chunk sizes, the staged and the
+// per-view plan on the batch itself and keeps the fastest.
 #include <stdio.h>
 #include <string.h>
 
